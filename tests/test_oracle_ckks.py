@@ -1,0 +1,205 @@
+"""Pins of the oracle RNS-CKKS (sampling, encoding, encryption, homomorphic operations)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ckks, ring
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _params(log_n=6, data=(60, 40, 40), special=(60,), ls=40):
+    return ckks.Params(log_n, data, special, ls)
+
+
+def test_splitmix64_published_sequence():
+    g = json.load(open(os.path.join(GOLD, "splitmix64.json")))
+    assert [int(x) for x in ckks.draws(g["seed"], 0, len(g["outputs"]))] == g["outputs"]
+
+
+def test_sampler_distributions():
+    h = ckks.stream_key(42, ckks.P_PK_E)
+    e = ckks.sample_gaussian(h, 200000, 3.2)
+    assert np.abs(e).max() <= 19
+    assert abs(e.std() - 3.2) < 0.05 and abs(e.mean()) < 0.05
+    t = ckks.sample_ternary(ckks.stream_key(42, ckks.P_SECRET), 90000)
+    assert set(np.unique(t).tolist()) == {-1, 0, 1}
+    for v in (-1, 0, 1):
+        assert abs((t == v).mean() - 1 / 3) < 0.01
+    q = ckks.gen_primes(10, [60])[0]
+    u = ckks.sample_uniform(ckks.stream_key(42, ckks.P_PK_A), 100000, q)
+    assert (u < np.uint64(q)).all()
+    # mean of a uniform residue is ~ q/2
+    assert abs(float(np.mean(u.astype(np.float64))) / q - 0.5) < 0.01
+    # the streams differ between purposes and objects
+    assert ckks.stream_key(1, 2, 3) != ckks.stream_key(1, 2, 4) != ckks.stream_key(1, 3, 3)
+
+
+def test_gaussian_table_is_a_cdf():
+    T = ckks.gaussian_table(3.2)
+    assert all(a < b for a, b in zip(T, T[1:])) and T[-1] <= (1 << 63)
+    # P(|e| = 0) = rho(0) / (rho(0) + 2 sum rho(x))
+    rho = [math.exp(-x * x / (2 * 3.2 ** 2)) for x in range(20)]
+    assert abs(T[0] / 2 ** 63 - 1 / (1 + 2 * sum(rho[1:]))) < 1e-12
+
+
+def test_slot_count_matches_paper():
+    g = json.load(open(os.path.join(GOLD, "slots.json")))
+    prm = ckks.Params(g["log_n"], (60, 40, 40), (60,), 40)
+    assert prm.slots == g["slots"]
+
+
+def test_encode_is_canonical_embedding():
+    prm = _params(log_n=5)
+    enc = ckks.Encoder(prm)
+    rng = np.random.default_rng(0)
+    z = rng.normal(size=prm.slots)
+    m = enc.encode(z)
+    # evaluate the integer polynomial at zeta^(5^t) directly
+    zeta = np.exp(1j * np.pi / prm.n)
+    for t in range(prm.slots):
+        root = zeta ** pow(5, t, 2 * prm.n)
+        val = sum(int(m[j]) * root ** j for j in range(prm.n)) / prm.delta
+        assert abs(val - z[t]) < 1e-9
+    # round trip via decode
+    assert np.abs(enc.decode(m) - z).max() < 2 ** -30 * np.abs(z).max() * prm.n
+
+
+def test_encode_constant_is_constant_polynomial():
+    prm = _params(log_n=8)
+    enc = ckks.Encoder(prm)
+    for c in (0.5, 3.0, -2.0):
+        m = enc.encode(np.full(prm.slots, c))
+        assert m[0] == round(c * prm.delta) and (m[1:] == 0).all()
+
+
+def _int_negacyclic(a, b):
+    n = len(a)
+    out = [0] * n
+    for i in range(n):
+        if a[i] == 0:
+            continue
+        for j in range(n):
+            k = i + j
+            if k < n:
+                out[k] += a[i] * b[j]
+            else:
+                out[k - n] -= a[i] * b[j]
+    return out
+
+
+def test_encrypt_decrypt_exact_error_polynomial():
+    """decrypt(encrypt(m)) = m + v*e_pk + e0 + e1*s exactly (integer ring identity)."""
+    prm = _params(log_n=5)
+    he = ckks.Ckks(prm)
+    he.keygen(7)
+    rng = np.random.default_rng(1)
+    m = rng.integers(-(1 << 45), 1 << 45, size=prm.n)
+    nonce = 3
+    ct = he.encrypt_coeffs(m, prm.top, nonce)
+    got = he.decrypt_coeffs(ct)
+    n = prm.n
+    v = ckks.sample_ternary(ckks.stream_key(7, ckks.P_ENC_V, nonce), n).tolist()
+    e0 = ckks.sample_gaussian(ckks.stream_key(7, ckks.P_ENC_E0, nonce), n, 3.2).tolist()
+    e1 = ckks.sample_gaussian(ckks.stream_key(7, ckks.P_ENC_E1, nonce), n, 3.2).tolist()
+    epk = ckks.sample_gaussian(ckks.stream_key(7, ckks.P_PK_E), n, 3.2).tolist()
+    s = he.s.tolist()
+    ve = _int_negacyclic(v, epk)
+    e1s = _int_negacyclic(e1, s)
+    want = [int(m[j]) + ve[j] + e0[j] + e1s[j] for j in range(n)]
+    assert got == want
+
+
+def test_decrypt_slots_and_add_sub():
+    prm = _params(log_n=7)
+    he = ckks.Ckks(prm)
+    he.keygen(11)
+    rng = np.random.default_rng(2)
+    x, y = rng.normal(size=prm.slots), rng.normal(size=prm.slots)
+    cx, cy = he.encrypt(x, prm.top, 1), he.encrypt(y, prm.top, 2)
+    assert np.abs(he.decrypt(cx) - x).max() < 1e-6
+    assert np.abs(he.decrypt(he.add(cx, cy)) - (x + y)).max() < 1e-6
+    assert np.abs(he.decrypt(he.sub(cx, cy)) - (x - y)).max() < 1e-6
+
+
+def test_tensor_decrypts_to_product_exactly():
+    """(d0 + d1 s + d2 s^2) = (a0 + a1 s)(b0 + b1 s) in R_Q: the tensor is the ring product."""
+    prm = _params(log_n=5)
+    he = ckks.Ckks(prm)
+    he.keygen(5)
+    rng = np.random.default_rng(3)
+    a = he.encrypt(rng.normal(size=prm.slots), prm.top, 1)
+    b = he.encrypt(rng.normal(size=prm.slots), prm.top, 2)
+    t = he.tensor(a, b)
+    for i, q in enumerate(prm.q):
+        s = ckks.to_rns(he.s, [q])[0]
+        s2 = ring.polymul(s, s, q)
+        lhs = (t.c[0][i].astype(object) + ring.polymul(t.c[1][i], s, q).astype(object)
+               + ring.polymul(t.c[2][i], s2, q).astype(object)) % q
+        pa = (a.c[0][i].astype(object) + ring.polymul(a.c[1][i], s, q).astype(object)) % q
+        pb = (b.c[0][i].astype(object) + ring.polymul(b.c[1][i], s, q).astype(object)) % q
+        rhs = ring.polymul(np.array(pa, dtype=np.uint64), np.array(pb, dtype=np.uint64), q)
+        assert [int(x) for x in lhs] == [int(x) for x in rhs]
+
+
+def test_relinearize_and_rescale():
+    prm = _params(log_n=8)
+    he = ckks.Ckks(prm)
+    he.keygen(13)
+    rng = np.random.default_rng(4)
+    x, y = rng.normal(size=prm.slots), rng.normal(size=prm.slots)
+    cx, cy = he.encrypt(x, prm.top, 1), he.encrypt(y, prm.top, 2)
+    r = he.mul_relin_rescale(cx, cy)
+    assert r.level == prm.top - 1
+    assert np.abs(he.decrypt(r) - x * y).max() < 1e-5
+
+
+def test_keyswitch_multi_digit_alpha2():
+    prm = ckks.Params(7, (50,) * 5, (60, 60), 50)
+    he = ckks.Ckks(prm)
+    he.keygen(17, [3])
+    rng = np.random.default_rng(5)
+    x, y = rng.normal(size=prm.slots), rng.normal(size=prm.slots)
+    cx, cy = he.encrypt(x, prm.top, 1), he.encrypt(y, prm.top, 2)
+    for lv in (prm.top, 2, 1):
+        a, b = he.drop(cx, lv), he.drop(cy, lv)
+        r = he.mul_relin_rescale(a, b)
+        assert np.abs(he.decrypt(r) - x * y).max() < 1e-6
+        assert np.abs(he.decrypt(he.rotate(a, 3)) - np.roll(x, -3)).max() < 1e-6
+
+
+def test_rotation_identities():
+    prm = _params(log_n=7)
+    he = ckks.Ckks(prm)
+    he.keygen(19, [1, 2, -1, 5])
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=prm.slots)
+    cx = he.encrypt(x, prm.top, 1)
+    for r in (1, 2, -1, 5):
+        assert np.abs(he.decrypt(he.rotate(cx, r)) - np.roll(x, -r)).max() < 1e-6
+    # rotation by the slot count is the identity (5 has order N/2 modulo 2N)
+    assert prm.galois(prm.slots) == 1
+    # rot(rot(x, 1), 1) = rot(x, 2)
+    assert np.abs(he.decrypt(he.rotate(he.rotate(cx, 1), 1)) - np.roll(x, -2)).max() < 1e-6
+
+
+def test_rotation_key_switches_from_rotated_secret():
+    """decrypt under phi_g(s) of (phi_g(c0), phi_g(c1)) equals phi_g applied to the plaintext."""
+    prm = _params(log_n=5)
+    he = ckks.Ckks(prm)
+    he.keygen(23, [1])
+    g = prm.galois(1)
+    rng = np.random.default_rng(7)
+    cx = he.encrypt(rng.normal(size=prm.slots), prm.top, 1)
+    q = prm.q[0]
+    s = ckks.to_rns(he.s, [q])[0]
+    m = (cx.c[0][0].astype(object) + ring.polymul(cx.c[1][0], s, q).astype(object)) % q
+    m_g = ring.automorphism(np.array(m, dtype=np.uint64), g, q)
+    c0g = ring.automorphism(cx.c[0][0], g, q)
+    c1g = ring.automorphism(cx.c[1][0], g, q)
+    s_g = ring.automorphism(s, g, q)
+    lhs = (c0g.astype(object) + ring.polymul(c1g, s_g, q).astype(object)) % q
+    assert [int(v) for v in lhs] == [int(v) for v in m_g]

@@ -1,0 +1,140 @@
+"""Pins of the oracle MF: the paper's batch-pair example, FP64 update algebra, plan, encrypted epoch."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ckks, mf
+from paper_2509_03024_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_batch_pair_example_from_paper():
+    g = json.load(open(os.path.join(GOLD, "batch_pairs.json")))
+    rows = [r for r, _ in g["ratings"]]
+    cols = [c for _, c in g["ratings"]]
+    pairs = mf.batch_pairs(rows, cols, g["batch_size"])
+    counts = {f"{b},{c}": len(v) for (b, c), v in pairs.items()}
+    assert counts == g["pair_counts"]
+    local0 = [i % g["batch_size"] for i, _ in pairs[(0, 0)]].count(0)
+    assert local0 == g["user_local_0_count_in_pair_0_0"]
+
+
+def test_plan_groups_partition_ratings():
+    csr, _, _ = W.tiny_workload(3)
+    rows, cols, vals = csr.triples()
+    for slots in (512, 4096):
+        plan = mf.build_plan(csr.n, csr.m, 4, rows, cols, vals, slots)
+        seen = set()
+        for g in plan.groups:
+            assert len(set(g.a.tolist())) == len(g.a)  # one rating per block per group
+            for a in g.a.tolist():
+                i = g.b * plan.B + a
+                j = g.c * plan.B + (a + g.delta) % plan.B
+                assert (i, j) not in seen
+                seen.add((i, j))
+        assert seen == set(zip(rows.tolist(), cols.tolist()))
+        assert len(plan.groups) <= plan.n_ub * plan.n_vb * plan.B
+        # the groups refine the paper's batch pairs
+        pairs = mf.batch_pairs(rows, cols, plan.B)
+        for (b, c), lst in pairs.items():
+            assert sum(len(g.a) for g in plan.groups if g.b == b and g.c == c) == len(lst)
+        for c, nodes in enumerate(plan.closure):
+            for d in nodes:
+                assert d == 0 or (d - (1 << mf.highest_bit(d))) in nodes
+
+
+def test_fp64_epoch_hand_checked_2x2():
+    U = np.array([[1.0, 0.0], [0.0, 1.0]])
+    V = np.array([[1.0, 1.0], [2.0, 0.0]])
+    rows, cols, vals = [0, 0, 1], [0, 1, 0], [3.0, 1.0, 2.0]
+    lr, lam = 0.1, 0.5
+    # e00 = 3 - 1 = 2; e01 = 1 - 2 = -1; e10 = 2 - 1 = 1
+    # u0 <- u0 (1 - .1*.5*2) + .1 (2 v0 - 1 v1) = (0.9, 0) + .1 (0, 2) = (0.9, 0.2)
+    # u1 <- u1 (1 - .05) + .1 (1 v0) = (0, .95) + (.1, .1) = (0.1, 1.05)
+    # v0 <- v0 (1 - .1) + .1 (2 u0 + 1 u1) = (.9, .9) + (.2, .1) = (1.1, 1.0)
+    # v1 <- v1 (1 - .05) + .1 (-1 u0) = (1.9, 0) + (-.1, 0) = (1.8, 0)
+    U2, V2 = mf.mf_epoch_fp64(U, V, rows, cols, vals, lr, lam)
+    assert np.allclose(U2, [[0.9, 0.2], [0.1, 1.05]], atol=1e-15)
+    assert np.allclose(V2, [[1.1, 1.0], [1.8, 0.0]], atol=1e-15)
+    # RMSE, Eq. 10
+    assert abs(mf.rmse(U, V, rows, cols, vals) - np.sqrt((4 + 1 + 1) / 3)) < 1e-15
+
+
+def test_fp64_epoch_equals_per_rating_accumulation():
+    """Alg. 2 with the accumulators applied once: the sum of per-rating Alg. 1 gradients."""
+    rng = np.random.default_rng(0)
+    n, m, k = 7, 5, 3
+    U, V = rng.normal(size=(n, k)), rng.normal(size=(m, k))
+    pairs = [(i, j) for i in range(n) for j in range(m) if rng.random() < 0.5]
+    rows = [p[0] for p in pairs]; cols = [p[1] for p in pairs]
+    vals = rng.integers(1, 6, size=len(pairs)).astype(float)
+    lr, lam = 0.05, 0.1
+    accU, accV = np.zeros_like(U), np.zeros_like(V)
+    for (i, j), r in zip(pairs, vals):
+        e = r - U[i] @ V[j]
+        accU[i] += lr * (e * V[j] - lam * U[i])
+        accV[j] += lr * (e * U[i] - lam * V[j])
+    U2, V2 = mf.mf_epoch_fp64(U, V, rows, cols, vals, lr, lam)
+    assert np.allclose(U2, U + accU, atol=1e-12) and np.allclose(V2, V + accV, atol=1e-12)
+
+
+@pytest.mark.parametrize("slots,k", [(512, 4), (4096, 4), (512, 3), (1024, 10), (256, 1)])
+def test_simulated_plan_equals_fp64(slots, k):
+    rng = np.random.default_rng(slots + k)
+    csr = W.uniform_ratings(150, 110, 0.05, slots)
+    rows, cols, vals = csr.triples()
+    U, V = rng.normal(0, 0.1, (csr.n, k)), rng.normal(0, 0.1, (csr.m, k))
+    plan = mf.build_plan(csr.n, csr.m, k, rows, cols, vals, slots)
+    Us, Vs = mf.simulate_epoch_slots(U, V, plan, 0.01, 0.02)
+    U1, V1 = mf.mf_epoch_fp64(U, V, rows, cols, vals, 0.01, 0.02)
+    assert np.abs(Us - U1).max() < 1e-12 and np.abs(Vs - V1).max() < 1e-12
+
+
+def _small_he(log_n=9, data=(60, 40, 40), special=(60,), ls=40, seed=5, steps=()):
+    he = ckks.Ckks(ckks.Params(log_n, data, special, ls))
+    he.keygen(seed, steps)
+    return he
+
+
+def test_encrypted_epoch_matches_fp64():
+    csr = W.uniform_ratings(40, 30, 0.08, 4)
+    rows, cols, vals = csr.triples()
+    rng = np.random.default_rng(1)
+    U, V = rng.normal(0, 0.1, (csr.n, 4)), rng.normal(0, 0.1, (csr.m, 4))
+    he = ckks.Ckks(ckks.Params(9, (60, 40, 40), (60,), 40))
+    plan = mf.build_plan(csr.n, csr.m, 4, rows, cols, vals, he.prm.slots)
+    he.keygen(5, plan.rotation_steps())
+    emf = mf.EncryptedMF(he, plan)
+    emf.encrypt_ratings()
+    UD, VD = emf.encrypt_factors(U, V)
+    U2, V2 = emf.epoch(UD, VD, 0.01, 0.02)
+    assert U2[0].level == he.prm.top - 2
+    Ud, Vd = emf.decrypt_factors(U2, V2)
+    U1, V1 = mf.mf_epoch_fp64(U, V, rows, cols, vals, 0.01, 0.02)
+    assert np.abs(Ud - U1).max() < 1e-3 and np.abs(Vd - V1).max() < 1e-3
+    # the reachable accuracy at 40-bit scale is far below the 1e-3 bar
+    assert np.abs(Ud - U1).max() < 1e-6
+
+
+def test_encrypted_epoch_group_order_independent():
+    """Modular accumulation is order-free: permuting the group order gives identical ciphertexts."""
+    csr = W.uniform_ratings(24, 20, 0.1, 6)
+    rows, cols, vals = csr.triples()
+    rng = np.random.default_rng(2)
+    U, V = rng.normal(0, 0.1, (csr.n, 2)), rng.normal(0, 0.1, (csr.m, 2))
+    he = ckks.Ckks(ckks.Params(7, (60, 40, 40), (60,), 40))
+    plan = mf.build_plan(csr.n, csr.m, 2, rows, cols, vals, he.prm.slots)
+    he.keygen(8, plan.rotation_steps())
+    emf = mf.EncryptedMF(he, plan)
+    emf.encrypt_ratings()
+    UD, VD = emf.encrypt_factors(U, V)
+    U2, V2 = emf.epoch(UD, VD, 0.01, 0.02)
+    perm = np.random.default_rng(3).permutation(len(plan.groups))
+    plan.groups = [plan.groups[t] for t in perm]
+    emf.R = [emf.R[t] for t in perm]
+    U3, V3 = emf.epoch(UD, VD, 0.01, 0.02)
+    for a, b in zip(U2 + V2, U3 + V3):
+        assert (a.c == b.c).all()
