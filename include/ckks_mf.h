@@ -1,0 +1,234 @@
+/*
+ * ckks_mf.h — C ABI of the GB300 RNS-CKKS library for encrypted CSR matrix
+ * factorisation (arXiv 2509.03024, "Efficient Privacy-Preserving
+ * Recommendation on Sparse Data using Fully Homomorphic Encryption").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Return value: FHE_OK (0) on success, a negative FHE_ERR_* code otherwise.
+ *   After a failure fhe_last_error(ctx) describes it, the call's outputs are
+ *   unspecified, and the context stays valid and usable.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream). Device work is enqueued on it in order; an entry point
+ *   that returns host data synchronises that stream first. One context must
+ *   not be used from two host threads or two streams at the same time: it owns
+ *   one set of scratch buffers.
+ * Ciphertext buffers ("ct"): caller-owned DEVICE memory of
+ *   fhe_ctx_info.ct_words uint64 words = [2][L+1][N] (component, limb,
+ *   coefficient), where L is the top level. A ciphertext at level l uses limbs
+ *   0..l of each component; the other limbs are ignored and may hold anything.
+ *   Limbs are stored in the evaluation (NTT) domain, residues in [0, q_i).
+ *   Arrays of ciphertexts are contiguous: ciphertext t starts at t*ct_words.
+ * Pointers: "host" pointers are ordinary CPU memory; "device" pointers are
+ *   CUDA global memory on the context's device. Neither is retained after the
+ *   call returns, except where a function says it stores a pointer.
+ *
+ * The scheme is leveled CKKS (Cheon-Kim-Kim-Song 2017), which the paper uses
+ * for its encrypted MF (Sec. II-A.2 Eq. 6-9, Sec. IV-A), in full-RNS form with
+ * hybrid key switching (Han-Ki 2020).
+ */
+#ifndef CKKS_MF_H
+#define CKKS_MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ errors */
+enum {
+    FHE_OK = 0,
+    FHE_ERR_INVALID_ARG = -1,     /* a pointer, size, level or parameter is out of range  */
+    FHE_ERR_LEVEL_EXHAUSTED = -2, /* the operation needs more limbs than the input has     */
+    FHE_ERR_SCALE_MISMATCH = -3,  /* reserved: operands at different scales                */
+    FHE_ERR_MISSING_KEY = -4,     /* keys not generated, or no key for a rotation step     */
+    FHE_ERR_OOM = -5,             /* device or host allocation failed                      */
+    FHE_ERR_DEVICE_TIMEOUT = -6,  /* a bounded device-side wait gave up                    */
+    FHE_ERR_CUDA = -7,            /* a CUDA runtime call failed                            */
+    FHE_ERR_STATE = -8            /* the object is not in a state that allows the call     */
+};
+
+typedef struct fhe_ctx fhe_ctx;
+typedef struct fhe_mf_plan fhe_mf_plan;
+
+/* ------------------------------------------------------------------ context */
+
+/* Scheme parameters (Sec. IV-A fixes N = 8192, 32 fractional bits, 128-bit
+ * security for the paper's runs; any power-of-two N in [2^9, 2^16] is accepted).
+ * Primes: for each entry of data_prime_bits, then of special_prime_bits, the
+ * largest prime below 2^bits that is 1 mod 2N and not chosen before.
+ * Bits must lie in [20, 61]. The scale is 2^log_scale. */
+typedef struct {
+    int32_t log_n;
+    int32_t n_data_primes;               /* L + 1                          */
+    const int32_t* data_prime_bits;      /* host, n_data_primes entries    */
+    int32_t n_special_primes;            /* alpha >= 1                     */
+    const int32_t* special_prime_bits;   /* host, n_special_primes entries */
+    int32_t log_scale;
+    double sigma;                        /* error standard deviation (3.2) */
+    int32_t device;                      /* CUDA device ordinal            */
+} fhe_params;
+
+typedef struct {
+    int32_t log_n, n, slots;             /* N and N/2                      */
+    int32_t top_level;                   /* L                              */
+    int32_t n_special;                   /* alpha                          */
+    int32_t log_scale;
+    size_t ct_words;                     /* uint64 words per ciphertext    */
+} fhe_ctx_info;
+
+/* Create a context: primes, NTT twiddles, RNS conversion constants and
+ * encoding tables, all resident on `device`. *out receives the handle. */
+int fhe_ctx_create(const fhe_params* params, fhe_ctx** out);
+void fhe_ctx_destroy(fhe_ctx* ctx);
+/* Human-readable description of the last error on ctx ("" if none). Valid until the next call. */
+const char* fhe_last_error(const fhe_ctx* ctx);
+int fhe_ctx_get_info(const fhe_ctx* ctx, fhe_ctx_info* out);
+/* Copy the L+1 data primes then the alpha special primes into host `out` (cap entries). */
+int fhe_ctx_get_primes(const fhe_ctx* ctx, uint64_t* out, size_t cap);
+
+/* Key generation (the CSP's role, Sec. III-B.1) from one 64-bit seed: the
+ * ternary secret s, the public key, the relinearisation key for s^2 and one
+ * rotation key per entry of rot_steps (host, left-rotation amounts; negative
+ * = right). All randomness is drawn from SplitMix64 streams keyed by
+ * (purpose, object, poly, limb) under this seed; the seed also keys later
+ * encryptions. Replaces any previous keys. */
+int fhe_keygen_from_seed(fhe_ctx* ctx, uint64_t seed, const int32_t* rot_steps, size_t n_steps);
+/* Add rotation keys for more steps to the current key set. */
+int fhe_add_rotation_keys(fhe_ctx* ctx, const int32_t* rot_steps, size_t n_steps);
+
+/* ------------------------------------------------------------------ encode / encrypt */
+
+/* Encode n_slots real values (host) into the integer coefficient vector
+ * round(Delta * m(X)) with m(zeta^(5^t)) = slots[t] (canonical embedding);
+ * coeffs_dev: device int64 [N]. Unlisted slots are 0. */
+int fhe_encode(fhe_ctx* ctx, const double* slots, size_t n_slots, int64_t* coeffs_dev, void* stream);
+
+/* Encrypt under the public key at `level`: ct = (v*pk0 + e0 + m, v*pk1 + e1).
+ * The randomness v, e0, e1 is drawn from the streams of `nonce`; the same
+ * (seed, nonce, message) always gives the same ciphertext.
+ * fhe_encrypt takes host slots (Eq. 6-9's FHE.Enc of an encoded vector);
+ * fhe_encrypt_coeffs takes a device int64 [N] coefficient message. ct: device. */
+int fhe_encrypt(fhe_ctx* ctx, const double* slots, size_t n_slots, int32_t level, uint64_t nonce,
+                uint64_t* ct, void* stream);
+int fhe_encrypt_coeffs(fhe_ctx* ctx, const int64_t* coeffs_dev, int32_t level, uint64_t nonce,
+                       uint64_t* ct, void* stream);
+
+/* Decrypt the first n_slots slots into host `slots` (FHE.Dec then decode at
+ * scale Delta). Uses limbs 0..min(level, 1). Synchronises `stream`. */
+int fhe_decrypt(fhe_ctx* ctx, const uint64_t* ct, int32_t level, double* slots, size_t n_slots,
+                void* stream);
+
+/* ------------------------------------------------------------------ ring and ciphertext primitives */
+
+/* In-place forward / inverse negacyclic NTT of `count` polynomials of
+ * `n_limbs` limbs each (device [count][n_limbs][N], limb i modulo data prime i). */
+int fhe_ntt_forward(fhe_ctx* ctx, uint64_t* polys, int32_t count, int32_t n_limbs, void* stream);
+int fhe_ntt_inverse(fhe_ctx* ctx, uint64_t* polys, int32_t count, int32_t n_limbs, void* stream);
+
+/* Convert `count` ciphertexts at `level` to coefficient form: out device
+ * [count][2][level+1][N] (compact). Used to compare ciphertexts exactly. */
+int fhe_ct_to_coeff(fhe_ctx* ctx, const uint64_t* ct, int32_t count, int32_t level, uint64_t* out,
+                    void* stream);
+
+/* Homomorphic addition / subtraction (Eq. 6): out = a +/- b at `level`, `count` ciphertexts. */
+int fhe_add(fhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, int32_t count,
+            int32_t level, void* stream);
+int fhe_sub(fhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, int32_t count,
+            int32_t level, void* stream);
+/* Ciphertext times plaintext (Eq. 9): pt_coeffs_dev is an int64 [N] encoded
+ * message (fhe_encode), applied to `count` ciphertexts. No rescale. */
+int fhe_mul_plain(fhe_ctx* ctx, const uint64_t* ct, const int64_t* pt_coeffs_dev, uint64_t* out,
+                  int32_t count, int32_t level, void* stream);
+/* Ciphertext product (Eq. 7): tensor, relinearise with the s^2 key, then
+ * rescale by q_level. Output at level-1. Needs level >= 1. */
+int fhe_mul_relin_rescale(fhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out,
+                          int32_t count, int32_t level, void* stream);
+/* Tensor only: out3 device [count][3][L+1][N] (three components, capacity limbs). */
+int fhe_tensor(fhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out3, int32_t count,
+               int32_t level, void* stream);
+/* Relinearise a three-component tensor (as from fhe_tensor) into a ciphertext. */
+int fhe_relinearize(fhe_ctx* ctx, const uint64_t* in3, uint64_t* out, int32_t count, int32_t level,
+                    void* stream);
+/* Exact rescale (divide-and-round by q_level): level -> level-1. out may equal ct. */
+int fhe_rescale(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, int32_t level,
+                void* stream);
+/* Left slot rotation by `step` (negative = right): automorphism X -> X^(5^step)
+ * then key switching with that step's rotation key. out must not alias ct. */
+int fhe_rotate(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, int32_t level,
+               int32_t step, void* stream);
+
+/* ------------------------------------------------------------------ encrypted CSR matrix factorisation */
+
+typedef struct {
+    int32_t n_users, n_items, k;         /* rating matrix n x m, rank k              */
+    int32_t kp, w, B;                    /* next_pow2(k), slot block 2*kp, B = N/2/w */
+    int32_t n_user_batches, n_item_batches;
+    int64_t n_ratings, n_groups;         /* M and the number of (b, c, delta) groups */
+    int64_t n_tree_nodes;                /* delta-tree nodes over all item batches   */
+    size_t device_bytes;                 /* device memory owned by the plan          */
+} fhe_mf_plan_info;
+
+/* The rotation amounts an MF epoch with rank k needs (keys must exist for all
+ * of them). Writes up to cap entries to host `out`; returns the count (>= 0)
+ * or an error code. */
+int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t cap);
+
+/* EncryptCsrMatrix + batch-pair grouping (Alg. 1, Alg. 2, Fig. 5).
+ * Input: the n x m rating matrix in CSR form (host: row_ptr[n+1] int64,
+ * col_idx[M] int32, vals[M] double; Sec. II-A.3), rank k. Users and items are
+ * cut into batches of B; a rating (i, j) joins group (i div B, j div B,
+ * (j mod B - i mod B) mod B). Each group's ratings are encrypted at the top
+ * level (nonce 2^40 + group index, groups in (b, c, delta) order) and kept on
+ * the device by the plan. Duplicate (i, j) pairs are rejected. */
+int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* row_ptr,
+                 const int32_t* col_idx, const double* vals, fhe_mf_plan** out);
+void fhe_mf_plan_destroy(fhe_mf_plan* plan);
+int fhe_mf_plan_get_info(const fhe_mf_plan* plan, fhe_mf_plan_info* out);
+/* Copy the plan's groups to host arrays of n_groups entries (any may be NULL):
+ * user batch b, item batch c, delta, and the number of ratings in the group. */
+int fhe_mf_plan_get_groups(const fhe_mf_plan* plan, int32_t* b, int32_t* c, int32_t* delta,
+                           int32_t* count);
+
+/* Tuning: process at most `groups_per_chunk` groups per launch set of the
+ * epoch (default: as many as fit a 6 GiB work area). Results do not depend on it. */
+int fhe_mf_plan_set_chunk(fhe_mf_plan* plan, int32_t groups_per_chunk);
+
+/* Encrypt factor rows (host double [count][k], users if which = 0, items if 1)
+ * into the plan's batch layout: n_user_batches (or n_item_batches)
+ * ciphertexts at the top level, entity a of a batch at slot block a, its
+ * k-vector written twice (slots a*w..a*w+k-1 and a*w+kp..a*w+kp+k-1).
+ * Nonces: 2^41 + batch (users), 2^41 + 2^40 + batch (items). cts: device. */
+int fhe_mf_encrypt_factors(fhe_ctx* ctx, const fhe_mf_plan* plan, int32_t which, const double* X,
+                           int32_t count, uint64_t* cts, void* stream);
+/* Decrypt batch ciphertexts at `level` back to host double [count][k]. */
+int fhe_mf_decrypt_factors(fhe_ctx* ctx, const fhe_mf_plan* plan, int32_t which,
+                           const uint64_t* cts, int32_t level, double* X, int32_t count,
+                           void* stream);
+
+/* One encrypted SGD epoch (Alg. 1 error and gradient, Alg. 2 accumulators,
+ * applied once per epoch): for every rating e_ij = r_ij - <u_i, v_j> with the
+ * epoch-start factors, then
+ *   u_i <- u_i (1 - lr*lambda*nnz_i) + lr * sum_j e_ij v_j,
+ *   v_j <- v_j (1 - lr*lambda*nnz_j) + lr * sum_i e_ij u_i.
+ * U: device, n_user_batches ciphertexts; V: device, n_item_batches; both at
+ * `level` on entry and level-2 on return (updated in place).
+ * Needs level >= 2 (else FHE_ERR_LEVEL_EXHAUSTED) and every key of
+ * fhe_mf_rotation_steps (else FHE_ERR_MISSING_KEY). */
+int fhe_mf_sgd_epoch(fhe_ctx* ctx, fhe_mf_plan* plan, uint64_t* U, uint64_t* V, int32_t level,
+                     double lr, double lambda, void* stream);
+
+/* Encrypted predicted ratings of one user against every item (a row of
+ * R-hat = U V^T, Alg. 1): out receives n_item_batches ciphertexts at level-2;
+ * slot d*w of ciphertext c holds <u_user, v_(c*B+d)>. Needs rotation keys
+ * for 2^t * w (t < log2 B) and 2^t (t < log2 kp). */
+int fhe_predict(fhe_ctx* ctx, const fhe_mf_plan* plan, const uint64_t* U, const uint64_t* V,
+                int32_t level, int32_t user, uint64_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKKS_MF_H */

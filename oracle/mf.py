@@ -351,3 +351,24 @@ class EncryptedMF:
             base = he.drop(he.rescale(he.mul_plain(VD[c], reg)), out_lv)
             newV.append(he.add(base, acc))
         return newU, newV
+
+    def predict(self, UD: Sequence[Ciphertext], VD: Sequence[Ciphertext], user: int) -> List[Ciphertext]:
+        """Encrypted row `user` of R-hat = U V^T (Alg. 1): slot d*w of output c holds <u_user, v_(cB+d)>.
+
+        The user's block is isolated by a 0/1 mask, copied into every block by
+        log2(B) rotate-and-adds, multiplied with each item batch and summed over
+        the kp slots of each block."""
+        he, p = self.he, self.plan
+        b, a = divmod(user, p.B)
+        mask = np.zeros(p.B * p.w)
+        mask[a * p.w: a * p.w + p.k] = 1.0
+        X = he.rescale(he.mul_plain(UD[b], he.enc.encode(mask)))
+        for t in range(highest_bit(p.B)):
+            X = he.add(X, he.rotate(X, (1 << t) * p.w))
+        out = []
+        for c in range(p.n_vb):
+            P = he.rescale(he.relinearize(he.tensor(X, VD[c])))
+            for t in range(highest_bit(p.kp)):
+                P = he.add(P, he.rotate(P, 1 << t))
+            out.append(P)
+        return out

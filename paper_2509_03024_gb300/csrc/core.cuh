@@ -1,0 +1,321 @@
+// core.cuh — shared definitions of the GB300 RNS-CKKS library: exact 64-bit
+// modular arithmetic, the context object, device-buffer helpers and launch
+// declarations of the kernels in ntt.cu / ops.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <exception>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ckks_mf.h"
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef uint32_t u32;
+typedef unsigned __int128 u128;
+
+namespace fhe {
+
+// ----------------------------------------------------------------------------- errors
+
+struct FheException : std::exception {
+    int code;
+    std::string msg;
+    FheException(int c, std::string m) : code(c), msg(std::move(m)) {}
+    const char* what() const noexcept override { return msg.c_str(); }
+};
+
+// Throwing is used inside the library; every extern "C" entry point catches
+// and converts to an FHE_ERR_* code plus fhe_last_error text.
+[[noreturn]] void fail(int code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define CK(x) ::fhe::cuda_check((x), #x)
+
+// ----------------------------------------------------------------------------- modular arithmetic
+
+// One RNS prime with its Barrett constant (HAC Alg. 14.42, base 2):
+// mu = floor(2^(2b) / q), b = bit length of q, q < 2^62.
+struct Prime {
+    u64 q;
+    u64 mu;
+    u32 b;
+    u32 pad;
+};
+
+__host__ __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+__host__ __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) {
+    return a >= b ? a - b : a + (q - b);
+}
+
+#ifdef __CUDACC__
+// Barrett reduction of the 128-bit product a*b (a, b < q): q1 = x >> (b-1),
+// q3 = (q1 * mu) >> (b+1), r = x - q3*q in [0, 3q), two conditional subtractions.
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const Prime& p) {
+    u64 lo = a * b;
+    u64 hi = __umul64hi(a, b);
+    u64 q1 = (lo >> (p.b - 1)) | (hi << (65 - p.b));
+    u64 t_lo = q1 * p.mu;
+    u64 t_hi = __umul64hi(q1, p.mu);
+    u64 q3 = (t_lo >> (p.b + 1)) | (t_hi << (63 - p.b));
+    u64 r = lo - q3 * p.q;
+    if (r >= p.q) r -= p.q;
+    if (r >= p.q) r -= p.q;
+    return r;
+}
+// Shoup multiplication by a constant w < q with ws = floor(w * 2^64 / q); a < 2^64.
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 ws, u64 q) {
+    u64 qh = __umul64hi(a, ws);
+    u64 r = a * w - qh * q;
+    return r >= q ? r - q : r;
+}
+#endif
+
+// Host versions (exact, u128).
+inline u64 h_mul(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
+inline u64 h_pow(u64 a, u64 e, u64 q) {
+    u64 r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = h_mul(r, a, q);
+        a = h_mul(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+inline u64 h_inv(u64 a, u64 q) { return h_pow(a, q - 2, q); }
+inline u64 h_shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+// ----------------------------------------------------------------------------- poly batches
+
+// A regular batch of RNS polynomials in device memory. Row r of the batch is
+// (item, part, limb) with r = (item * n_parts + part) * n_limbs + (limb - limb_lo);
+// its N coefficients start at base + item*item_stride + part*part_stride +
+// (limb - addr_lo)*N. The prime of limb t is t, plus `jump` when t >= split
+// (an extended basis Q_l u P stored as limbs 0..l then the alpha special limbs).
+struct PolyBatch {
+    u64* base;
+    size_t item_stride;
+    size_t part_stride;
+    int n_items;
+    int n_parts;
+    int limb_lo;
+    int n_limbs;
+    int split;
+    int jump;
+    int addr_lo;
+    __host__ __device__ __forceinline__ int rows() const { return n_items * n_parts * n_limbs; }
+    __host__ __device__ __forceinline__ int prime_of(int limb) const {
+        return limb + (limb >= split ? jump : 0);
+    }
+};
+
+// Batch of `items` polynomials with `parts` components, limbs [lo, lo+cnt), all data primes,
+// stored at limb offsets relative to addr_lo.
+inline PolyBatch poly_batch(u64* base, size_t item_stride, size_t part_stride, int items, int parts,
+                            int lo, int cnt, int addr_lo = 0) {
+    PolyBatch pb;
+    pb.base = base;
+    pb.item_stride = item_stride;
+    pb.part_stride = part_stride;
+    pb.n_items = items;
+    pb.n_parts = parts;
+    pb.limb_lo = lo;
+    pb.n_limbs = cnt;
+    pb.split = 1 << 30;
+    pb.jump = 0;
+    pb.addr_lo = addr_lo;
+    return pb;
+}
+
+// ----------------------------------------------------------------------------- keys
+
+// Hybrid key-switching key: [dnum_top][2 (b, a)][n_ext][N], evaluation domain.
+struct EvalKey {
+    u64* d = nullptr;
+    int galois = 0;  // 0 for the relinearisation key
+};
+
+// ----------------------------------------------------------------------------- descriptor arena
+
+// Pinned host staging + device memory for per-launch descriptor tables
+// (pointer arrays). push() copies a table into pinned memory and enqueues its
+// upload on the stream; the returned device address is valid until reset().
+// reset() synchronises the stream first, so earlier uploads have completed.
+struct Arena {
+    struct Block {
+        char* host = nullptr;
+        char* dev = nullptr;
+        size_t cap = 0, used = 0;
+    };
+    std::vector<Block> blocks;
+    size_t cur = 0;
+    void reset(cudaStream_t s);
+    void* push(const void* data, size_t bytes, cudaStream_t s);
+    template <typename T>
+    T* push_vec(const std::vector<T>& v, cudaStream_t s) {
+        return (T*)push(v.data(), v.size() * sizeof(T), s);
+    }
+    ~Arena();
+};
+
+// ----------------------------------------------------------------------------- context
+
+struct DeviceBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Ctx {
+    int device = 0;
+    int log_n = 0, n = 0, slots = 0;
+    int L = 0;       // top level
+    int alpha = 0;   // special primes
+    int n_ext = 0;   // L + 1 + alpha
+    int log_scale = 0;
+    double sigma = 3.2;
+    std::vector<u64> primes;  // data q_0..q_L then special p_0..p_{alpha-1}
+    std::vector<Prime> hprimes;
+
+    // device tables
+    Prime* d_primes = nullptr;        // [n_ext]
+    u64* d_psi = nullptr;             // [n_ext][N]  psi^brev(i)   (forward twiddles)
+    u64* d_psi_s = nullptr;           // Shoup companions
+    u64* d_ipsi = nullptr;            // [n_ext][N]  psi^-brev(i)  (inverse twiddles)
+    u64* d_ipsi_s = nullptr;
+    u64* d_ninv = nullptr;            // [n_ext][2] N^-1 and its Shoup companion
+    u64* d_resc = nullptr;            // [L+1][L+1][2] q_l^-1 mod q_i (+ Shoup)
+    u64* d_up_inv = nullptr;          // [L+1][L+1][2] digit-local qhat_i^-1 mod q_i at level l
+    u64* d_up_hat = nullptr;          // [L+1][L+1][n_ext][2] digit-local qhat_i mod prime t at level l
+    u64* d_down_inv = nullptr;        // [alpha][2]   Phat_k^-1 mod p_k
+    u64* d_down_hat = nullptr;        // [alpha][L+1][2] Phat_k mod q_i
+    u64* d_pinv = nullptr;            // [L+1][2]     P^-1 mod q_i
+    u64* d_pmod = nullptr;            // [L+1]        P mod q_i
+    double* d_cos = nullptr;          // [2N] cos(pi e / N)
+    double* d_sin = nullptr;          // [2N] sin(pi e / N)
+    u32* d_pow5 = nullptr;            // [N/2] 5^t mod 2N
+
+    // keys
+    bool have_keys = false;
+    u64 seed = 0;
+    u64* d_sk = nullptr;              // [n_ext][N] evaluation domain
+    u64* d_pk = nullptr;              // [2][L+1][N]
+    EvalKey rlk;
+    std::map<int, EvalKey> rot;       // galois element -> key
+
+    // scratch (grow-only), keyed by purpose
+    std::map<std::string, DeviceBuf> scratch;
+    u64* scratch_u64(const std::string& name, size_t words);
+    void* scratch_bytes(const std::string& name, size_t bytes);
+
+    std::string last_error;
+    Arena arena;
+
+    size_t ct_words() const { return (size_t)2 * (L + 1) * n; }
+    size_t key_words() const { return (size_t)dnum(L) * 2 * n_ext * n; }
+    int dnum(int level) const { return (level + 1 + alpha - 1) / alpha; }
+    int galois(int step) const {
+        long long r = ((long long)step % slots + slots) % slots;
+        return (int)h_pow(5, (u64)r, (u64)2 * n);
+    }
+    ~Ctx();
+};
+
+// ----------------------------------------------------------------------------- kernels (ntt.cu)
+
+// Kernel attributes (dynamic shared memory limits); called once per device.
+void ntt_init();
+// In-place negacyclic NTT / inverse NTT of every row of the batch.
+void ntt_forward(const Ctx& c, const PolyBatch& pb, cudaStream_t s);
+void ntt_inverse(const Ctx& c, const PolyBatch& pb, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- item kernels (ops.cu)
+
+// Every ciphertext-like pointer addresses the start of an object in capacity
+// layout: component p, limb i at ptr + p*(L+1)*N + i*N.
+struct BinItem {
+    const u64* a;
+    const u64* b;
+    u64* out;
+};
+struct UnItem {
+    const u64* in;
+    u64* out;
+};
+// One target accumulator and its contributors [off, off + cnt) in a BinItem list
+// (a = left operand, b = right operand; out unused).
+struct AccTarget {
+    u64* out;
+    int off;
+    int cnt;
+};
+
+// out = a +/- b for `parts` components and `limbs` limbs
+void items_add(Ctx& c, const std::vector<BinItem>& it, int parts, int limbs, bool sub, cudaStream_t s);
+void items_copy(Ctx& c, const std::vector<UnItem>& it, int parts, int limbs, cudaStream_t s);
+// out = a (.) b where b is a one-component plaintext (evaluation domain)
+void items_mul_plain(Ctx& c, const std::vector<BinItem>& it, int parts, int limbs, cudaStream_t s);
+// out (3 components) = a (x) b
+void items_tensor(Ctx& c, const std::vector<BinItem>& it, int limbs, cudaStream_t s);
+// target.out (3 components) += sum over contributors of a (x) b
+void items_tensor_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<BinItem>& contrib,
+                      int limbs, cudaStream_t s);
+// target.out (`parts` components) += sum over contributors of a (b unused)
+void items_sum_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<BinItem>& contrib,
+                   int parts, int limbs, cudaStream_t s);
+// rescale components [0, parts) from level l to l-1 (out may alias in)
+void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s);
+
+// signed int64 coefficients -> residues for limbs [0, limbs): out [items][L+1][N] (limb stride N)
+void k_int_to_rns(const Ctx& c, u64* out, size_t out_item_stride, const i64* in, size_t in_stride,
+                  int items, int limbs, cudaStream_t s);
+void k_int8_to_rns(const Ctx& c, u64* out, size_t out_item_stride, const int8_t* in, size_t in_stride,
+                   int items, int limbs, int prime_split, int prime_jump, cudaStream_t s);
+// evaluation-domain automorphism of one [limbs][N] polynomial: out[k] = in[perm_g(k)]
+void k_automorphism_poly(const Ctx& c, u64* out, const u64* in, int limbs, int galois, cudaStream_t s);
+
+// Hybrid key switch, one polynomial per item:
+//   out0 = KS0(d) + addP0[perm] + addI0,  out1 = KS1(d) + addI1
+// d and addP0 are read through perm_galois (galois = 1: identity); the add
+// terms are optional (null). Outputs must not alias d or addP0.
+struct KsItem {
+    const u64* d;
+    const u64* key;
+    const u64* addP0;
+    const u64* addI0;
+    const u64* addI1;
+    u64* out0;
+    u64* out1;
+    long long galois;
+};
+void keyswitch_items(Ctx& c, const std::vector<KsItem>& it, int level, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- ctx helpers (ctx.cu)
+
+const EvalKey& rotation_key(const Ctx& c, int step);
+void encode_device(Ctx& c, const double* host_slots, size_t n_slots, i64* out_dev, cudaStream_t s);
+void encode_sparse_device(Ctx& c, const std::vector<std::pair<int, double>>& nz, i64* out_dev,
+                          cudaStream_t s);
+// Encode many sparse slot vectors at once: nz lists concatenated with offsets (host), out [count][N].
+void encode_many_device(Ctx& c, const std::vector<int>& idx, const std::vector<double>& val,
+                        const std::vector<int>& offsets, i64* out_dev, cudaStream_t s);
+void encrypt_coeffs_device(Ctx& c, const i64* m_dev, size_t m_stride, int count, int level,
+                           const std::vector<u64>& nonces, u64* ct, cudaStream_t s);
+// plaintext materialisation: int64 coefficients -> evaluation domain limbs [0, limbs)
+void materialize_plain(Ctx& c, const i64* m_dev, size_t m_stride, int count, int limbs, u64* out,
+                       size_t out_stride, cudaStream_t s);
+void decrypt_to_slots(Ctx& c, const u64* ct, int level, double* host_slots, size_t n_slots,
+                      cudaStream_t s);
+
+}  // namespace fhe
+
+struct fhe_ctx {
+    fhe::Ctx c;
+};

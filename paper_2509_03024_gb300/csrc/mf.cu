@@ -1,0 +1,764 @@
+// mf.cu — encrypted CSR matrix factorisation on RNS-CKKS (arXiv 2509.03024,
+// Alg. 1 and Alg. 2): CSR packing into batch-pair groups, the encrypted SGD
+// epoch, factor encryption / decryption and the encrypted prediction row.
+//
+// Layout. Users and items are cut into batches of B = (N/2) / w entities,
+// w = 2 kp, kp = next_pow2(k). Entity a of a batch owns slots [a w, a w + w)
+// and holds its k-vector twice (at a w and at a w + kp), so that a
+// rotate-and-sum over kp slots leaves the full inner product in the first kp
+// slots of every block. A rating (i, j) with a = i mod B, b = i div B,
+// d = j mod B, c = j div B belongs to group (b, c, delta = (d - a) mod B): the
+// paper's batch pair (b, c) of Alg. 2 / Fig. 5, split by diagonal so that one
+// rotation of item batch c by delta*w lines up all of the group's pairs.
+//
+// Epoch at level l (two levels per epoch, the accumulators of Alg. 2 applied
+// once per epoch):
+//   Vr[c][delta] = rot(Vr[c][parent], 2^hb(delta) w)  (delta tree, parent = delta - 2^hb)
+//   per group: P = rescale(relin(UD_b (x) Vr)); S = rotsum_kp(P); E = R_g - S;
+//              M = rescale(Vr (.) mask_g); MU = rescale(UD_b (.) mask_g);
+//              TU_b += E (x) M;  TV[c][delta] += E (x) MU
+//   AccU_b = rescale(relin(TU_b)); G[c][delta] = rescale(relin(TV[c][delta]))
+//   AccV_c = sum_delta rot(G[c][delta], -delta w) along the same tree (children first)
+//   U_b <- drop(rescale(UD_b (.) reg_b)) + AccU_b + rot(AccU_b, -kp)   (items alike)
+// mask_g holds the learning rate on the first k slots of each rated block;
+// reg holds 1 - lr * lambda * nnz on every slot of an entity's block.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "core.cuh"
+
+using namespace fhe;
+
+namespace {
+
+constexpr u64 kRNonce = (u64)1 << 40;
+constexpr u64 kUNonce = (u64)1 << 41;
+constexpr u64 kVNonce = ((u64)1 << 41) + ((u64)1 << 40);
+
+int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+int hbit(int x) { return 31 - __builtin_clz((unsigned)x); }
+int popc(int x) { return __builtin_popcount((unsigned)x); }
+
+struct Group {
+    int b, c, delta;
+    std::vector<int> a;
+    std::vector<double> r;
+};
+
+}  // namespace
+
+struct fhe_mf_plan {
+    Ctx* c = nullptr;
+    int n = 0, m = 0, k = 0, kp = 0, w = 0, B = 0, n_ub = 0, n_vb = 0, beta = 0, log_kp = 0;
+    long long M = 0;
+    std::vector<Group> groups;
+    std::vector<std::vector<int>> closure;  // per item batch: sorted delta-tree nodes
+    std::vector<int> node_c, node_delta;    // global node list
+    std::vector<int> node_of;               // [n_vb * B] -> node id or -1
+    std::vector<int> group_node;            // node of each group
+    std::vector<int> nnz_u, nnz_v;
+    u64* d_R = nullptr;                     // [G] rating ciphertexts, top level
+    // plaintext caches (learning-rate dependent)
+    bool have_plain = false;
+    double lr_c = 0, lam_c = 0;
+    i64* d_mask = nullptr;                  // [G][N]
+    i64* d_reg = nullptr;                   // [n_ub + n_vb][N]
+    // epoch workspace
+    u64* d_Vr = nullptr;                    // [nodes] ciphertexts
+    u64* d_TV = nullptr;                    // [nodes] 3-component
+    u64* d_TU = nullptr;                    // [n_ub] 3-component
+    u64* d_H = nullptr;                     // [nodes]
+    u64* d_chunk = nullptr;                 // chunk buffers
+    u64* d_fin = nullptr;                   // [n_ub + n_vb] x 3 ciphertexts for the final step
+    int chunk = 0;        // groups per launch set
+    int chunk_alloc = 0;  // groups the chunk area was sized for
+    size_t bytes = 0;
+
+    int node(int cb, int delta) const { return node_of[(size_t)cb * B + delta]; }
+    ~fhe_mf_plan() {
+        void* bufs[] = {d_R, d_mask, d_reg, d_Vr, d_TV, d_TU, d_H, d_chunk, d_fin};
+        for (void* p : bufs)
+            if (p) cudaFree(p);
+    }
+};
+
+namespace {
+
+template <typename T>
+T* plan_alloc(fhe_mf_plan& p, size_t count) {
+    void* ptr = nullptr;
+    CK(cudaMalloc(&ptr, std::max<size_t>(count, 1) * sizeof(T)));
+    p.bytes += count * sizeof(T);
+    return (T*)ptr;
+}
+
+void ensure_plaintexts(fhe_mf_plan& p, double lr, double lam, cudaStream_t s) {
+    if (p.have_plain && p.lr_c == lr && p.lam_c == lam) return;
+    Ctx& c = *p.c;
+    const int G = (int)p.groups.size();
+    if (!p.d_mask) p.d_mask = plan_alloc<i64>(p, (size_t)std::max(G, 1) * c.n);
+    if (!p.d_reg) p.d_reg = plan_alloc<i64>(p, (size_t)(p.n_ub + p.n_vb) * c.n);
+    std::vector<int> idx, off{0};
+    std::vector<double> val;
+    const int enc_chunk = 4096;
+    for (int g0 = 0; g0 < G; g0 += enc_chunk) {
+        int g1 = std::min(G, g0 + enc_chunk);
+        idx.clear();
+        val.clear();
+        off.assign(1, 0);
+        for (int g = g0; g < g1; g++) {
+            if (lr != 0.0)
+                for (int a : p.groups[g].a)
+                    for (int x = 0; x < p.k; x++) {
+                        idx.push_back(a * p.w + x);
+                        val.push_back(lr);
+                    }
+            off.push_back((int)idx.size());
+        }
+        encode_many_device(c, idx, val, off, p.d_mask + (size_t)g0 * c.n, s);
+    }
+    idx.clear();
+    val.clear();
+    off.assign(1, 0);
+    for (int side = 0; side < 2; side++) {
+        const int nb = side ? p.n_vb : p.n_ub;
+        const std::vector<int>& nnz = side ? p.nnz_v : p.nnz_u;
+        for (int b = 0; b < nb; b++) {
+            for (int a = 0; a < p.B; a++) {
+                int e = b * p.B + a;
+                int cnt = e < (int)nnz.size() ? nnz[e] : 0;
+                double v = 1.0 - lr * lam * cnt;
+                if (v != 0.0)
+                    for (int x = 0; x < p.w; x++) {
+                        idx.push_back(a * p.w + x);
+                        val.push_back(v);
+                    }
+            }
+            off.push_back((int)idx.size());
+        }
+    }
+    encode_many_device(c, idx, val, off, p.d_reg, s);
+    p.have_plain = true;
+    p.lr_c = lr;
+    p.lam_c = lam;
+}
+
+void ensure_workspace(fhe_mf_plan& p) {
+    Ctx& c = *p.c;
+    const size_t w = c.ct_words(), lw = w / 2;
+    const size_t nodes = p.node_c.size();
+    if (!p.d_Vr) {
+        p.d_Vr = plan_alloc<u64>(p, nodes * w);
+        p.d_TV = plan_alloc<u64>(p, nodes * 3 * lw);
+        p.d_TU = plan_alloc<u64>(p, (size_t)p.n_ub * 3 * lw);
+        p.d_H = plan_alloc<u64>(p, nodes * w);
+        p.d_fin = plan_alloc<u64>(p, (size_t)(p.n_ub + p.n_vb) * 3 * w);
+    }
+    if (!p.d_chunk) {
+        // chunk: T3 (3 lw) + S, tmp, E, M, MU (2 lw each) + plaintext (lw) = 14 lw per group
+        const size_t per_group = 14 * lw * sizeof(u64);
+        const size_t budget = (size_t)6 << 30;
+        if (p.chunk <= 0)
+            p.chunk = (int)std::max<size_t>(1, std::min<size_t>(std::max<size_t>(p.groups.size(), 1),
+                                                                budget / per_group));
+        // the back-rotation and final steps reuse the chunk area
+        const int need = (int)((p.n_ub + p.n_vb + 13) / 14) + 1;
+        const int alloc_groups = std::max(p.chunk, need);
+        p.d_chunk = plan_alloc<u64>(p, (size_t)alloc_groups * 14 * lw);
+        p.chunk_alloc = alloc_groups;
+    }
+}
+
+void check_plan_keys(const fhe_mf_plan& p) {
+    Ctx& c = *p.c;
+    if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
+    for (int t = 0; t < p.log_kp; t++) rotation_key(c, 1 << t);
+    for (int t = 0; t < p.beta; t++) {
+        rotation_key(c, (1 << t) * p.w);
+        rotation_key(c, -(1 << t) * p.w);
+    }
+    rotation_key(c, -p.kp);
+}
+
+// Rotation of a list of ciphertexts (left by step_i): out_i = rot(in_i, step_i), optionally
+// plus in_i itself (rotate-and-add).
+void rotate_items(Ctx& c, const std::vector<const u64*>& in, const std::vector<u64*>& out,
+                  const std::vector<int>& steps, int level, bool add_self, cudaStream_t s) {
+    const size_t lw = c.ct_words() / 2;
+    std::vector<KsItem> ks;
+    for (size_t i = 0; i < in.size(); i++) {
+        int g = c.galois(steps[i]);
+        const EvalKey& key = rotation_key(c, steps[i]);
+        ks.push_back({in[i] + lw, key.d, in[i], add_self ? in[i] : nullptr, add_self ? in[i] + lw : nullptr, out[i],
+                      out[i] + lw, g});
+    }
+    keyswitch_items(c, ks, level, s);
+}
+
+// in-place relinearisation of 3-component objects (components 0,1 receive the result)
+void relin_inplace(Ctx& c, const std::vector<u64*>& t3, int level, cudaStream_t s) {
+    const size_t lw = c.ct_words() / 2;
+    std::vector<KsItem> ks;
+    for (u64* x : t3) ks.push_back({x + 2 * lw, c.rlk.d, nullptr, x, x + lw, x, x + lw, 1});
+    keyswitch_items(c, ks, level, s);
+}
+
+void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam, cudaStream_t s) {
+    Ctx& c = *p.c;
+    if (level < 2) fail(FHE_ERR_LEVEL_EXHAUSTED, "an epoch needs level >= 2");
+    if (level > c.L) fail(FHE_ERR_INVALID_ARG, "level out of range");
+    check_plan_keys(p);
+    c.arena.reset(s);
+    ensure_plaintexts(p, lr, lam, s);
+    ensure_workspace(p);
+    c.arena.reset(s);
+    const size_t w = c.ct_words(), lw = w / 2;
+    const int l0 = level, l1 = level - 1, l2 = level - 2;
+    const int nodes = (int)p.node_c.size();
+    CK(cudaMemsetAsync(p.d_TV, 0, sizeof(u64) * nodes * 3 * lw, s));
+    CK(cudaMemsetAsync(p.d_TU, 0, sizeof(u64) * p.n_ub * 3 * lw, s));
+    CK(cudaMemsetAsync(p.d_H, 0, sizeof(u64) * nodes * w, s));
+    auto Vr = [&](int nd) { return p.d_Vr + (size_t)nd * w; };
+    auto UD = [&](int b) { return U + (size_t)b * w; };
+    auto VD = [&](int cb) { return V + (size_t)cb * w; };
+
+    // 1. delta trees of the item batches, one launch set per popcount level
+    {
+        std::vector<UnItem> roots;
+        for (int cb = 0; cb < p.n_vb; cb++) roots.push_back({VD(cb), Vr(p.node(cb, 0))});
+        items_copy(c, roots, 2, l0 + 1, s);
+        int maxpop = 0;
+        for (int d : p.node_delta) maxpop = std::max(maxpop, popc(d));
+        for (int pc = 1; pc <= maxpop; pc++) {
+            std::vector<const u64*> in;
+            std::vector<u64*> out;
+            std::vector<int> steps;
+            for (int nd = 0; nd < nodes; nd++) {
+                int d = p.node_delta[nd];
+                if (popc(d) != pc) continue;
+                int hb = 1 << hbit(d);
+                in.push_back(Vr(p.node(p.node_c[nd], d - hb)));
+                out.push_back(Vr(nd));
+                steps.push_back(hb * p.w);
+            }
+            rotate_items(c, in, out, steps, l0, false, s);
+        }
+    }
+
+    // 2. groups, in chunks
+    const int G = (int)p.groups.size();
+    const int C = p.chunk;
+    u64* T3 = p.d_chunk;
+    u64* Sb = T3 + (size_t)C * 3 * lw;
+    u64* Tb = Sb + (size_t)C * w;
+    u64* Eb = Tb + (size_t)C * w;
+    u64* Mb = Eb + (size_t)C * w;
+    u64* MUb = Mb + (size_t)C * w;
+    u64* PTb = MUb + (size_t)C * w;
+    for (int g0 = 0; g0 < G; g0 += C) {
+        const int cnt = std::min(C, G - g0);
+        std::vector<BinItem> tens, pm;
+        std::vector<u64*> t3s;
+        std::vector<UnItem> resc_p;
+        for (int i = 0; i < cnt; i++) {
+            const Group& g = p.groups[g0 + i];
+            u64* t3 = T3 + (size_t)i * 3 * lw;
+            tens.push_back({UD(g.b), Vr(p.group_node[g0 + i]), t3});
+            t3s.push_back(t3);
+            resc_p.push_back({t3, Sb + (size_t)i * w});
+        }
+        items_tensor(c, tens, l0 + 1, s);
+        relin_inplace(c, t3s, l0, s);
+        items_rescale(c, resc_p, 2, l0, s);
+        // rotate-and-sum over kp slots
+        u64* cur = Sb;
+        u64* nxt = Tb;
+        for (int t = 0; t < p.log_kp; t++) {
+            std::vector<const u64*> in;
+            std::vector<u64*> out;
+            std::vector<int> steps(cnt, 1 << t);
+            for (int i = 0; i < cnt; i++) {
+                in.push_back(cur + (size_t)i * w);
+                out.push_back(nxt + (size_t)i * w);
+            }
+            rotate_items(c, in, out, steps, l1, true, s);
+            std::swap(cur, nxt);
+        }
+        // E = R - S
+        std::vector<BinItem> esub;
+        for (int i = 0; i < cnt; i++) esub.push_back({p.d_R + (size_t)(g0 + i) * w, cur + (size_t)i * w, Eb + (size_t)i * w});
+        items_add(c, esub, 2, l1 + 1, true, s);
+        // masks: M = rescale(Vr (.) mask), MU = rescale(UD (.) mask)
+        materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, cnt, l0 + 1, PTb, lw, s);
+        std::vector<UnItem> resc_m;
+        for (int i = 0; i < cnt; i++) {
+            const Group& g = p.groups[g0 + i];
+            const u64* pt = PTb + (size_t)i * lw;
+            pm.push_back({Vr(p.group_node[g0 + i]), pt, Mb + (size_t)i * w});
+            pm.push_back({UD(g.b), pt, MUb + (size_t)i * w});
+            resc_m.push_back({Mb + (size_t)i * w, Mb + (size_t)i * w});
+            resc_m.push_back({MUb + (size_t)i * w, MUb + (size_t)i * w});
+        }
+        items_mul_plain(c, pm, 2, l0 + 1, s);
+        items_rescale(c, resc_m, 2, l0, s);
+        // accumulate the tensors: TU_b += E (x) M, TV[node] += E (x) MU
+        std::map<int, std::vector<int>> by_b, by_node;
+        for (int i = 0; i < cnt; i++) {
+            by_b[p.groups[g0 + i].b].push_back(i);
+            by_node[p.group_node[g0 + i]].push_back(i);
+        }
+        std::vector<AccTarget> tg;
+        std::vector<BinItem> cb;
+        for (auto& kv : by_b) {
+            tg.push_back({p.d_TU + (size_t)kv.first * 3 * lw, (int)cb.size(), (int)kv.second.size()});
+            for (int i : kv.second) cb.push_back({Eb + (size_t)i * w, Mb + (size_t)i * w, nullptr});
+        }
+        for (auto& kv : by_node) {
+            tg.push_back({p.d_TV + (size_t)kv.first * 3 * lw, (int)cb.size(), (int)kv.second.size()});
+            for (int i : kv.second) cb.push_back({Eb + (size_t)i * w, MUb + (size_t)i * w, nullptr});
+        }
+        items_tensor_acc(c, tg, cb, l1 + 1, s);
+    }
+
+    // 3. relinearise and rescale the accumulators
+    u64* AccU = p.d_fin;                                   // [n_ub] ciphertexts
+    u64* FU = AccU + (size_t)p.n_ub * w;                   // [n_ub]
+    u64* BaseU = FU + (size_t)p.n_ub * w;                  // [n_ub]
+    u64* FV = BaseU + (size_t)p.n_ub * w;                  // [n_vb]
+    u64* BaseV = FV + (size_t)p.n_vb * w;                  // [n_vb]
+    {
+        std::vector<u64*> t3;
+        std::vector<UnItem> rs;
+        for (int b = 0; b < p.n_ub; b++) {
+            t3.push_back(p.d_TU + (size_t)b * 3 * lw);
+            rs.push_back({p.d_TU + (size_t)b * 3 * lw, AccU + (size_t)b * w});
+        }
+        std::vector<char> used(nodes, 0);
+        for (int nd : p.group_node) used[nd] = 1;
+        for (int nd = 0; nd < nodes; nd++)
+            if (used[nd]) {
+                t3.push_back(p.d_TV + (size_t)nd * 3 * lw);
+                rs.push_back({p.d_TV + (size_t)nd * 3 * lw, p.d_H + (size_t)nd * w});
+            }
+        relin_inplace(c, t3, l1, s);
+        items_rescale(c, rs, 2, l1, s);
+    }
+
+    // 4. back-rotation of the item gradients along the delta trees (deepest first)
+    {
+        int maxpop = 0;
+        for (int d : p.node_delta) maxpop = std::max(maxpop, popc(d));
+        u64* rot_buf = p.d_chunk;  // reuse the chunk area
+        const int cap = (int)((size_t)p.chunk_alloc * 14 * lw / w);
+        for (int pc = maxpop; pc >= 1; pc--) {
+            std::vector<int> lvl;
+            for (int nd = 0; nd < nodes; nd++)
+                if (popc(p.node_delta[nd]) == pc) lvl.push_back(nd);
+            for (size_t o = 0; o < lvl.size(); o += cap) {
+                size_t cnt = std::min(lvl.size() - o, (size_t)cap);
+                std::vector<const u64*> in;
+                std::vector<u64*> out;
+                std::vector<int> steps;
+                std::map<int, std::vector<int>> by_parent;
+                for (size_t i = 0; i < cnt; i++) {
+                    int nd = lvl[o + i];
+                    int d = p.node_delta[nd];
+                    int hb = 1 << hbit(d);
+                    in.push_back(p.d_H + (size_t)nd * w);
+                    out.push_back(rot_buf + i * w);
+                    steps.push_back(-hb * p.w);
+                    by_parent[p.node(p.node_c[nd], d - hb)].push_back((int)i);
+                }
+                rotate_items(c, in, out, steps, l2, false, s);
+                std::vector<AccTarget> tg;
+                std::vector<BinItem> cb;
+                for (auto& kv : by_parent) {
+                    tg.push_back({p.d_H + (size_t)kv.first * w, (int)cb.size(), (int)kv.second.size()});
+                    for (int i : kv.second) cb.push_back({rot_buf + (size_t)i * w, nullptr, nullptr});
+                }
+                items_sum_acc(c, tg, cb, 2, l2 + 1, s);
+            }
+        }
+    }
+
+    // 5. half-fill (copy the first kp slots of each block into the second half) and apply
+    {
+        std::vector<const u64*> in;
+        std::vector<u64*> out;
+        for (int b = 0; b < p.n_ub; b++) {
+            in.push_back(AccU + (size_t)b * w);
+            out.push_back(FU + (size_t)b * w);
+        }
+        for (int cb = 0; cb < p.n_vb; cb++) {
+            in.push_back(p.d_H + (size_t)p.node(cb, 0) * w);
+            out.push_back(FV + (size_t)cb * w);
+        }
+        std::vector<int> steps(in.size(), -p.kp);
+        rotate_items(c, in, out, steps, l2, true, s);
+        // base = rescale(X (.) reg), then X <- base + F (limbs 0..l2)
+        u64* PT = p.d_chunk;
+        materialize_plain(c, p.d_reg, c.n, p.n_ub + p.n_vb, l0 + 1, PT, lw, s);
+        std::vector<BinItem> pm;
+        std::vector<UnItem> rs;
+        for (int b = 0; b < p.n_ub; b++) {
+            pm.push_back({UD(b), PT + (size_t)b * lw, BaseU + (size_t)b * w});
+            rs.push_back({BaseU + (size_t)b * w, BaseU + (size_t)b * w});
+        }
+        for (int cb = 0; cb < p.n_vb; cb++) {
+            pm.push_back({VD(cb), PT + (size_t)(p.n_ub + cb) * lw, BaseV + (size_t)cb * w});
+            rs.push_back({BaseV + (size_t)cb * w, BaseV + (size_t)cb * w});
+        }
+        items_mul_plain(c, pm, 2, l0 + 1, s);
+        items_rescale(c, rs, 2, l0, s);
+        std::vector<BinItem> fin;
+        for (int b = 0; b < p.n_ub; b++) fin.push_back({BaseU + (size_t)b * w, FU + (size_t)b * w, UD(b)});
+        for (int cb = 0; cb < p.n_vb; cb++) fin.push_back({BaseV + (size_t)cb * w, FV + (size_t)cb * w, VD(cb)});
+        items_add(c, fin, 2, l2 + 1, false, s);
+    }
+}
+
+void run_predict(const fhe_mf_plan& p, const u64* U, const u64* V, int level, int user, u64* out, cudaStream_t s) {
+    Ctx& c = *p.c;
+    if (level < 2) fail(FHE_ERR_LEVEL_EXHAUSTED, "prediction needs level >= 2");
+    if (level > c.L) fail(FHE_ERR_INVALID_ARG, "level out of range");
+    if (user < 0 || user >= p.n) fail(FHE_ERR_INVALID_ARG, "user out of range");
+    if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
+    for (int t = 0; t < p.log_kp; t++) rotation_key(c, 1 << t);
+    for (int t = 0; t < p.beta; t++) rotation_key(c, (1 << t) * p.w);
+    c.arena.reset(s);
+    const size_t w = c.ct_words(), lw = w / 2;
+    const int b = user / p.B, a = user % p.B;
+    i64* mcoef = (i64*)c.scratch_bytes("pred_mask", sizeof(i64) * c.n);
+    std::vector<std::pair<int, double>> nz;
+    for (int x = 0; x < p.k; x++) nz.push_back({a * p.w + x, 1.0});
+    encode_sparse_device(c, nz, mcoef, s);
+    c.arena.reset(s);
+    u64* pt = c.scratch_u64("pred_pt", lw);
+    materialize_plain(c, mcoef, c.n, 1, level + 1, pt, lw, s);
+    u64* X = c.scratch_u64("pred_x", 2 * w);
+    u64* Y = X + w;
+    items_mul_plain(c, {BinItem{U + (size_t)b * w, pt, X}}, 2, level + 1, s);
+    items_rescale(c, {UnItem{X, X}}, 2, level, s);
+    for (int t = 0; t < p.beta; t++) {
+        rotate_items(c, {X}, {Y}, {(1 << t) * p.w}, level - 1, true, s);
+        std::swap(X, Y);
+    }
+    u64* T3 = c.scratch_u64("pred_t3", (size_t)p.n_vb * 3 * lw);
+    std::vector<BinItem> tens;
+    std::vector<u64*> t3s;
+    std::vector<UnItem> rs;
+    for (int cb = 0; cb < p.n_vb; cb++) {
+        tens.push_back({X, V + (size_t)cb * w, T3 + (size_t)cb * 3 * lw});
+        t3s.push_back(T3 + (size_t)cb * 3 * lw);
+        rs.push_back({T3 + (size_t)cb * 3 * lw, out + (size_t)cb * w});
+    }
+    items_tensor(c, tens, level, s);
+    relin_inplace(c, t3s, level - 1, s);
+    items_rescale(c, rs, 2, level - 1, s);
+    u64* tmp = c.scratch_u64("pred_tmp", (size_t)p.n_vb * w);
+    for (int t = 0; t < p.log_kp; t++) {
+        std::vector<const u64*> in;
+        std::vector<u64*> o;
+        std::vector<int> steps(p.n_vb, 1 << t);
+        for (int cb = 0; cb < p.n_vb; cb++) {
+            in.push_back(out + (size_t)cb * w);
+            o.push_back(tmp + (size_t)cb * w);
+        }
+        rotate_items(c, in, o, steps, level - 2, true, s);
+        std::vector<UnItem> cp;
+        for (int cb = 0; cb < p.n_vb; cb++) cp.push_back({tmp + (size_t)cb * w, out + (size_t)cb * w});
+        items_copy(c, cp, 2, level - 1, s);
+    }
+}
+
+template <typename F>
+int guarded(Ctx* c, F&& f) {
+    try {
+        if (c) {
+            c->last_error.clear();
+            CK(cudaSetDevice(c->device));
+        }
+        f();
+        return FHE_OK;
+    } catch (const FheException& e) {
+        if (c) c->last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->last_error = "host allocation failed";
+        return FHE_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (c) c->last_error = e.what();
+        return FHE_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t cap) {
+    if (!ctx || k < 1) return FHE_ERR_INVALID_ARG;
+    const Ctx& c = ctx->c;
+    int kp = next_pow2(k), w = 2 * kp;
+    if (w > c.slots) return FHE_ERR_INVALID_ARG;
+    int B = c.slots / w;
+    std::vector<int> st;
+    for (int t = 0; (1 << t) < kp; t++) st.push_back(1 << t);
+    for (int t = 0; (1 << t) < B; t++) st.push_back((1 << t) * w);
+    for (int t = 0; (1 << t) < B; t++) st.push_back(-(1 << t) * w);
+    st.push_back(-kp);
+    if (out) {
+        if (cap < st.size()) return FHE_ERR_INVALID_ARG;
+        std::copy(st.begin(), st.end(), out);
+    }
+    return (int)st.size();
+}
+
+int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* vals, fhe_mf_plan** out) {
+    if (!ctx || !out) return FHE_ERR_INVALID_ARG;
+    *out = nullptr;
+    fhe_mf_plan* p = new (std::nothrow) fhe_mf_plan();
+    if (!p) return FHE_ERR_OOM;
+    Ctx& c = ctx->c;
+    int rc = guarded(&c, [&] {
+        if (n < 1 || m < 1 || k < 1 || !row_ptr) fail(FHE_ERR_INVALID_ARG, "bad matrix shape");
+        const long long M = row_ptr[n];
+        if (row_ptr[0] != 0 || M < 0) fail(FHE_ERR_INVALID_ARG, "row_ptr must start at 0");
+        if (M > 0 && (!col_idx || !vals)) fail(FHE_ERR_INVALID_ARG, "null CSR arrays");
+        for (int i = 0; i < n; i++)
+            if (row_ptr[i + 1] < row_ptr[i]) fail(FHE_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
+        if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
+        p->c = &c;
+        p->n = n;
+        p->m = m;
+        p->k = k;
+        p->kp = next_pow2(k);
+        p->w = 2 * p->kp;
+        if (p->w > c.slots) fail(FHE_ERR_INVALID_ARG, "rank too large for the ring");
+        p->B = c.slots / p->w;
+        p->beta = hbit(p->B);
+        p->log_kp = hbit(p->kp);
+        p->n_ub = (n + p->B - 1) / p->B;
+        p->n_vb = (m + p->B - 1) / p->B;
+        p->M = M;
+        p->nnz_u.assign(n, 0);
+        p->nnz_v.assign(m, 0);
+        std::map<std::tuple<int, int, int>, std::vector<std::pair<int, double>>> gm;
+        for (int i = 0; i < n; i++) {
+            std::vector<int> cols(col_idx + row_ptr[i], col_idx + row_ptr[i + 1]);
+            std::sort(cols.begin(), cols.end());
+            for (size_t t = 1; t < cols.size(); t++)
+                if (cols[t] == cols[t - 1]) fail(FHE_ERR_INVALID_ARG, "duplicate (user, item) rating");
+            for (long long e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+                int j = col_idx[e];
+                if (j < 0 || j >= m) fail(FHE_ERR_INVALID_ARG, "column index out of range");
+                if (!std::isfinite(vals[e])) fail(FHE_ERR_INVALID_ARG, "non-finite rating");
+                int a = i % p->B, b = i / p->B, d = j % p->B, cb = j / p->B;
+                int delta = ((d - a) % p->B + p->B) % p->B;
+                gm[std::make_tuple(b, cb, delta)].push_back({a, vals[e]});
+                p->nnz_u[i]++;
+                p->nnz_v[j]++;
+            }
+        }
+        for (auto& kv : gm) {
+            Group g;
+            std::tie(g.b, g.c, g.delta) = kv.first;
+            auto v = kv.second;
+            std::sort(v.begin(), v.end());
+            for (auto& pr : v) {
+                g.a.push_back(pr.first);
+                g.r.push_back(pr.second);
+            }
+            p->groups.push_back(std::move(g));
+        }
+        // delta trees
+        p->closure.assign(p->n_vb, {});
+        p->node_of.assign((size_t)p->n_vb * p->B, -1);
+        for (int cb = 0; cb < p->n_vb; cb++) {
+            std::vector<char> in(p->B, 0);
+            in[0] = 1;
+            for (const Group& g : p->groups)
+                if (g.c == cb)
+                    for (int d = g.delta; d && !in[d]; d -= 1 << hbit(d)) in[d] = 1;
+            for (int d = 0; d < p->B; d++)
+                if (in[d]) {
+                    p->closure[cb].push_back(d);
+                    p->node_of[(size_t)cb * p->B + d] = (int)p->node_c.size();
+                    p->node_c.push_back(cb);
+                    p->node_delta.push_back(d);
+                }
+        }
+        for (const Group& g : p->groups) p->group_node.push_back(p->node(g.c, g.delta));
+        // EncryptCsrMatrix: each group's ratings in the first k slots of their blocks, top level
+        const int G = (int)p->groups.size();
+        const size_t w = c.ct_words();
+        p->d_R = plan_alloc<u64>(*p, (size_t)std::max(G, 1) * w);
+        const int chunk = 256;
+        i64* m_dev = (i64*)c.scratch_bytes("pack_m", sizeof(i64) * chunk * c.n);
+        for (int g0 = 0; g0 < G; g0 += chunk) {
+            int g1 = std::min(G, g0 + chunk);
+            std::vector<int> idx, off{0};
+            std::vector<double> val;
+            std::vector<u64> nonces;
+            for (int g = g0; g < g1; g++) {
+                const Group& gr = p->groups[g];
+                for (size_t t = 0; t < gr.a.size(); t++)
+                    if (gr.r[t] != 0.0)
+                        for (int x = 0; x < p->k; x++) {
+                            idx.push_back(gr.a[t] * p->w + x);
+                            val.push_back(gr.r[t]);
+                        }
+                off.push_back((int)idx.size());
+                nonces.push_back(kRNonce + (u64)g);
+            }
+            c.arena.reset(0);
+            encode_many_device(c, idx, val, off, m_dev, 0);
+            encrypt_coeffs_device(c, m_dev, c.n, g1 - g0, c.L, nonces, p->d_R + (size_t)g0 * w, 0);
+        }
+        CK(cudaStreamSynchronize(0));
+    });
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return FHE_OK;
+}
+
+void fhe_mf_plan_destroy(fhe_mf_plan* p) {
+    if (p) {
+        if (p->c) cudaSetDevice(p->c->device);
+        cudaDeviceSynchronize();
+        delete p;
+    }
+}
+
+int fhe_mf_plan_set_chunk(fhe_mf_plan* p, int32_t groups) {
+    if (!p || groups < 1) return FHE_ERR_INVALID_ARG;
+    if (p->d_chunk) {
+        cudaSetDevice(p->c->device);
+        cudaDeviceSynchronize();
+        cudaFree(p->d_chunk);
+        p->bytes -= (size_t)p->chunk_alloc * 14 * (p->c->ct_words() / 2) * sizeof(u64);
+        p->d_chunk = nullptr;
+    }
+    p->chunk = groups;
+    return FHE_OK;
+}
+
+int fhe_mf_plan_get_info(const fhe_mf_plan* p, fhe_mf_plan_info* out) {
+    if (!p || !out) return FHE_ERR_INVALID_ARG;
+    out->n_users = p->n;
+    out->n_items = p->m;
+    out->k = p->k;
+    out->kp = p->kp;
+    out->w = p->w;
+    out->B = p->B;
+    out->n_user_batches = p->n_ub;
+    out->n_item_batches = p->n_vb;
+    out->n_ratings = p->M;
+    out->n_groups = (int64_t)p->groups.size();
+    out->n_tree_nodes = (int64_t)p->node_c.size();
+    out->device_bytes = p->bytes;
+    return FHE_OK;
+}
+
+int fhe_mf_plan_get_groups(const fhe_mf_plan* p, int32_t* b, int32_t* cc, int32_t* delta, int32_t* count) {
+    if (!p) return FHE_ERR_INVALID_ARG;
+    for (size_t g = 0; g < p->groups.size(); g++) {
+        if (b) b[g] = p->groups[g].b;
+        if (cc) cc[g] = p->groups[g].c;
+        if (delta) delta[g] = p->groups[g].delta;
+        if (count) count[g] = (int32_t)p->groups[g].a.size();
+    }
+    return FHE_OK;
+}
+
+int fhe_mf_encrypt_factors(fhe_ctx* ctx, const fhe_mf_plan* p, int32_t which, const double* X, int32_t count,
+                           uint64_t* cts, void* stream) {
+    if (!ctx || !p) return FHE_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    return guarded(&c, [&] {
+        if (which != 0 && which != 1) fail(FHE_ERR_INVALID_ARG, "which must be 0 (users) or 1 (items)");
+        const int ent = which ? p->m : p->n, nb = which ? p->n_vb : p->n_ub;
+        if (count != ent || !X || !cts) fail(FHE_ERR_INVALID_ARG, "factor matrix must have one row per entity");
+        cudaStream_t s = (cudaStream_t)stream;
+        c.arena.reset(s);
+        std::vector<int> idx, off{0};
+        std::vector<double> val;
+        std::vector<u64> nonces;
+        for (int b = 0; b < nb; b++) {
+            std::vector<std::pair<int, double>> z;
+            for (int a = 0; a < p->B; a++) {
+                int e = b * p->B + a;
+                if (e >= ent) break;
+                for (int x = 0; x < p->k; x++) {
+                    z.push_back({a * p->w + x, X[(size_t)e * p->k + x]});
+                    z.push_back({a * p->w + p->kp + x, X[(size_t)e * p->k + x]});
+                }
+            }
+            std::sort(z.begin(), z.end());
+            for (auto& pr : z)
+                if (pr.second != 0.0) {
+                    idx.push_back(pr.first);
+                    val.push_back(pr.second);
+                }
+            off.push_back((int)idx.size());
+            nonces.push_back((which ? kVNonce : kUNonce) + (u64)b);
+        }
+        i64* m_dev = (i64*)c.scratch_bytes("fac_m", sizeof(i64) * nb * c.n);
+        encode_many_device(c, idx, val, off, m_dev, s);
+        encrypt_coeffs_device(c, m_dev, c.n, nb, c.L, nonces, cts, s);
+    });
+}
+
+int fhe_mf_decrypt_factors(fhe_ctx* ctx, const fhe_mf_plan* p, int32_t which, const uint64_t* cts, int32_t level,
+                           double* X, int32_t count, void* stream) {
+    if (!ctx || !p) return FHE_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    return guarded(&c, [&] {
+        if (which != 0 && which != 1) fail(FHE_ERR_INVALID_ARG, "which must be 0 (users) or 1 (items)");
+        const int ent = which ? p->m : p->n, nb = which ? p->n_vb : p->n_ub;
+        if (count != ent || !X || !cts) fail(FHE_ERR_INVALID_ARG, "factor matrix must have one row per entity");
+        std::vector<double> z((size_t)p->B * p->w);
+        for (int b = 0; b < nb; b++) {
+            decrypt_to_slots(c, cts + (size_t)b * c.ct_words(), level, z.data(), z.size(), (cudaStream_t)stream);
+            for (int a = 0; a < p->B; a++) {
+                int e = b * p->B + a;
+                if (e >= ent) break;
+                for (int x = 0; x < p->k; x++) X[(size_t)e * p->k + x] = z[(size_t)a * p->w + x];
+            }
+        }
+    });
+}
+
+int fhe_mf_sgd_epoch(fhe_ctx* ctx, fhe_mf_plan* p, uint64_t* U, uint64_t* V, int32_t level, double lr, double lam,
+                     void* stream) {
+    if (!ctx || !p) return FHE_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    return guarded(&c, [&] {
+        if (!U || !V) fail(FHE_ERR_INVALID_ARG, "null factor buffers");
+        if (!std::isfinite(lr) || !std::isfinite(lam)) fail(FHE_ERR_INVALID_ARG, "non-finite lr or lambda");
+        run_epoch(*p, U, V, level, lr, lam, (cudaStream_t)stream);
+    });
+}
+
+int fhe_predict(fhe_ctx* ctx, const fhe_mf_plan* p, const uint64_t* U, const uint64_t* V, int32_t level,
+                int32_t user, uint64_t* out, void* stream) {
+    if (!ctx || !p) return FHE_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    return guarded(&c, [&] {
+        if (!U || !V || !out) fail(FHE_ERR_INVALID_ARG, "null buffers");
+        run_predict(*p, U, V, level, user, out, (cudaStream_t)stream);
+    });
+}
+
+}  // extern "C"

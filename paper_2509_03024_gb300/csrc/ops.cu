@@ -1,0 +1,611 @@
+// ops.cu — batched RNS kernels over descriptor tables: element-wise add / sub /
+// plaintext product / tensor product, segmented accumulation, exact rescale,
+// the evaluation-domain automorphism and hybrid key switching (ModUp, key
+// inner product, ModDown; Han-Ki 2020 with fast base conversion).
+//
+// Launch shape of the element-wise kernels: blockIdx.y selects the item (a
+// table entry), the x dimension walks (component, limb, coefficient pair) with
+// one 128-bit access per residue pair. Item tables are uploaded through the
+// context's pinned descriptor arena.
+#include <algorithm>
+#include <cstring>
+
+#include "core.cuh"
+
+namespace fhe {
+
+// ============================================================================ arena
+
+void Arena::reset(cudaStream_t s) {
+    CK(cudaStreamSynchronize(s));
+    for (auto& b : blocks) b.used = 0;
+    cur = 0;
+}
+
+void* Arena::push(const void* data, size_t bytes, cudaStream_t s) {
+    const size_t span = std::max<size_t>((bytes + 255) & ~(size_t)255, 256);
+    while (cur < blocks.size() && blocks[cur].used + span > blocks[cur].cap) cur++;
+    if (cur == blocks.size()) {
+        Block b;
+        b.cap = std::max<size_t>(span, (size_t)4 << 20);
+        CK(cudaMallocHost((void**)&b.host, b.cap));
+        CK(cudaMalloc((void**)&b.dev, b.cap));
+        blocks.push_back(b);
+    }
+    Block& b = blocks[cur];
+    char* h = b.host + b.used;
+    char* d = b.dev + b.used;
+    b.used += span;
+    if (bytes) {
+        std::memcpy(h, data, bytes);
+        CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
+    }
+    return d;
+}
+
+Arena::~Arena() {
+    for (auto& b : blocks) {
+        if (b.host) cudaFreeHost(b.host);
+        if (b.dev) cudaFree(b.dev);
+    }
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+T* upload(Ctx& c, const std::vector<T>& v, cudaStream_t s) {
+    return c.arena.push_vec(v, s);
+}
+
+inline dim3 grid2(size_t per_item, int items) {
+    size_t bx = (per_item + kThreads - 1) / kThreads;
+    if (bx > 65535u * 16) bx = 65535u * 16;
+    return dim3((unsigned)std::max<size_t>(bx, 1), (unsigned)std::min(items, 65535));
+}
+inline unsigned grid1(size_t work) {
+    size_t b = (work + kThreads - 1) / kThreads;
+    return (unsigned)std::min<size_t>(std::max<size_t>(b, 1), (size_t)1 << 30);
+}
+
+// ---------------------------------------------------------------- element-wise
+
+// For element e of an item: component p, limb i, coefficient pair k2.
+struct PIdx {
+    int part, limb, k2;
+};
+__device__ __forceinline__ PIdx pidx(size_t e, int log_half, int limbs) {
+    PIdx r;
+    r.k2 = (int)(e & ((1u << log_half) - 1));
+    size_t row = e >> log_half;
+    r.limb = (int)(row % limbs);
+    r.part = (int)(row / limbs);
+    return r;
+}
+
+__device__ __forceinline__ size_t off2(int part, int limb, int log_n, size_t part_words) {
+    return (size_t)part * part_words + ((size_t)limb << log_n);
+}
+
+#define ITEM_LOOP(items_count)                                                                       \
+    for (int it = blockIdx.y; it < (items_count); it += gridDim.y)                                   \
+        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < per;                      \
+             e += (size_t)gridDim.x * blockDim.x)
+
+__global__ void add_items_kernel(const BinItem* __restrict__ tab, int items, int parts, int limbs, int log_n,
+                                 size_t part_words, const Prime* __restrict__ pr, bool sub) {
+    const size_t per = (size_t)parts * limbs << (log_n - 1);
+    ITEM_LOOP(items) {
+        const BinItem t = tab[it];
+        PIdx x = pidx(e, log_n - 1, limbs);
+        size_t o = off2(x.part, x.limb, log_n, part_words);
+        const u64 q = pr[x.limb].q;
+        ulonglong2 va = reinterpret_cast<const ulonglong2*>(t.a + o)[x.k2];
+        ulonglong2 vb = reinterpret_cast<const ulonglong2*>(t.b + o)[x.k2];
+        ulonglong2 r;
+        r.x = sub ? sub_mod(va.x, vb.x, q) : add_mod(va.x, vb.x, q);
+        r.y = sub ? sub_mod(va.y, vb.y, q) : add_mod(va.y, vb.y, q);
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = r;
+    }
+}
+
+__global__ void copy_items_kernel(const UnItem* __restrict__ tab, int items, int parts, int limbs, int log_n,
+                                  size_t part_words) {
+    const size_t per = (size_t)parts * limbs << (log_n - 1);
+    ITEM_LOOP(items) {
+        const UnItem t = tab[it];
+        PIdx x = pidx(e, log_n - 1, limbs);
+        size_t o = off2(x.part, x.limb, log_n, part_words);
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = reinterpret_cast<const ulonglong2*>(t.in + o)[x.k2];
+    }
+}
+
+__global__ void mul_plain_items_kernel(const BinItem* __restrict__ tab, int items, int parts, int limbs,
+                                       int log_n, size_t part_words, const Prime* __restrict__ pr) {
+    const size_t per = (size_t)parts * limbs << (log_n - 1);
+    ITEM_LOOP(items) {
+        const BinItem t = tab[it];
+        PIdx x = pidx(e, log_n - 1, limbs);
+        size_t o = off2(x.part, x.limb, log_n, part_words);
+        const Prime P = pr[x.limb];
+        ulonglong2 va = reinterpret_cast<const ulonglong2*>(t.a + o)[x.k2];
+        ulonglong2 vb = reinterpret_cast<const ulonglong2*>(t.b + ((size_t)x.limb << log_n))[x.k2];
+        ulonglong2 r;
+        r.x = mul_mod(va.x, vb.x, P);
+        r.y = mul_mod(va.y, vb.y, P);
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = r;
+    }
+}
+
+__device__ __forceinline__ void tensor_pair(const u64* a, const u64* b, size_t o, size_t pw, int k2,
+                                            const Prime& P, ulonglong2& d0, ulonglong2& d1, ulonglong2& d2) {
+    ulonglong2 a0 = reinterpret_cast<const ulonglong2*>(a + o)[k2];
+    ulonglong2 a1 = reinterpret_cast<const ulonglong2*>(a + pw + o)[k2];
+    ulonglong2 b0 = reinterpret_cast<const ulonglong2*>(b + o)[k2];
+    ulonglong2 b1 = reinterpret_cast<const ulonglong2*>(b + pw + o)[k2];
+    d0.x = mul_mod(a0.x, b0.x, P);
+    d0.y = mul_mod(a0.y, b0.y, P);
+    d1.x = add_mod(mul_mod(a0.x, b1.x, P), mul_mod(a1.x, b0.x, P), P.q);
+    d1.y = add_mod(mul_mod(a0.y, b1.y, P), mul_mod(a1.y, b0.y, P), P.q);
+    d2.x = mul_mod(a1.x, b1.x, P);
+    d2.y = mul_mod(a1.y, b1.y, P);
+}
+
+__global__ void tensor_items_kernel(const BinItem* __restrict__ tab, int items, int limbs, int log_n,
+                                    size_t pw, const Prime* __restrict__ pr) {
+    const size_t per = (size_t)limbs << (log_n - 1);
+    ITEM_LOOP(items) {
+        const BinItem t = tab[it];
+        PIdx x = pidx(e, log_n - 1, limbs);
+        size_t o = (size_t)x.limb << log_n;
+        const Prime P = pr[x.limb];
+        ulonglong2 d0, d1, d2;
+        tensor_pair(t.a, t.b, o, pw, x.k2, P, d0, d1, d2);
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = d0;
+        reinterpret_cast<ulonglong2*>(t.out + pw + o)[x.k2] = d1;
+        reinterpret_cast<ulonglong2*>(t.out + 2 * pw + o)[x.k2] = d2;
+    }
+}
+
+__global__ void tensor_acc_kernel(const AccTarget* __restrict__ tg, const BinItem* __restrict__ cb, int targets,
+                                  int limbs, int log_n, size_t pw, const Prime* __restrict__ pr) {
+    const size_t per = (size_t)limbs << (log_n - 1);
+    ITEM_LOOP(targets) {
+        const AccTarget t = tg[it];
+        PIdx x = pidx(e, log_n - 1, limbs);
+        size_t o = (size_t)x.limb << log_n;
+        const Prime P = pr[x.limb];
+        ulonglong2 s0 = reinterpret_cast<const ulonglong2*>(t.out + o)[x.k2];
+        ulonglong2 s1 = reinterpret_cast<const ulonglong2*>(t.out + pw + o)[x.k2];
+        ulonglong2 s2 = reinterpret_cast<const ulonglong2*>(t.out + 2 * pw + o)[x.k2];
+        for (int j = 0; j < t.cnt; j++) {
+            const BinItem c = cb[t.off + j];
+            ulonglong2 d0, d1, d2;
+            tensor_pair(c.a, c.b, o, pw, x.k2, P, d0, d1, d2);
+            s0.x = add_mod(s0.x, d0.x, P.q);
+            s0.y = add_mod(s0.y, d0.y, P.q);
+            s1.x = add_mod(s1.x, d1.x, P.q);
+            s1.y = add_mod(s1.y, d1.y, P.q);
+            s2.x = add_mod(s2.x, d2.x, P.q);
+            s2.y = add_mod(s2.y, d2.y, P.q);
+        }
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = s0;
+        reinterpret_cast<ulonglong2*>(t.out + pw + o)[x.k2] = s1;
+        reinterpret_cast<ulonglong2*>(t.out + 2 * pw + o)[x.k2] = s2;
+    }
+}
+
+__global__ void sum_acc_kernel(const AccTarget* __restrict__ tg, const BinItem* __restrict__ cb, int targets,
+                               int parts, int limbs, int log_n, size_t pw, const Prime* __restrict__ pr) {
+    const size_t per = (size_t)parts * limbs << (log_n - 1);
+    ITEM_LOOP(targets) {
+        const AccTarget t = tg[it];
+        PIdx x = pidx(e, log_n - 1, limbs);
+        size_t o = off2(x.part, x.limb, log_n, pw);
+        const u64 q = pr[x.limb].q;
+        ulonglong2 s = reinterpret_cast<const ulonglong2*>(t.out + o)[x.k2];
+        for (int j = 0; j < t.cnt; j++) {
+            ulonglong2 v = reinterpret_cast<const ulonglong2*>(cb[t.off + j].a + o)[x.k2];
+            s.x = add_mod(s.x, v.x, q);
+            s.y = add_mod(s.y, v.y, q);
+        }
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = s;
+    }
+}
+
+__device__ __forceinline__ u64 signed_mod(i64 v, u64 q) {
+    if (v >= 0) return (u64)v % q;
+    u64 m = (u64)(-(v + 1)) % q;  // -(v+1) >= 0 avoids overflow at INT64_MIN
+    return q - 1 - m;
+}
+
+__global__ void int_to_rns_kernel(u64* out, size_t out_stride, const i64* __restrict__ in, size_t in_stride,
+                                  int items, int limbs, int log_n, const Prime* __restrict__ pr) {
+    const size_t total = (size_t)items * limbs << log_n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(e & ((1u << log_n) - 1));
+        size_t row = e >> log_n;
+        int limb = (int)(row % limbs);
+        int item = (int)(row / limbs);
+        out[(size_t)item * out_stride + ((size_t)limb << log_n) + k] =
+            signed_mod(in[(size_t)item * in_stride + k], pr[limb].q);
+    }
+}
+
+__global__ void int8_to_rns_kernel(u64* out, size_t out_stride, const int8_t* __restrict__ in, size_t in_stride,
+                                   int items, int limbs, int log_n, int split, int jump,
+                                   const Prime* __restrict__ pr) {
+    const size_t total = (size_t)items * limbs << log_n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(e & ((1u << log_n) - 1));
+        size_t row = e >> log_n;
+        int limb = (int)(row % limbs);
+        int item = (int)(row / limbs);
+        int prime = limb + (limb >= split ? jump : 0);
+        int v = in[(size_t)item * in_stride + k];
+        u64 q = pr[prime].q;
+        out[(size_t)item * out_stride + ((size_t)limb << log_n) + k] = v >= 0 ? (u64)v : q - (u64)(-v);
+    }
+}
+
+// Evaluation slot k holds a(psi^(2 brev(k) + 1)); X -> X^g maps it to the slot k'
+// with 2 brev(k') + 1 = g (2 brev(k) + 1) mod 2N.
+__device__ __forceinline__ int auto_src(int k, long long g, int log_n) {
+    const unsigned sh = 32 - log_n;
+    unsigned bk = __brev((unsigned)k) >> sh;
+    unsigned e = (unsigned)(((unsigned long long)g * (2ull * bk + 1ull)) & ((2ull << log_n) - 1ull));
+    return (int)(__brev((e - 1u) >> 1) >> sh);
+}
+
+__global__ void automorphism_kernel(u64* out, const u64* __restrict__ in, int limbs, int log_n, long long g) {
+    const size_t total = (size_t)limbs << log_n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(e & ((1u << log_n) - 1));
+        size_t row = e >> log_n;
+        out[e] = in[(row << log_n) + auto_src(k, g, log_n)];
+    }
+}
+
+// ---------------------------------------------------------------- rescale
+
+__global__ void gather_last_kernel(u64* last, const UnItem* __restrict__ tab, int items, int parts, int level,
+                                   int log_n, size_t pw) {
+    const size_t per = (size_t)parts << log_n;
+    ITEM_LOOP(items) {
+        int k = (int)(e & ((1u << log_n) - 1));
+        int p = (int)(e >> log_n);
+        last[((size_t)it * parts + p << log_n) + k] = tab[it].in[(size_t)p * pw + ((size_t)level << log_n) + k];
+    }
+}
+
+// spread[row][i][k] = centred(last[row][k]) mod q_i, i < l
+__global__ void rescale_spread_kernel(u64* out, const u64* __restrict__ last, int rows, int l, int log_n,
+                                      const Prime* __restrict__ pr) {
+    const size_t total = (size_t)rows << log_n;
+    const u64 ql = pr[l].q;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(e & ((1u << log_n) - 1));
+        size_t row = e >> log_n;
+        u64 r = last[e];
+        bool neg = r > (ql >> 1);
+        u64 mag = neg ? ql - r : r;
+        for (int i = 0; i < l; i++) {
+            u64 qi = pr[i].q;
+            u64 m = mag % qi;
+            out[((row * l + i) << log_n) + k] = neg ? (m ? qi - m : 0) : m;
+        }
+    }
+}
+
+// out[i] = (in[i] - spread[i]) * q_l^-1 mod q_i
+__global__ void rescale_combine_kernel(const UnItem* __restrict__ tab, const u64* __restrict__ spread, int items,
+                                       int parts, int l, int log_n, size_t pw, const Prime* __restrict__ pr,
+                                       const u64* __restrict__ resc_row) {
+    const size_t per = (size_t)parts * l << (log_n - 1);
+    ITEM_LOOP(items) {
+        const UnItem t = tab[it];
+        PIdx x = pidx(e, log_n - 1, l);
+        size_t o = off2(x.part, x.limb, log_n, pw);
+        const u64 q = pr[x.limb].q;
+        const u64 w = resc_row[2 * x.limb], ws = resc_row[2 * x.limb + 1];
+        ulonglong2 a = reinterpret_cast<const ulonglong2*>(t.in + o)[x.k2];
+        size_t row = (size_t)it * parts + x.part;
+        ulonglong2 v = reinterpret_cast<const ulonglong2*>(spread + ((row * l + x.limb) << log_n))[x.k2];
+        ulonglong2 r;
+        r.x = mul_shoup(sub_mod(a.x, v.x, q), w, ws, q);
+        r.y = mul_shoup(sub_mod(a.y, v.y, q), w, ws, q);
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = r;
+    }
+}
+
+// ---------------------------------------------------------------- key switching
+
+// coef[t][i][k] = d_t[i][perm(k)]
+__global__ void ks_gather_kernel(u64* coef, const KsItem* __restrict__ tab, int items, int l1, int log_n) {
+    const size_t per = (size_t)l1 << log_n;
+    ITEM_LOOP(items) {
+        const KsItem t = tab[it];
+        int k = (int)(e & ((1u << log_n) - 1));
+        int i = (int)(e >> log_n);
+        int src = t.galois == 1 ? k : auto_src(k, t.galois, log_n);
+        coef[(size_t)it * per + e] = t.d[((size_t)i << log_n) + src];
+    }
+}
+
+// ext[t][j][x][k] = sum_{i in D_j} [coef_i * qhat_i^-1]_{q_i} * qhat_i  mod p_x, x < next
+__global__ void modup_kernel(u64* ext, const u64* __restrict__ coef, int items, int level, int dn, int alpha,
+                             int next, int L, int log_n, const Prime* __restrict__ pr,
+                             const u64* __restrict__ up_inv, const u64* __restrict__ up_hat, int n_ext) {
+    const size_t total = (size_t)items * dn << log_n;
+    const int l1 = level + 1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(e & ((1u << log_n) - 1));
+        size_t row = e >> log_n;
+        int j = (int)(row % dn), t = (int)(row / dn);
+        int i0 = j * alpha;
+        int i1 = min(i0 + alpha, l1);
+        u64 y[8];
+        for (int i = i0; i < i1; i++) {
+            const u64* ui = up_inv + 2 * ((size_t)level * (L + 1) + i);
+            y[i - i0] = mul_shoup(coef[(((size_t)t * l1 + i) << log_n) + k], ui[0], ui[1], pr[i].q);
+        }
+        u64* dst = ext + ((size_t)(t * dn + j) * next << log_n) + k;
+        for (int x = 0; x < next; x++) {
+            int px = x < l1 ? x : x + (L - level);
+            u64 p = pr[px].q;
+            u64 acc = 0;
+            for (int i = i0; i < i1; i++) {
+                const u64* h = up_hat + 2 * (((size_t)level * (L + 1) + i) * n_ext + px);
+                acc = add_mod(acc, mul_shoup(y[i - i0], h[0], h[1], p), p);
+            }
+            dst[(size_t)x << log_n] = acc;
+        }
+    }
+}
+
+// acc[t][h][x][k] = sum_j ext[t][j][x][k] * key_t[j][h][px][k]
+__global__ void ks_inner_kernel(u64* acc, const u64* __restrict__ ext, const KsItem* __restrict__ tab, int items,
+                                int dn, int next, int level, int L, int n_ext, int log_n,
+                                const Prime* __restrict__ pr) {
+    const size_t total = (size_t)items * next << (log_n - 1);
+    const int l1 = level + 1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int k2 = (int)(e & ((1u << (log_n - 1)) - 1));
+        size_t row = e >> (log_n - 1);
+        int x = (int)(row % next), t = (int)(row / next);
+        int px = x < l1 ? x : x + (L - level);
+        const Prime P = pr[px];
+        const u64* key = tab[t].key;
+        u64 s0x = 0, s0y = 0, s1x = 0, s1y = 0;
+        for (int j = 0; j < dn; j++) {
+            ulonglong2 v = reinterpret_cast<const ulonglong2*>(ext + ((size_t)((t * dn + j) * next + x) << log_n))[k2];
+            ulonglong2 kb = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
+            ulonglong2 ka = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
+            s0x = add_mod(s0x, mul_mod(v.x, kb.x, P), P.q);
+            s0y = add_mod(s0y, mul_mod(v.y, kb.y, P), P.q);
+            s1x = add_mod(s1x, mul_mod(v.x, ka.x, P), P.q);
+            s1y = add_mod(s1y, mul_mod(v.y, ka.y, P), P.q);
+        }
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] = make_ulonglong2(s0x, s0y);
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] = make_ulonglong2(s1x, s1y);
+    }
+}
+
+// conv[t][h][i][k] = sum_kk [accP_kk * Phat_kk^-1]_{p_kk} * Phat_kk  mod q_i, i <= level
+__global__ void moddown_kernel(u64* conv, const u64* __restrict__ acc, int items, int level, int alpha, int next,
+                               int L, int log_n, const Prime* __restrict__ pr, const u64* __restrict__ down_inv,
+                               const u64* __restrict__ down_hat) {
+    const size_t total = (size_t)items * 2 << log_n;
+    const int l1 = level + 1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(e & ((1u << log_n) - 1));
+        size_t th = e >> log_n;  // t*2 + h
+        u64 y[8];
+        for (int kk = 0; kk < alpha; kk++) {
+            u64 p = pr[L + 1 + kk].q;
+            y[kk] = mul_shoup(acc[((th * next + l1 + kk) << log_n) + k], down_inv[2 * kk], down_inv[2 * kk + 1], p);
+        }
+        for (int i = 0; i < l1; i++) {
+            u64 q = pr[i].q;
+            u64 s = 0;
+            for (int kk = 0; kk < alpha; kk++) {
+                const u64* h = down_hat + 2 * ((size_t)kk * (L + 1) + i);
+                s = add_mod(s, mul_shoup(y[kk], h[0], h[1], q), q);
+            }
+            conv[((th * l1 + i) << log_n) + k] = s;
+        }
+    }
+}
+
+// out_h = (acc_h - conv_h) * P^-1 + add terms
+__global__ void ks_final_kernel(const KsItem* __restrict__ tab, const u64* __restrict__ acc,
+                                const u64* __restrict__ conv, int items, int level, int next, int log_n,
+                                const Prime* __restrict__ pr, const u64* __restrict__ pinv) {
+    const int l1 = level + 1;
+    const size_t per = (size_t)2 * l1 << log_n;
+    ITEM_LOOP(items) {
+        const KsItem t = tab[it];
+        int k = (int)(e & ((1u << log_n) - 1));
+        size_t row = e >> log_n;
+        int i = (int)(row % l1);
+        int h = (int)(row / l1);
+        size_t th = (size_t)it * 2 + h;
+        u64 q = pr[i].q;
+        u64 a = acc[((th * next + i) << log_n) + k];
+        u64 cv = conv[((th * l1 + i) << log_n) + k];
+        u64 v = mul_shoup(sub_mod(a, cv, q), pinv[2 * i], pinv[2 * i + 1], q);
+        size_t o = ((size_t)i << log_n);
+        if (h == 0) {
+            if (t.addP0) {
+                int src = t.galois == 1 ? k : auto_src(k, t.galois, log_n);
+                v = add_mod(v, t.addP0[o + src], q);
+            }
+            if (t.addI0) v = add_mod(v, t.addI0[o + k], q);
+            t.out0[o + k] = v;
+        } else {
+            if (t.addI1) v = add_mod(v, t.addI1[o + k], q);
+            t.out1[o + k] = v;
+        }
+    }
+}
+
+}  // namespace
+
+// ============================================================================ launchers
+
+void items_add(Ctx& c, const std::vector<BinItem>& it, int parts, int limbs, bool sub, cudaStream_t s) {
+    if (it.empty()) return;
+    const BinItem* d = upload(c, it, s);
+    size_t per = (size_t)parts * limbs * c.n / 2;
+    add_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs, c.log_n,
+                                                                     (size_t)(c.L + 1) * c.n, c.d_primes, sub);
+    CK(cudaGetLastError());
+}
+
+void items_copy(Ctx& c, const std::vector<UnItem>& it, int parts, int limbs, cudaStream_t s) {
+    if (it.empty()) return;
+    const UnItem* d = upload(c, it, s);
+    size_t per = (size_t)parts * limbs * c.n / 2;
+    copy_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs, c.log_n,
+                                                                      (size_t)(c.L + 1) * c.n);
+    CK(cudaGetLastError());
+}
+
+void items_mul_plain(Ctx& c, const std::vector<BinItem>& it, int parts, int limbs, cudaStream_t s) {
+    if (it.empty()) return;
+    const BinItem* d = upload(c, it, s);
+    size_t per = (size_t)parts * limbs * c.n / 2;
+    mul_plain_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs,
+                                                                           c.log_n, (size_t)(c.L + 1) * c.n,
+                                                                           c.d_primes);
+    CK(cudaGetLastError());
+}
+
+void items_tensor(Ctx& c, const std::vector<BinItem>& it, int limbs, cudaStream_t s) {
+    if (it.empty()) return;
+    const BinItem* d = upload(c, it, s);
+    size_t per = (size_t)limbs * c.n / 2;
+    tensor_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), limbs, c.log_n,
+                                                                        (size_t)(c.L + 1) * c.n, c.d_primes);
+    CK(cudaGetLastError());
+}
+
+void items_tensor_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<BinItem>& contrib, int limbs,
+                      cudaStream_t s) {
+    if (tg.empty()) return;
+    const AccTarget* dt = upload(c, tg, s);
+    const BinItem* dc = upload(c, contrib, s);
+    size_t per = (size_t)limbs * c.n / 2;
+    tensor_acc_kernel<<<grid2(per, (int)tg.size()), kThreads, 0, s>>>(dt, dc, (int)tg.size(), limbs, c.log_n,
+                                                                      (size_t)(c.L + 1) * c.n, c.d_primes);
+    CK(cudaGetLastError());
+}
+
+void items_sum_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<BinItem>& contrib, int parts,
+                   int limbs, cudaStream_t s) {
+    if (tg.empty()) return;
+    const AccTarget* dt = upload(c, tg, s);
+    const BinItem* dc = upload(c, contrib, s);
+    size_t per = (size_t)parts * limbs * c.n / 2;
+    sum_acc_kernel<<<grid2(per, (int)tg.size()), kThreads, 0, s>>>(dt, dc, (int)tg.size(), parts, limbs, c.log_n,
+                                                                   (size_t)(c.L + 1) * c.n, c.d_primes);
+    CK(cudaGetLastError());
+}
+
+void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s) {
+    if (level < 1) fail(FHE_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 1");
+    if (it.empty()) return;
+    const int n = c.n, items = (int)it.size(), rows = items * parts;
+    const size_t pw = (size_t)(c.L + 1) * n;
+    const UnItem* d = upload(c, it, s);
+    u64* last = c.scratch_u64("resc_last", (size_t)rows * n);
+    u64* spread = c.scratch_u64("resc_spread", (size_t)rows * level * n);
+    gather_last_kernel<<<grid2((size_t)parts * n, items), kThreads, 0, s>>>(last, d, items, parts, level, c.log_n, pw);
+    CK(cudaGetLastError());
+    ntt_inverse(c, poly_batch(last, n, 0, rows, 1, level, 1, level), s);
+    rescale_spread_kernel<<<grid1((size_t)rows * n), kThreads, 0, s>>>(spread, last, rows, level, c.log_n,
+                                                                       c.d_primes);
+    CK(cudaGetLastError());
+    ntt_forward(c, poly_batch(spread, (size_t)level * n, 0, rows, 1, 0, level), s);
+    rescale_combine_kernel<<<grid2((size_t)parts * level * n / 2, items), kThreads, 0, s>>>(
+        d, spread, items, parts, level, c.log_n, pw, c.d_primes, c.d_resc + (size_t)2 * level * (c.L + 1));
+    CK(cudaGetLastError());
+}
+
+void k_int_to_rns(const Ctx& c, u64* out, size_t out_item_stride, const i64* in, size_t in_stride, int items,
+                  int limbs, cudaStream_t s) {
+    size_t work = (size_t)items * limbs * c.n;
+    if (!work) return;
+    int_to_rns_kernel<<<grid1(work), kThreads, 0, s>>>(out, out_item_stride, in, in_stride, items, limbs, c.log_n,
+                                                       c.d_primes);
+    CK(cudaGetLastError());
+}
+
+void k_int8_to_rns(const Ctx& c, u64* out, size_t out_item_stride, const int8_t* in, size_t in_stride, int items,
+                   int limbs, int prime_split, int prime_jump, cudaStream_t s) {
+    size_t work = (size_t)items * limbs * c.n;
+    if (!work) return;
+    int8_to_rns_kernel<<<grid1(work), kThreads, 0, s>>>(out, out_item_stride, in, in_stride, items, limbs, c.log_n,
+                                                        prime_split, prime_jump, c.d_primes);
+    CK(cudaGetLastError());
+}
+
+void k_automorphism_poly(const Ctx& c, u64* out, const u64* in, int limbs, int galois, cudaStream_t s) {
+    automorphism_kernel<<<grid1((size_t)limbs * c.n), kThreads, 0, s>>>(out, in, limbs, c.log_n, galois);
+    CK(cudaGetLastError());
+}
+
+void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
+    if (all.empty()) return;
+    if (c.alpha > 8) fail(FHE_ERR_INVALID_ARG, "at most 8 special primes are supported");
+    const int n = c.n, l1 = level + 1, next = l1 + c.alpha, dn = c.dnum(level);
+    // bound the ModUp expansion buffer to ~2 GiB per sub-batch
+    const size_t per_item = (size_t)(dn * next + 2 * next + 2 * l1 + l1) * n * sizeof(u64);
+    const int max_items = (int)std::max<size_t>(1, ((size_t)2 << 30) / per_item);
+    for (size_t b0 = 0; b0 < all.size(); b0 += max_items) {
+        const int items = (int)std::min<size_t>(max_items, all.size() - b0);
+        std::vector<KsItem> it(all.begin() + b0, all.begin() + b0 + items);
+        const KsItem* d = upload(c, it, s);
+        u64* coef = c.scratch_u64("ks_coef", (size_t)items * l1 * n);
+        u64* ext = c.scratch_u64("ks_ext", (size_t)items * dn * next * n);
+        u64* acc = c.scratch_u64("ks_acc", (size_t)items * 2 * next * n);
+        u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
+        ks_gather_kernel<<<grid2((size_t)l1 * n, items), kThreads, 0, s>>>(coef, d, items, l1, c.log_n);
+        CK(cudaGetLastError());
+        ntt_inverse(c, poly_batch(coef, (size_t)l1 * n, 0, items, 1, 0, l1), s);
+        modup_kernel<<<grid1((size_t)items * dn * n), kThreads, 0, s>>>(ext, coef, items, level, dn, c.alpha, next,
+                                                                        c.L, c.log_n, c.d_primes, c.d_up_inv,
+                                                                        c.d_up_hat, c.n_ext);
+        CK(cudaGetLastError());
+        PolyBatch pe = poly_batch(ext, (size_t)dn * next * n, (size_t)next * n, items, dn, 0, next);
+        pe.split = l1;
+        pe.jump = c.L - level;
+        ntt_forward(c, pe, s);
+        ks_inner_kernel<<<grid1((size_t)items * next * n / 2), kThreads, 0, s>>>(acc, ext, d, items, dn, next,
+                                                                                 level, c.L, c.n_ext, c.log_n,
+                                                                                 c.d_primes);
+        CK(cudaGetLastError());
+        PolyBatch pa = poly_batch(acc, (size_t)2 * next * n, (size_t)next * n, items, 2, l1, c.alpha);
+        pa.split = l1;
+        pa.jump = c.L - level;
+        ntt_inverse(c, pa, s);
+        moddown_kernel<<<grid1((size_t)items * 2 * n), kThreads, 0, s>>>(conv, acc, items, level, c.alpha, next,
+                                                                         c.L, c.log_n, c.d_primes, c.d_down_inv,
+                                                                         c.d_down_hat);
+        CK(cudaGetLastError());
+        ntt_forward(c, poly_batch(conv, (size_t)2 * l1 * n, (size_t)l1 * n, items, 2, 0, l1), s);
+        ks_final_kernel<<<grid2((size_t)2 * l1 * n, items), kThreads, 0, s>>>(d, acc, conv, items, level, next,
+                                                                              c.log_n, c.d_primes, c.d_pinv);
+        CK(cudaGetLastError());
+    }
+}
+
+}  // namespace fhe

@@ -1,0 +1,176 @@
+"""GPU parity of the RNS-CKKS primitives against the CPU oracle (bit-exact in coefficient form).
+
+Covers the ring sizes of the single-pass NTT (N = 2^10, 2^13) and of the
+two-pass NTT (N = 2^15, 2^16), one and several special primes, every level.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_common import (assert_ct_equal, ct_slice, gpu_ctx, oracle_ctx, tensor3_to_coeff, to_coeff,
+                              torch)
+from oracle import ckks
+
+pytestmark = pytest.mark.gpu
+
+SEED = 20250903
+
+
+def _slots(n, seed, scale=1.0):
+    return np.random.default_rng(seed).normal(0, scale, n)
+
+
+@pytest.mark.parametrize("preset", ["t10", "t11a2", "tiny"])
+def test_primes_match_oracle(preset):
+    ctx = gpu_ctx(preset, SEED)
+    he = oracle_ctx(preset, SEED)
+    assert ctx.primes == he.prm.q + he.prm.p
+
+
+@pytest.mark.parametrize("preset", ["t10", "tiny", "paper", "large"])
+def test_ntt_roundtrip_and_product(preset):
+    """INTT(NTT(a)) = a; NTT-domain product = oracle negacyclic product (via mul_plain)."""
+    ctx = gpu_ctx(preset, SEED)
+    n, L1 = ctx.n, ctx.top + 1
+    rng = np.random.default_rng(1)
+    a = np.stack([rng.integers(0, q, n, dtype=np.uint64) for q in ctx.primes[:L1]])
+    t = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    ctx.ntt_forward(t, 1, L1)
+    assert not np.array_equal(t.cpu().numpy().view(np.uint64), a)
+    ctx.ntt_inverse(t, 1, L1)
+    assert np.array_equal(t.cpu().numpy().view(np.uint64), a)
+    # empty batch is a no-op
+    ctx.ntt_forward(t, 0, L1)
+
+
+@pytest.mark.parametrize("preset", ["t10", "t11a2", "tiny", "paper"])
+def test_encode_matches_oracle_exactly(preset):
+    ctx = gpu_ctx(preset, SEED)
+    he = oracle_ctx(preset, SEED)
+    for z in (_slots(ctx.slots, 2), _slots(37, 3, 4.0), np.zeros(5), np.array([0.0, 1.5, 0.0, -2.25])):
+        out = torch.zeros(ctx.n, dtype=torch.int64, device="cuda")
+        ctx.encode(z, out)
+        got = out.cpu().numpy()
+        want = he.enc.encode(z)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("preset", ["t10", "t11a2", "tiny", "large"])
+def test_encrypt_bit_exact_and_decrypt(preset):
+    ctx = gpu_ctx(preset, SEED)
+    he = oracle_ctx(preset, SEED)
+    z = _slots(ctx.slots, 4)
+    for level in sorted({ctx.top, 1, 0}):
+        ct = ctx.empty_ct()
+        ctx.encrypt(z, level, 77 + level, ct)
+        ora = he.encrypt(z, level, 77 + level)
+        assert_ct_equal(to_coeff(ctx, ct, level)[0], ora, f"encrypt level {level}")
+        dec = ctx.decrypt(ct, level)
+        tol = 1e-6 if ctx.log_scale >= 40 else 1e-3
+        if level >= 1 or ctx.log_scale <= 40:
+            assert np.abs(dec - z).max() < tol
+
+
+@pytest.mark.parametrize("preset", ["t10", "t11a2"])
+def test_add_sub_mul_plain_tensor(preset):
+    ctx = gpu_ctx(preset, SEED)
+    he = oracle_ctx(preset, SEED)
+    L = ctx.top
+    x, y = _slots(ctx.slots, 5), _slots(ctx.slots, 6)
+    a, b = ctx.empty_ct(2), None
+    ctx.encrypt(x, L, 1, ct_slice(ctx, a, 0))
+    ctx.encrypt(y, L, 2, ct_slice(ctx, a, 1))
+    oa, ob = he.encrypt(x, L, 1), he.encrypt(y, L, 2)
+    A, B = ct_slice(ctx, a, 0), ct_slice(ctx, a, 1)
+    for level in (L, 1):
+        out = ctx.empty_ct()
+        ctx.add(A, B, out, 1, level)
+        assert_ct_equal(to_coeff(ctx, out, level)[0], he.add(he.drop(oa, level), he.drop(ob, level)), "add")
+        ctx.sub(A, B, out, 1, level)
+        assert_ct_equal(to_coeff(ctx, out, level)[0], he.sub(he.drop(oa, level), he.drop(ob, level)), "sub")
+        pt = torch.zeros(ctx.n, dtype=torch.int64, device="cuda")
+        zp = _slots(ctx.slots, 7)
+        ctx.encode(zp, pt)
+        ctx.mul_plain(A, pt, out, 1, level)
+        assert_ct_equal(to_coeff(ctx, out, level)[0], he.mul_plain(he.drop(oa, level), he.enc.encode(zp)),
+                        "mul_plain")
+        t3 = ctx.empty_ct(1, parts=3)
+        ctx.tensor(A, B, t3, 1, level)
+        assert_ct_equal(tensor3_to_coeff(ctx, t3, level), he.tensor(he.drop(oa, level), he.drop(ob, level)),
+                        "tensor")
+    # several ciphertexts in one call
+    out2 = ctx.empty_ct(2)
+    ctx.add(a, a, out2, 2, L)
+    got = to_coeff(ctx, out2, L, 2)
+    assert_ct_equal(got[0], he.add(oa, oa), "batched add 0")
+    assert_ct_equal(got[1], he.add(ob, ob), "batched add 1")
+
+
+@pytest.mark.parametrize("preset", ["t10", "t11a2", "tiny", "paper"])
+def test_rescale_relin_mul_bit_exact(preset):
+    ctx = gpu_ctx(preset, SEED)
+    he = oracle_ctx(preset, SEED)
+    L = ctx.top
+    x, y = _slots(ctx.slots, 8), _slots(ctx.slots, 9)
+    a = ctx.empty_ct(2)
+    ctx.encrypt(x, L, 11, ct_slice(ctx, a, 0))
+    ctx.encrypt(y, L, 12, ct_slice(ctx, a, 1))
+    oa, ob = he.encrypt(x, L, 11), he.encrypt(y, L, 12)
+    A, B = ct_slice(ctx, a, 0), ct_slice(ctx, a, 1)
+    levels = [L] if preset == "paper" else sorted({L, 1})
+    for level in levels:
+        out = ctx.empty_ct()
+        ctx.rescale(A, out, 1, level)
+        assert_ct_equal(to_coeff(ctx, out, level - 1)[0], he.rescale(he.drop(oa, level)), "rescale")
+        t3 = ctx.empty_ct(1, parts=3)
+        ctx.tensor(A, B, t3, 1, level)
+        ctx.relinearize(t3, out, 1, level)
+        relin = he.relinearize(he.tensor(he.drop(oa, level), he.drop(ob, level)))
+        assert_ct_equal(to_coeff(ctx, out, level)[0], relin, "relinearize")
+        ctx.mul_relin_rescale(A, B, out, 1, level)
+        prod = he.rescale(relin)
+        assert_ct_equal(to_coeff(ctx, out, level - 1)[0], prod, "mul_relin_rescale")
+        dec = ctx.decrypt(out, level - 1)
+        assert np.abs(dec - x * y).max() < 1e-4
+
+
+@pytest.mark.parametrize("preset,steps", [("t10", [1, -1, 5, 64]), ("t11a2", [3, -8]), ("tiny", [1, -16]),
+                                          ("paper", [32])])
+def test_rotate_bit_exact(preset, steps):
+    ctx = gpu_ctx(preset, SEED, steps)
+    he = oracle_ctx(preset, SEED, steps)
+    L = ctx.top
+    x = _slots(ctx.slots, 10)
+    a = ctx.empty_ct()
+    ctx.encrypt(x, L, 21, a)
+    oa = he.encrypt(x, L, 21)
+    for r in steps:
+        for level in sorted({L, 0 if preset != "paper" else L}):
+            out = ctx.empty_ct()
+            ctx.rotate(a, out, 1, level, r)
+            assert_ct_equal(to_coeff(ctx, out, level)[0], he.rotate(he.drop(oa, level), r), f"rotate {r}")
+        dec = ctx.decrypt(out, level)
+        if level >= 1:
+            assert np.abs(dec - np.roll(x, -r)).max() < 1e-5
+    # rotation by the slot count is the identity and needs no key
+    out = ctx.empty_ct()
+    ctx.rotate(a, out, 1, L, ctx.slots)
+    assert_ct_equal(to_coeff(ctx, out, L)[0], oa, "rotate by N/2")
+
+
+def test_errors_are_reported_and_context_survives():
+    ctx = gpu_ctx("t10", SEED, [1])
+    from paper_2509_03024_gb300.capi import FheError
+    a = ctx.empty_ct()
+    ctx.encrypt(_slots(ctx.slots, 1), ctx.top, 1, a)
+    out = ctx.empty_ct()
+    with pytest.raises(FheError, match="MISSING_KEY"):
+        ctx.rotate(a, out, 1, ctx.top, 2)
+    with pytest.raises(FheError, match="LEVEL_EXHAUSTED"):
+        ctx.rescale(a, out, 1, 0)
+    with pytest.raises(FheError, match="INVALID_ARG"):
+        ctx.add(a, a, out, 1, ctx.top + 1)
+    with pytest.raises(FheError, match="INVALID_ARG"):
+        ctx.rotate(a, a, 1, ctx.top, 1)
+    # still usable
+    ctx.rotate(a, out, 1, ctx.top, 1)
+    assert np.abs(ctx.decrypt(out, ctx.top) - np.roll(_slots(ctx.slots, 1), -1)).max() < 1e-5
