@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput of the encrypted CSR matrix-factorisation epoch on one GB300.
+
+Workload (the paper-scale configuration): 943 users x 1682 items with 100,000
+synthetic ratings shaped like MovieLens-100K (Zipf(1.0) item popularity, >= 20
+ratings per user, MovieLens rating law), a 10 % held-out split, rank k = 10;
+RNS-CKKS with N = 2^15, eight 50-bit data primes, two 60-bit special primes,
+scale 2^50. One step = one encrypted SGD epoch (lr 0.005, lambda 0.02) over the
+90 % training split, starting from top-level encrypted factors (restored from a
+resident copy at the start of each step; the chain holds three epochs).
+
+Metric: training ratings processed per second (whole job over all ranks).
+Multi-GPU runs are independent replicas (one per rank, weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "encrypted MF ratings/sec, served vs one-by-one on 1 GB300; p50/p99 latency"
+UNIT = "ratings/s"
+SEED = 20250903
+LR, LAM, K_RANK = 0.005, 0.02, 10
+WORKLOAD = ("paper-scale encrypted MF epoch: 943 users x 1682 items, 100,000 synthetic MovieLens-shaped "
+            "ratings (90,000 train), k=10; RNS-CKKS N=2^15, 8x50-bit data + 2x60-bit special primes, "
+            "scale 2^50; one SGD epoch (lr 0.005, lambda 0.02) per step")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-kernel-timing", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def start_clocks(device: int):
+    path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+    try:
+        proc = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={CLOCK_FIELDS}",
+                                 "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None, path
+    return proc, path
+
+
+def stop_clocks(proc, path):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax = float(f[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def workload():
+    from paper_2509_03024_gb300 import workloads as W
+    train, test, U, V = W.paper_workload(seed=2)
+    return train, test, U, V
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle baseline
+
+def oracle_sample(train, U, V, groups_sampled: int = 2):
+    """Time the oracle (as it stands) on a bounded sample of the epoch and extrapolate.
+
+    Sample: the per-group work (product, relinearise, rescale, rotate-and-sum,
+    masks, tensors) of `groups_sampled` groups plus one delta-tree rotation; the
+    epoch estimate is per-group time x groups + per-rotation time x 2 x tree
+    nodes + per-relinearisation time x tree nodes. Returns (ratings/s, seconds
+    measured, description)."""
+    from oracle import ckks, mf
+    from paper_2509_03024_gb300.workloads import PRESETS
+    rows, cols, vals = train.triples()
+    he = ckks.Ckks(ckks.Params.from_preset(PRESETS["paper"]))
+    plan = mf.build_plan(train.n, train.m, K_RANK, rows, cols, vals, he.prm.slots)
+    steps = [1 << t for t in range(mf.highest_bit(plan.kp))] + [plan.w]
+    he.keygen(SEED, steps)
+    emf = mf.EncryptedMF(he, plan)
+    top = he.prm.top
+    pick = list(range(0, len(plan.groups), max(1, len(plan.groups) // groups_sampled)))[:groups_sampled]
+    emf.R = [None] * len(plan.groups)
+    for t in pick:
+        emf.R[t] = he.encrypt(mf.rating_slots(plan.groups[t], plan), top, mf.R_NONCE_BASE + t)
+    UD = {g.b: None for g in (plan.groups[t] for t in pick)}
+    for b in UD:
+        UD[b] = he.encrypt(mf.pack_factors(U, plan, b), top, mf.U_NONCE_BASE + b)
+    VDc = {}
+    for t in pick:
+        c = plan.groups[t].c
+        if c not in VDc:
+            VDc[c] = he.encrypt(mf.pack_factors(V, plan, c), top, mf.V_NONCE_BASE + c)
+    t0 = time.perf_counter()
+    for t in pick:
+        g = plan.groups[t]
+        emf.group_terms(t, UD[g.b], VDc[g.c], LR)   # Vr of delta 0 stands in for the rotated copy
+    t_groups = (time.perf_counter() - t0) / len(pick)
+    t1 = time.perf_counter()
+    he.rotate(next(iter(VDc.values())), plan.w)
+    t_rot = time.perf_counter() - t1
+    nodes = sum(len(c) for c in plan.closure)
+    est = t_groups * len(plan.groups) + t_rot * 2 * nodes + t_rot * nodes
+    desc = (f"oracle on {len(pick)} of {len(plan.groups)} groups + 1 rotation at N=2^15, single thread; "
+            f"epoch extrapolated as groups x {t_groups:.2f} s + {3 * nodes} rotation-sized key switches x "
+            f"{t_rot:.2f} s = {est:.0f} s")
+    return rows.size / est, time.perf_counter() - t0, desc
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2509_03024_gb300 import build as B
+    B.build()
+    from paper_2509_03024_gb300 import capi
+    from paper_2509_03024_gb300.workloads import PRESETS
+
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", dev))
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    train, test, U, V = workload()
+    ctx = capi.Context.from_preset(PRESETS["paper"], device=dev)
+    ctx.keygen(SEED + rank, ctx.mf_rotation_steps(K_RANK))
+    plan = capi.MfPlan(ctx, train.n, train.m, K_RANK, train.row_ptr, train.col_idx, train.vals)
+    U0, V0 = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
+    plan.encrypt_factors(0, U, U0)
+    plan.encrypt_factors(1, V, V0)
+    UD, VD = torch.empty_like(U0), torch.empty_like(V0)
+    stream = torch.cuda.Stream(device=dev)
+    ratings = train.nnz
+    top = ctx.top
+
+    def step():
+        with torch.cuda.stream(stream):
+            UD.copy_(U0)
+            VD.copy_(V0)
+        plan.sgd_epoch(UD, VD, top, LR, LAM, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk, clk_path = start_clocks(dev)
+    ctx.profile_begin(time_kernels=not args.no_kernel_timing)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    stats = ctx.profile_end()
+    clocks = stop_clocks(clk, clk_path)
+    barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * ratings * args.steps / (elapsed_ms / 1e3)
+
+    # decrypted accuracy of the last step against the FP64 epoch (sanity, not timed)
+    from oracle import mf as omf
+    rows, cols, vals = train.triples()
+    U1, V1 = omf.mf_epoch_fp64(U, V, rows, cols, vals, LR, LAM)
+    Ud = plan.decrypt_factors(0, UD, top - 2, train.n)
+    Vd = plan.decrypt_factors(1, VD, top - 2, train.m)
+    err = max(float(np.abs(Ud - U1).max()), float(np.abs(Vd - V1).max()))
+    trow, tcol, tval = test.triples()
+    rmse_gap = abs(omf.rmse(Ud, Vd, trow, tcol, tval) - omf.rmse(U1, V1, trow, tcol, tval))
+
+    # end to end through the C ABI with host buffers: H2D of the encrypted factors, epoch, D2H
+    hU = torch.empty(U0.numel(), dtype=torch.int64, pin_memory=True)
+    hV = torch.empty(V0.numel(), dtype=torch.int64, pin_memory=True)
+    hU.copy_(U0.cpu())
+    hV.copy_(V0.cpu())
+    oU = torch.empty_like(hU, pin_memory=True)
+    oV = torch.empty_like(hV, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        with torch.cuda.stream(stream):
+            UD.copy_(hU, non_blocking=True)
+            VD.copy_(hV, non_blocking=True)
+        plan.sgd_epoch(UD, VD, top, LR, LAM, stream)
+        with torch.cuda.stream(stream):
+            oU.copy_(UD, non_blocking=True)
+            oV.copy_(VD, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    bytes_h2d = (hU.numel() + hV.numel()) * 8
+    e2e = {"value": world * ratings * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d}
+
+    # roofline of the dominant kernel class (longest summed device time)
+    peaks = measured_peaks()
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    name, (launches, dev_ms, alg_bytes) = dom
+    achieved = (alg_bytes / launches) / ((dev_ms / launches) / 1e3) / 1e9 if dev_ms > 0 else None
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak if achieved else None, "traffic": None,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                "launches": launches, "avg_launch_us": 1e3 * dev_ms / launches if launches else None,
+                "alg_bytes_per_launch": alg_bytes / launches if launches else None,
+                "share_of_timed_device_time": dev_ms / sum(v[1] for v in stats.values())}
+    gpu_launches = sum(v[0] for v in stats.values())
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "ratings_per_step": ratings, "parallelism": "replicas",
+                      "l2": "inputs larger than L2 (rating ciphertexts alone are ~16 GiB)",
+                      "groups": int(plan.info.n_groups), "tree_nodes": int(plan.info.n_tree_nodes),
+                      "plan_device_gib": plan.info.device_bytes / 2 ** 30},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
+           "accuracy": {"max_abs_vs_fp64": err, "rmse_gap_test": rmse_gap},
+           "kernels": {k: {"launches": v[0], "device_ms": round(v[1], 3), "alg_gb": round(v[2] / 1e9, 3)}
+                       for k, v in stats.items() if v[0]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rps, secs, desc = oracle_sample(train, U, V)
+        out["cpu_baseline"] = {"value": rps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                               "measured_s": round(secs, 1)}
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args, rank, world):
+    """The oracle (CPU, as it stands) on the same workload and metric; rank 0 only."""
+    if rank != 0:
+        return None
+    train, test, U, V = workload()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        rps, secs, desc = oracle_sample(train, U, V, groups_sampled=1)
+        if i >= args.warmup:
+            vals.append(rps)
+    v = statistics.median(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

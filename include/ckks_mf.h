@@ -160,6 +160,25 @@ int fhe_rescale(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, 
 int fhe_rotate(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, int32_t level,
                int32_t step, void* stream);
 
+/* ------------------------------------------------------------------ launch accounting */
+
+/* Per kernel class: launches, summed device time (only when timing was
+ * requested) and the algorithmic bytes those launches must move (inputs read
+ * once plus outputs written once). `name` points to a static string. */
+typedef struct {
+    const char* name;
+    int64_t launches;
+    double device_ms;
+    double bytes;
+} fhe_kernel_stat;
+
+/* Reset the counters. With time_kernels != 0 every launch is also bracketed
+ * by CUDA events on its stream (small overhead per launch). */
+int fhe_profile_begin(fhe_ctx* ctx, int32_t time_kernels);
+/* Synchronise the device, write up to cap class records to host `out`, stop
+ * timing. Returns the number of classes (>= 0) or an error code. */
+int fhe_profile_end(fhe_ctx* ctx, fhe_kernel_stat* out, int32_t cap);
+
 /* ------------------------------------------------------------------ encrypted CSR matrix factorisation */
 
 typedef struct {

@@ -29,7 +29,7 @@ EXPORTS = [
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale",
-    "fhe_rotate", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
+    "fhe_rotate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict",
 ]
@@ -52,6 +52,11 @@ class CtxInfo(ctypes.Structure):
     _fields_ = [("log_n", ctypes.c_int32), ("n", ctypes.c_int32), ("slots", ctypes.c_int32),
                 ("top_level", ctypes.c_int32), ("n_special", ctypes.c_int32), ("log_scale", ctypes.c_int32),
                 ("ct_words", ctypes.c_size_t)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("device_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -97,6 +102,8 @@ def lib() -> ctypes.CDLL:
             "fhe_relinearize": [vp, vp, vp, i32, i32, vp],
             "fhe_rescale": [vp, vp, vp, i32, i32, vp],
             "fhe_rotate": [vp, vp, vp, i32, i32, i32, vp],
+            "fhe_profile_begin": [vp, i32],
+            "fhe_profile_end": [vp, vp, i32],
             "fhe_mf_rotation_steps": [vp, i32, vp, sz],
             "fhe_csr_pack": [vp, i32, i32, i32, vp, vp, vp, ctypes.POINTER(vp)],
             "fhe_mf_plan_destroy": [vp],
@@ -251,6 +258,19 @@ class Context:
 
     def rotate(self, ct, out, count: int, level: int, step: int, stream=None):
         self._check(lib().fhe_rotate(self.h, _ptr(ct), _ptr(out), count, level, step, _stream(stream)))
+
+    # ---- launch accounting
+    def profile_begin(self, time_kernels: bool = False):
+        self._check(lib().fhe_profile_begin(self.h, 1 if time_kernels else 0))
+
+    def profile_end(self):
+        """-> {class name: (launches, device_ms, algorithmic_bytes)}"""
+        arr = (KernelStat * 32)()
+        rc = lib().fhe_profile_end(self.h, ctypes.cast(arr, ctypes.c_void_p), 32)
+        if rc < 0:
+            self._check(rc)
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].device_ms), float(arr[i].bytes))
+                for i in range(rc)}
 
     # ---- matrix factorisation
     def mf_rotation_steps(self, k: int):

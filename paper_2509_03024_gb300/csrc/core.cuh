@@ -166,6 +166,53 @@ struct Arena {
     ~Arena();
 };
 
+// ----------------------------------------------------------------------------- launch accounting
+
+// Kernel classes for launch counting and optional per-launch CUDA-event timing.
+enum KClass {
+    K_NTT_FWD = 0,
+    K_NTT_INV,
+    K_KS_GATHER,
+    K_MODUP,
+    K_KS_INNER,
+    K_MODDOWN,
+    K_KS_FINAL,
+    K_RESCALE,
+    K_TENSOR,
+    K_ELEMENTWISE,
+    K_ENCODE,
+    K_OTHER,
+    K_COUNT
+};
+extern const char* const kKClassNames[K_COUNT];
+
+struct Profiler {
+    bool timing = false;
+    long long launches[K_COUNT] = {};
+    double bytes[K_COUNT] = {};
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    cudaEvent_t get_event();
+    void reset();
+    ~Profiler();
+};
+
+// RAII scope around one kernel launch: counts it, adds its algorithmic bytes
+// and, when timing is on, brackets it with CUDA events on its stream.
+struct LaunchScope {
+    Profiler& p;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t b = nullptr;
+    LaunchScope(Profiler& prof, int k, double bytes, cudaStream_t st);
+    ~LaunchScope();
+};
+
 // ----------------------------------------------------------------------------- context
 
 struct DeviceBuf {
@@ -217,6 +264,7 @@ struct Ctx {
 
     std::string last_error;
     Arena arena;
+    mutable Profiler prof;
 
     size_t ct_words() const { return (size_t)2 * (L + 1) * n; }
     size_t key_words() const { return (size_t)dnum(L) * 2 * n_ext * n; }

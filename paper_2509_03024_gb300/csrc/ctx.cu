@@ -530,9 +530,12 @@ void encode_many_device(Ctx& c, const std::vector<int>& idx, const std::vector<d
     for (int v0 = 0; v0 < count; v0 += 65535) {
         int cnt = std::min(65535, count - v0);
         dim3 grid((c.n + 255) / 256, cnt);
-        encode_kernel<<<grid, 256, 0, s>>>(out_dev + (size_t)v0 * c.n, d_idx, d_val, d_off + v0, c.d_cos,
-                                           c.d_pow5, c.log_n, factor);
-        CK(cudaGetLastError());
+        {
+            LaunchScope _ls(c.prof, K_ENCODE, 8.0 * cnt * c.n + 12.0 * nz, s);
+            encode_kernel<<<grid, 256, 0, s>>>(out_dev + (size_t)v0 * c.n, d_idx, d_val, d_off + v0, c.d_cos,
+                                               c.d_pow5, c.log_n, factor);
+            CK(cudaGetLastError());
+        }
     }
     // the host vectors may be released once the copies have been consumed
     CK(cudaStreamSynchronize(s));
@@ -592,16 +595,22 @@ void encrypt_coeffs_device(Ctx& c, const i64* m_dev, size_t m_stride, int count,
         k_int8_to_rns(c, c0, st, d_small + n, (size_t)3 * n, cnt, l1, 1 << 30, 0, s);
         k_int8_to_rns(c, c1, st, d_small + 2 * n, (size_t)3 * n, cnt, l1, 1 << 30, 0, s);
         k_int_to_rns(c, mm, st, m_dev + (size_t)t0 * m_stride, m_stride, cnt, l1, s);
-        add_compact_kernel<<<blocks_for((size_t)cnt * st), kT, 0, s>>>(c0, mm, (size_t)cnt * st, l1,
-                                                                       c.log_n, c.d_primes);
-        CK(cudaGetLastError());
+        {
+            LaunchScope _ls(c.prof, K_ELEMENTWISE, 24.0 * cnt * st, s);
+            add_compact_kernel<<<blocks_for((size_t)cnt * st), kT, 0, s>>>(c0, mm, (size_t)cnt * st, l1,
+                                                                           c.log_n, c.d_primes);
+            CK(cudaGetLastError());
+        }
         ntt_forward(c, poly_batch(v, st, 0, cnt, 1, 0, l1), s);
         ntt_forward(c, poly_batch(c0, st, 0, cnt, 1, 0, l1), s);
         ntt_forward(c, poly_batch(c1, st, 0, cnt, 1, 0, l1), s);
-        enc_combine_kernel<<<blocks_for((size_t)cnt * st), kT, 0, s>>>(
-            ct + (size_t)t0 * c.ct_words(), c.ct_words(), (size_t)(c.L + 1) * n, v, c0, c1, c.d_pk,
-            c.d_pk + (size_t)(c.L + 1) * n, cnt, l1, c.log_n, c.d_primes);
-        CK(cudaGetLastError());
+        {
+            LaunchScope _ls(c.prof, K_ELEMENTWISE, 56.0 * cnt * st, s);
+            enc_combine_kernel<<<blocks_for((size_t)cnt * st), kT, 0, s>>>(
+                ct + (size_t)t0 * c.ct_words(), c.ct_words(), (size_t)(c.L + 1) * n, v, c0, c1, c.d_pk,
+                c.d_pk + (size_t)(c.L + 1) * n, cnt, l1, c.log_n, c.d_primes);
+            CK(cudaGetLastError());
+        }
         CK(cudaStreamSynchronize(s));  // `host` is refilled by the next chunk
     }
 }
@@ -615,18 +624,27 @@ void decrypt_to_slots(Ctx& c, const u64* ct, int level, double* host_slots, size
     u64* m = c.scratch_u64("dec_m", (size_t)nl * n);
     double* md = (double*)c.scratch_bytes("dec_md", sizeof(double) * n);
     double* z = (double*)c.scratch_bytes("dec_z", sizeof(double) * (n_slots + 1));
-    dec_kernel<<<blocks_for((size_t)nl * n), kT, 0, s>>>(m, ct, (size_t)(c.L + 1) * n, c.d_sk, nl, c.log_n,
-                                                         c.d_primes);
-    CK(cudaGetLastError());
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 32.0 * nl * n, s);
+        dec_kernel<<<blocks_for((size_t)nl * n), kT, 0, s>>>(m, ct, (size_t)(c.L + 1) * n, c.d_sk, nl, c.log_n,
+                                                             c.d_primes);
+        CK(cudaGetLastError());
+    }
     ntt_inverse(c, poly_batch(m, (size_t)nl * n, 0, 1, 1, 0, nl), s);
     u64 q0 = c.primes[0], q1 = c.primes[1 % (c.L + 1)];
     u64 q0i = nl == 2 ? h_inv(q0 % q1, q1) : 0;
-    crt_kernel<<<blocks_for(n), kT, 0, s>>>(md, m, nl, c.log_n, q0, q1, q0i);
-    CK(cudaGetLastError());
-    if (n_slots) {
-        decode_kernel<<<(unsigned)n_slots, 256, 0, s>>>(z, md, c.d_cos, c.d_pow5, c.log_n,
-                                                        std::ldexp(1.0, -c.log_scale), (int)n_slots);
+    {
+        LaunchScope _ls(c.prof, K_ENCODE, 8.0 * (nl + 1) * n, s);
+        crt_kernel<<<blocks_for(n), kT, 0, s>>>(md, m, nl, c.log_n, q0, q1, q0i);
         CK(cudaGetLastError());
+    }
+    if (n_slots) {
+        {
+            LaunchScope _ls(c.prof, K_ENCODE, 8.0 * (n + n_slots), s);
+            decode_kernel<<<(unsigned)n_slots, 256, 0, s>>>(z, md, c.d_cos, c.d_pow5, c.log_n,
+                                                            std::ldexp(1.0, -c.log_scale), (int)n_slots);
+            CK(cudaGetLastError());
+        }
         CK(cudaMemcpyAsync(host_slots, z, sizeof(double) * n_slots, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -652,9 +670,12 @@ static void make_evk(Ctx& c, EvalKey& key, const u64* d_s2, u64 obj, cudaStream_
         k_int8_to_rns(c, d_e, 0, d_e8, 0, 1, ne, 1 << 30, 0, s);
         ntt_forward(c, poly_batch(d_e, 0, 0, 1, 1, 0, ne), s);
         int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, c.L + 1);
-        evk_kernel<<<blocks_for((size_t)ne * n), kT, 0, s>>>(kb, ka, c.d_sk, d_e, d_s2, ne, c.L, lo, hi,
-                                                             c.log_n, c.d_primes, c.d_pmod);
-        CK(cudaGetLastError());
+        {
+            LaunchScope _ls(c.prof, K_OTHER, 40.0 * ne * n, s);
+            evk_kernel<<<blocks_for((size_t)ne * n), kT, 0, s>>>(kb, ka, c.d_sk, d_e, d_s2, ne, c.L, lo, hi,
+                                                                 c.log_n, c.d_primes, c.d_pmod);
+            CK(cudaGetLastError());
+        }
         CK(cudaStreamSynchronize(s));  // host staging buffers are reused
     }
 }
@@ -698,13 +719,19 @@ static void keygen(Ctx& c, u64 seed, const int32_t* steps, size_t n_steps, cudaS
     u64* de = c.scratch_u64("kg_e", (size_t)ne * n);
     k_int8_to_rns(c, de, 0, de8, 0, 1, l1, 1 << 30, 0, s);
     ntt_forward(c, poly_batch(de, 0, 0, 1, 1, 0, l1), s);
-    pk_kernel<<<blocks_for((size_t)l1 * n), kT, 0, s>>>(c.d_pk, pk1, c.d_sk, de, l1, c.log_n, c.d_primes);
-    CK(cudaGetLastError());
+    {
+        LaunchScope _ls(c.prof, K_OTHER, 32.0 * l1 * n, s);
+        pk_kernel<<<blocks_for((size_t)l1 * n), kT, 0, s>>>(c.d_pk, pk1, c.d_sk, de, l1, c.log_n, c.d_primes);
+        CK(cudaGetLastError());
+    }
     CK(cudaStreamSynchronize(s));
     // relinearisation key for s^2
     u64* s2 = c.scratch_u64("kg_s2", (size_t)ne * n);
-    square_kernel<<<blocks_for((size_t)ne * n), kT, 0, s>>>(s2, c.d_sk, ne, c.log_n, c.d_primes);
-    CK(cudaGetLastError());
+    {
+        LaunchScope _ls(c.prof, K_OTHER, 16.0 * ne * n, s);
+        square_kernel<<<blocks_for((size_t)ne * n), kT, 0, s>>>(s2, c.d_sk, ne, c.log_n, c.d_primes);
+        CK(cudaGetLastError());
+    }
     make_evk(c, c.rlk, s2, 0, s);
     c.have_keys = true;
     for (size_t i = 0; i < n_steps; i++) add_rotation_key(c, steps[i], s);
@@ -1077,6 +1104,41 @@ int fhe_rotate(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, i
         }
         keyswitch_items(c, ks, level, S(stream));
     });
+}
+
+int fhe_profile_begin(fhe_ctx* ctx, int32_t time_kernels) {
+    return guarded(ctx, [&] {
+        check_ptr(ctx, "ctx");
+        CK(cudaDeviceSynchronize());
+        ctx->c.prof.reset();
+        ctx->c.prof.timing = time_kernels != 0;
+    });
+}
+
+int fhe_profile_end(fhe_ctx* ctx, fhe_kernel_stat* out, int32_t cap) {
+    int rc = guarded(ctx, [&] {
+        check_ptr(ctx, "ctx");
+        check_ptr(out, "out");
+        if (cap < K_COUNT) fail(FHE_ERR_INVALID_ARG, "cap must be at least the number of kernel classes");
+        CK(cudaDeviceSynchronize());
+        Profiler& p = ctx->c.prof;
+        double ms[K_COUNT] = {};
+        for (auto& r : p.recs) {
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, r.a, r.b));
+            ms[r.cls] += t;
+        }
+        for (int k = 0; k < K_COUNT; k++) {
+            out[k].name = kKClassNames[k];
+            out[k].launches = p.launches[k];
+            out[k].device_ms = ms[k];
+            out[k].bytes = p.bytes[k];
+        }
+        p.timing = false;
+        p.recs.clear();
+        p.pool_used = 0;
+    });
+    return rc ? rc : (int)K_COUNT;
 }
 
 }  // extern "C"

@@ -176,7 +176,10 @@ void run_ntt(const Ctx& c, const PolyBatch& pb, cudaStream_t s) {
     const u64* tw = INV ? c.d_ipsi : c.d_psi;
     const u64* tws = INV ? c.d_ipsi_s : c.d_psi_s;
     const int log_n = c.log_n;
+    const double bytes = 16.0 * rows * ((size_t)1 << log_n);
+    const int cls = INV ? K_NTT_INV : K_NTT_FWD;
     if (log_n <= 14) {
+        LaunchScope _ls(c.prof, cls, bytes, s);
         size_t smem = sizeof(u64) << log_n;
         int threads = log_n >= 12 ? 512 : (1 << (log_n - 1));
         ntt_col_kernel<INV><<<dim3(rows, 1), threads, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv,
@@ -193,17 +196,27 @@ void run_ntt(const Ctx& c, const PolyBatch& pb, cudaStream_t s) {
     dim3 gcol(rows, 1 << (log_n2 - log_cols));
     dim3 grow(rows, 1 << (S1 - log_rows));
     if (!INV) {
-        ntt_col_kernel<false><<<gcol, 256, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv, log_n, S1,
-                                                      log_cols);
-        CK(cudaGetLastError());
-        ntt_row_kernel<false><<<grow, 256, smem, s>>>(pb, c.d_primes, tw, tws, log_n, S1, log_rows);
-        CK(cudaGetLastError());
+        {
+            LaunchScope _ls(c.prof, cls, bytes, s);
+            ntt_col_kernel<false><<<gcol, 256, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv, log_n, S1, log_cols);
+            CK(cudaGetLastError());
+        }
+        {
+            LaunchScope _ls(c.prof, cls, bytes, s);
+            ntt_row_kernel<false><<<grow, 256, smem, s>>>(pb, c.d_primes, tw, tws, log_n, S1, log_rows);
+            CK(cudaGetLastError());
+        }
     } else {
-        ntt_row_kernel<true><<<grow, 256, smem, s>>>(pb, c.d_primes, tw, tws, log_n, S1, log_rows);
-        CK(cudaGetLastError());
-        ntt_col_kernel<true><<<gcol, 256, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv, log_n, S1,
-                                                     log_cols);
-        CK(cudaGetLastError());
+        {
+            LaunchScope _ls(c.prof, cls, bytes, s);
+            ntt_row_kernel<true><<<grow, 256, smem, s>>>(pb, c.d_primes, tw, tws, log_n, S1, log_rows);
+            CK(cudaGetLastError());
+        }
+        {
+            LaunchScope _ls(c.prof, cls, bytes, s);
+            ntt_col_kernel<true><<<gcol, 256, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv, log_n, S1, log_cols);
+            CK(cudaGetLastError());
+        }
     }
 }
 

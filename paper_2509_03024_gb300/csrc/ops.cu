@@ -50,6 +50,51 @@ Arena::~Arena() {
     }
 }
 
+// ============================================================================ launch accounting
+
+const char* const kKClassNames[K_COUNT] = {"ntt_forward", "ntt_inverse", "ks_gather", "modup", "ks_inner",
+                                           "moddown",     "ks_final",    "rescale",   "tensor", "elementwise",
+                                           "encode",      "other"};
+
+cudaEvent_t Profiler::get_event() {
+    if (pool_used == pool.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        pool.push_back(e);
+    }
+    return pool[pool_used++];
+}
+
+void Profiler::reset() {
+    for (int k = 0; k < K_COUNT; k++) {
+        launches[k] = 0;
+        bytes[k] = 0;
+    }
+    recs.clear();
+    pool_used = 0;
+}
+
+Profiler::~Profiler() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+LaunchScope::LaunchScope(Profiler& prof, int k, double nbytes, cudaStream_t st) : p(prof), cls(k), s(st) {
+    p.launches[k]++;
+    p.bytes[k] += nbytes;
+    if (p.timing) {
+        b = p.get_event();
+        CK(cudaEventRecord(b, s));
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (b) {
+        cudaEvent_t e = p.get_event();
+        cudaEventRecord(e, s);
+        p.recs.push_back({cls, b, e});
+    }
+}
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -465,37 +510,49 @@ void items_add(Ctx& c, const std::vector<BinItem>& it, int parts, int limbs, boo
     if (it.empty()) return;
     const BinItem* d = upload(c, it, s);
     size_t per = (size_t)parts * limbs * c.n / 2;
-    add_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 3.0 * 8 * per * 2 * it.size(), s);
+        add_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs, c.log_n,
                                                                      (size_t)(c.L + 1) * c.n, c.d_primes, sub);
     CK(cudaGetLastError());
+    }
 }
 
 void items_copy(Ctx& c, const std::vector<UnItem>& it, int parts, int limbs, cudaStream_t s) {
     if (it.empty()) return;
     const UnItem* d = upload(c, it, s);
     size_t per = (size_t)parts * limbs * c.n / 2;
-    copy_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 2.0 * 8 * per * 2 * it.size(), s);
+        copy_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs, c.log_n,
                                                                       (size_t)(c.L + 1) * c.n);
     CK(cudaGetLastError());
+    }
 }
 
 void items_mul_plain(Ctx& c, const std::vector<BinItem>& it, int parts, int limbs, cudaStream_t s) {
     if (it.empty()) return;
     const BinItem* d = upload(c, it, s);
     size_t per = (size_t)parts * limbs * c.n / 2;
-    mul_plain_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs,
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 2.5 * 8 * per * 2 * it.size(), s);
+        mul_plain_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs,
                                                                            c.log_n, (size_t)(c.L + 1) * c.n,
                                                                            c.d_primes);
     CK(cudaGetLastError());
+    }
 }
 
 void items_tensor(Ctx& c, const std::vector<BinItem>& it, int limbs, cudaStream_t s) {
     if (it.empty()) return;
     const BinItem* d = upload(c, it, s);
     size_t per = (size_t)limbs * c.n / 2;
-    tensor_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), limbs, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_TENSOR, 7.0 * 8 * per * 2 * it.size(), s);
+        tensor_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), limbs, c.log_n,
                                                                         (size_t)(c.L + 1) * c.n, c.d_primes);
     CK(cudaGetLastError());
+    }
 }
 
 void items_tensor_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<BinItem>& contrib, int limbs,
@@ -504,9 +561,12 @@ void items_tensor_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vecto
     const AccTarget* dt = upload(c, tg, s);
     const BinItem* dc = upload(c, contrib, s);
     size_t per = (size_t)limbs * c.n / 2;
-    tensor_acc_kernel<<<grid2(per, (int)tg.size()), kThreads, 0, s>>>(dt, dc, (int)tg.size(), limbs, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_TENSOR, 8.0 * per * 2 * (4.0 * contrib.size() + 6.0 * tg.size()), s);
+        tensor_acc_kernel<<<grid2(per, (int)tg.size()), kThreads, 0, s>>>(dt, dc, (int)tg.size(), limbs, c.log_n,
                                                                       (size_t)(c.L + 1) * c.n, c.d_primes);
     CK(cudaGetLastError());
+    }
 }
 
 void items_sum_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<BinItem>& contrib, int parts,
@@ -515,9 +575,12 @@ void items_sum_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<B
     const AccTarget* dt = upload(c, tg, s);
     const BinItem* dc = upload(c, contrib, s);
     size_t per = (size_t)parts * limbs * c.n / 2;
-    sum_acc_kernel<<<grid2(per, (int)tg.size()), kThreads, 0, s>>>(dt, dc, (int)tg.size(), parts, limbs, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 8.0 * per * 2 * (contrib.size() + 2.0 * tg.size()), s);
+        sum_acc_kernel<<<grid2(per, (int)tg.size()), kThreads, 0, s>>>(dt, dc, (int)tg.size(), parts, limbs, c.log_n,
                                                                    (size_t)(c.L + 1) * c.n, c.d_primes);
     CK(cudaGetLastError());
+    }
 }
 
 void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s) {
@@ -528,39 +591,57 @@ void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, 
     const UnItem* d = upload(c, it, s);
     u64* last = c.scratch_u64("resc_last", (size_t)rows * n);
     u64* spread = c.scratch_u64("resc_spread", (size_t)rows * level * n);
-    gather_last_kernel<<<grid2((size_t)parts * n, items), kThreads, 0, s>>>(last, d, items, parts, level, c.log_n, pw);
+    {
+        LaunchScope _ls(c.prof, K_RESCALE, 16.0 * rows * n, s);
+        gather_last_kernel<<<grid2((size_t)parts * n, items), kThreads, 0, s>>>(last, d, items, parts, level, c.log_n, pw);
     CK(cudaGetLastError());
+    }
     ntt_inverse(c, poly_batch(last, n, 0, rows, 1, level, 1, level), s);
-    rescale_spread_kernel<<<grid1((size_t)rows * n), kThreads, 0, s>>>(spread, last, rows, level, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_RESCALE, 8.0 * rows * n * (1 + level), s);
+        rescale_spread_kernel<<<grid1((size_t)rows * n), kThreads, 0, s>>>(spread, last, rows, level, c.log_n,
                                                                        c.d_primes);
     CK(cudaGetLastError());
+    }
     ntt_forward(c, poly_batch(spread, (size_t)level * n, 0, rows, 1, 0, level), s);
-    rescale_combine_kernel<<<grid2((size_t)parts * level * n / 2, items), kThreads, 0, s>>>(
+    {
+        LaunchScope _ls(c.prof, K_RESCALE, 24.0 * rows * level * n, s);
+        rescale_combine_kernel<<<grid2((size_t)parts * level * n / 2, items), kThreads, 0, s>>>(
         d, spread, items, parts, level, c.log_n, pw, c.d_primes, c.d_resc + (size_t)2 * level * (c.L + 1));
     CK(cudaGetLastError());
+    }
 }
 
 void k_int_to_rns(const Ctx& c, u64* out, size_t out_item_stride, const i64* in, size_t in_stride, int items,
                   int limbs, cudaStream_t s) {
     size_t work = (size_t)items * limbs * c.n;
     if (!work) return;
-    int_to_rns_kernel<<<grid1(work), kThreads, 0, s>>>(out, out_item_stride, in, in_stride, items, limbs, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 8.0 * items * c.n + 8.0 * work, s);
+        int_to_rns_kernel<<<grid1(work), kThreads, 0, s>>>(out, out_item_stride, in, in_stride, items, limbs, c.log_n,
                                                        c.d_primes);
     CK(cudaGetLastError());
+    }
 }
 
 void k_int8_to_rns(const Ctx& c, u64* out, size_t out_item_stride, const int8_t* in, size_t in_stride, int items,
                    int limbs, int prime_split, int prime_jump, cudaStream_t s) {
     size_t work = (size_t)items * limbs * c.n;
     if (!work) return;
-    int8_to_rns_kernel<<<grid1(work), kThreads, 0, s>>>(out, out_item_stride, in, in_stride, items, limbs, c.log_n,
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 1.0 * items * c.n + 8.0 * work, s);
+        int8_to_rns_kernel<<<grid1(work), kThreads, 0, s>>>(out, out_item_stride, in, in_stride, items, limbs, c.log_n,
                                                         prime_split, prime_jump, c.d_primes);
     CK(cudaGetLastError());
+    }
 }
 
 void k_automorphism_poly(const Ctx& c, u64* out, const u64* in, int limbs, int galois, cudaStream_t s) {
-    automorphism_kernel<<<grid1((size_t)limbs * c.n), kThreads, 0, s>>>(out, in, limbs, c.log_n, galois);
+    {
+        LaunchScope _ls(c.prof, K_OTHER, 16.0 * limbs * c.n, s);
+        automorphism_kernel<<<grid1((size_t)limbs * c.n), kThreads, 0, s>>>(out, in, limbs, c.log_n, galois);
     CK(cudaGetLastError());
+    }
 }
 
 void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
@@ -569,42 +650,64 @@ void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStre
     const int n = c.n, l1 = level + 1, next = l1 + c.alpha, dn = c.dnum(level);
     // bound the ModUp expansion buffer to ~2 GiB per sub-batch
     const size_t per_item = (size_t)(dn * next + 2 * next + 2 * l1 + l1) * n * sizeof(u64);
-    const int max_items = (int)std::max<size_t>(1, ((size_t)2 << 30) / per_item);
+    const int max_items = (int)std::max<size_t>(1, ((size_t)6 << 30) / per_item);
     for (size_t b0 = 0; b0 < all.size(); b0 += max_items) {
         const int items = (int)std::min<size_t>(max_items, all.size() - b0);
         std::vector<KsItem> it(all.begin() + b0, all.begin() + b0 + items);
         const KsItem* d = upload(c, it, s);
+        size_t nkeys = 0;
+        {
+            std::vector<const u64*> ks;
+            for (auto& x : it) ks.push_back(x.key);
+            std::sort(ks.begin(), ks.end());
+            nkeys = std::unique(ks.begin(), ks.end()) - ks.begin();
+        }
         u64* coef = c.scratch_u64("ks_coef", (size_t)items * l1 * n);
         u64* ext = c.scratch_u64("ks_ext", (size_t)items * dn * next * n);
         u64* acc = c.scratch_u64("ks_acc", (size_t)items * 2 * next * n);
         u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
+        {
+        LaunchScope _ls(c.prof, K_KS_GATHER, 16.0 * items * l1 * n, s);
         ks_gather_kernel<<<grid2((size_t)l1 * n, items), kThreads, 0, s>>>(coef, d, items, l1, c.log_n);
         CK(cudaGetLastError());
+    }
         ntt_inverse(c, poly_batch(coef, (size_t)l1 * n, 0, items, 1, 0, l1), s);
+        {
+        LaunchScope _ls(c.prof, K_MODUP, 8.0 * items * n * (l1 + (double)dn * next), s);
         modup_kernel<<<grid1((size_t)items * dn * n), kThreads, 0, s>>>(ext, coef, items, level, dn, c.alpha, next,
                                                                         c.L, c.log_n, c.d_primes, c.d_up_inv,
                                                                         c.d_up_hat, c.n_ext);
         CK(cudaGetLastError());
+    }
         PolyBatch pe = poly_batch(ext, (size_t)dn * next * n, (size_t)next * n, items, dn, 0, next);
         pe.split = l1;
         pe.jump = c.L - level;
         ntt_forward(c, pe, s);
+        {
+        LaunchScope _ls(c.prof, K_KS_INNER, 8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next), s);
         ks_inner_kernel<<<grid1((size_t)items * next * n / 2), kThreads, 0, s>>>(acc, ext, d, items, dn, next,
                                                                                  level, c.L, c.n_ext, c.log_n,
                                                                                  c.d_primes);
         CK(cudaGetLastError());
+    }
         PolyBatch pa = poly_batch(acc, (size_t)2 * next * n, (size_t)next * n, items, 2, l1, c.alpha);
         pa.split = l1;
         pa.jump = c.L - level;
         ntt_inverse(c, pa, s);
+        {
+        LaunchScope _ls(c.prof, K_MODDOWN, 8.0 * items * 2 * n * (c.alpha + l1), s);
         moddown_kernel<<<grid1((size_t)items * 2 * n), kThreads, 0, s>>>(conv, acc, items, level, c.alpha, next,
                                                                          c.L, c.log_n, c.d_primes, c.d_down_inv,
                                                                          c.d_down_hat);
         CK(cudaGetLastError());
+    }
         ntt_forward(c, poly_batch(conv, (size_t)2 * l1 * n, (size_t)l1 * n, items, 2, 0, l1), s);
+        {
+        LaunchScope _ls(c.prof, K_KS_FINAL, 8.0 * items * 2 * l1 * n * 3, s);
         ks_final_kernel<<<grid2((size_t)2 * l1 * n, items), kThreads, 0, s>>>(d, acc, conv, items, level, next,
                                                                               c.log_n, c.d_primes, c.d_pinv);
         CK(cudaGetLastError());
+    }
     }
 }
 
