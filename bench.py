@@ -231,6 +231,14 @@ def run_gpu(args, rank, world, local_rank):
     rmse_gap = abs(omf.rmse(Ud, Vd, trow, tcol, tval) - omf.rmse(U1, V1, trow, tcol, tval))
 
     # end to end through the C ABI with host buffers: H2D of the encrypted factors, epoch, D2H
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier)
+    return finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
+                  train, U, V, dist)
+
+
+def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier):
     hU = torch.empty(U0.numel(), dtype=torch.int64, pin_memory=True)
     hV = torch.empty(V0.numel(), dtype=torch.int64, pin_memory=True)
     hU.copy_(U0.cpu())
@@ -257,9 +265,12 @@ def run_gpu(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     bytes_h2d = (hU.numel() + hV.numel()) * 8
-    e2e = {"value": world * ratings * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d}
+    return {"value": world * ratings * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d}
 
+
+def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
+           train, U, V, dist):
     # roofline of the dominant kernel class (longest summed device time)
     peaks = measured_peaks()
     dom = max(stats.items(), key=lambda kv: kv[1][1])

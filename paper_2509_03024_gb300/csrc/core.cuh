@@ -238,6 +238,15 @@ struct Ctx {
     u64* d_ipsi = nullptr;            // [n_ext][N]  psi^-brev(i)  (inverse twiddles)
     u64* d_ipsi_s = nullptr;
     u64* d_ninv = nullptr;            // [n_ext][2] N^-1 and its Shoup companion
+    // NTT twiddles interleaved with their Shoup companions (one 128-bit load each):
+    // column / single-pass tables [prime][i] = (psi^brev(i), companion), inverse alike;
+    // row-pass tables of the two-pass NTT laid out [prime][stage s'][group g][row r]
+    // (value = psi^brev(2^(S1+s') + r 2^s' + g)), so that consecutive rows are contiguous
+    ulonglong2* d_tw = nullptr;
+    ulonglong2* d_itw = nullptr;
+    ulonglong2* d_tw2 = nullptr;
+    ulonglong2* d_itw2 = nullptr;
+    int ntt_s1 = 0;                   // column stages of the two-pass NTT (0: single pass)
     u64* d_resc = nullptr;            // [L+1][L+1][2] q_l^-1 mod q_i (+ Shoup)
     u64* d_up_inv = nullptr;          // [L+1][L+1][2] digit-local qhat_i^-1 mod q_i at level l
     u64* d_up_hat = nullptr;          // [L+1][L+1][n_ext][2] digit-local qhat_i mod prime t at level l

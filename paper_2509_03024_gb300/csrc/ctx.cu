@@ -63,7 +63,7 @@ u64* Ctx::scratch_u64(const std::string& name, size_t words) {
 Ctx::~Ctx() {
     cudaSetDevice(device);
     cudaDeviceSynchronize();
-    void* bufs[] = {d_primes, d_psi, d_psi_s, d_ipsi, d_ipsi_s, d_ninv, d_resc, d_up_inv, d_up_hat,
+    void* bufs[] = {d_primes, d_psi, d_psi_s, d_ipsi, d_ipsi_s, d_ninv, d_tw, d_itw, d_tw2, d_itw2, d_resc, d_up_inv, d_up_hat,
                     d_down_inv, d_down_hat, d_pinv, d_pmod, d_cos, d_sin, d_pow5, d_sk, d_pk, rlk.d};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -257,6 +257,32 @@ static void build_tables(Ctx& c) {
     c.d_ipsi = dupload(ipsi);
     c.d_ipsi_s = dupload(ipsi_s);
     c.d_ninv = dupload(ninv);
+    std::vector<ulonglong2> tw((size_t)ne * n), itw(tw.size());
+    for (size_t i = 0; i < tw.size(); i++) {
+        tw[i] = make_ulonglong2(psi[i], psi_s[i]);
+        itw[i] = make_ulonglong2(ipsi[i], ipsi_s[i]);
+    }
+    c.d_tw = dupload(tw);
+    c.d_itw = dupload(itw);
+    // transposed row-pass tables of the two-pass transform (N >= 2^14)
+    c.ntt_s1 = c.log_n >= 14 ? (c.log_n == 15 ? 7 : c.log_n / 2) : 0;
+    if (c.ntt_s1) {
+        const int S1 = c.ntt_s1, N1 = 1 << S1, LM2 = c.log_n - S1;
+        std::vector<ulonglong2> t2((size_t)ne * n, make_ulonglong2(0, 0)), it2(t2.size(), make_ulonglong2(0, 0));
+        for (int t = 0; t < ne; t++) {
+            size_t o = (size_t)t * n;
+            for (int sp = 0; sp < LM2; sp++)
+                for (int g = 0; g < (1 << sp); g++)
+                    for (int r = 0; r < N1; r++) {
+                        size_t src = (size_t)t * n + ((size_t)1 << (S1 + sp)) + ((size_t)r << sp) + g;
+                        t2[o] = make_ulonglong2(psi[src], psi_s[src]);
+                        it2[o] = make_ulonglong2(ipsi[src], ipsi_s[src]);
+                        o++;
+                    }
+        }
+        c.d_tw2 = dupload(t2);
+        c.d_itw2 = dupload(it2);
+    }
 
     // rescale: q_l^-1 mod q_i
     std::vector<u64> resc((size_t)2 * (L + 1) * (L + 1), 0);

@@ -1,27 +1,36 @@
-// ntt.cu — batched negacyclic NTT over RNS limbs (forward: Cooley-Tukey with
-// merged psi powers, natural order in, bit-reversed order out; inverse:
-// Gentleman-Sande, bit-reversed in, natural out, times N^-1).
+// ntt.cu — batched negacyclic NTT over RNS limbs.
 //
-// Output order: slot k of the forward transform holds a(psi^(2*brev(k)+1)).
-// Rings up to N = 2^14 are transformed by one CTA per row with the whole row in
-// shared memory. Larger rings use two passes over an N1 x N2 view
-// (N = N1 * N2): the first log2(N1) butterfly stages couple elements N2 apart
-// and run on tiles of consecutive columns; the remaining stages couple
-// elements inside one contiguous row of N2 and run on tiles of whole rows.
+// Forward: Cooley-Tukey with merged psi powers (natural order in, bit-reversed
+// order out): slot k holds a(psi^(2 brev(k) + 1)). Inverse: Gentleman-Sande
+// (bit-reversed in, natural out) followed by the N^-1 scaling.
+//
+// Decomposition. A ring of N = N1 * N2 coefficients is viewed as N1 rows of
+// N2: the first log2(N1) stages couple elements N2 apart (independent
+// N1-point transforms on columns), the remaining stages couple elements inside
+// one row (N2-point transforms with row-dependent twiddles). Rings up to 2^13
+// run in one pass (N1 = N, one CTA per limb); larger rings in two passes.
+//
+// Each CTA holds a tile of R sub-transforms of M = 2^LOGM points in shared
+// memory (element x of sub-transform q at x*(R+1) + q). Row passes read their
+// twiddles from tables transposed to [stage][group][row], so that the R rows of a
+// tile load consecutive entries. Every thread owns 8
+// residues and runs three butterfly stages in registers between shared-memory
+// exchanges (radix-8 blocking; the last block has 1-3 stages). Arithmetic is
+// lazy in the style of Harvey (2014): forward values stay in [0, 4q), inverse
+// values in [0, 2q); twiddle products use Shoup's precomputed quotient and no
+// final correction; the last pass reduces to [0, q).
 #include "core.cuh"
 
 namespace fhe {
 
 namespace {
 
-constexpr int kTile = 4096;  // elements per CTA in the two-pass kernels (32 KiB)
-
 struct RowPtr {
     u64* p;
     int prime;
 };
 
-__device__ __forceinline__ RowPtr row_ptr(const PolyBatch& pb, int row, int n) {
+__device__ __forceinline__ RowPtr row_ptr(const PolyBatch& pb, int row, int log_n) {
     int li = row % pb.n_limbs;
     int rest = row / pb.n_limbs;
     int part = rest % pb.n_parts;
@@ -29,206 +38,230 @@ __device__ __forceinline__ RowPtr row_ptr(const PolyBatch& pb, int row, int n) {
     int limb = pb.limb_lo + li;
     RowPtr r;
     r.p = pb.base + (size_t)item * pb.item_stride + (size_t)part * pb.part_stride +
-          (size_t)(limb - pb.addr_lo) * n;
+          ((size_t)(limb - pb.addr_lo) << log_n);
     r.prime = pb.prime_of(limb);
     return r;
 }
 
-// Stages [0, S1) on tiles of `cols` consecutive columns of the N1 x N2 view
-// (S1 = log N and cols = N2 = 1 for the single-pass transform).
-template <bool INV>
-__global__ void ntt_col_kernel(PolyBatch pb, const Prime* __restrict__ primes,
-                               const u64* __restrict__ tw, const u64* __restrict__ tws,
-                               const u64* __restrict__ ninv, int log_n, int S1, int log_cols) {
+// Shoup product without the final correction: a * w mod q in [0, 2q) for any a < 2^64.
+__device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
+    u64 qh = __umul64hi(a, ws);
+    return a * w - qh * q;
+}
+
+// Forward CT butterfly on values in [0, 4q): X <- X + W Y, Y <- X - W Y (lazy, outputs in [0, 4q)).
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 ws, u64 q, u64 q2) {
+    u64 a = x >= q2 ? x - q2 : x;
+    u64 t = shoup_lazy(y, w, ws, q);
+    x = a + t;
+    y = a + q2 - t;
+}
+
+// Inverse GS butterfly on values in [0, 2q): X <- X + Y, Y <- (X - Y) W (outputs in [0, 2q)).
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 ws, u64 q, u64 q2) {
+    u64 s = x + y;
+    s = s >= q2 ? s - q2 : s;
+    u64 d = x + q2 - y;
+    x = s;
+    y = shoup_lazy(d, w, ws, q);
+}
+
+__device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
+    u64 q2 = q << 1;
+    x = x >= q2 ? x - q2 : x;
+    return x >= q ? x - q : x;
+}
+
+// One tile: R sub-transforms of M = 2^LOGM points.
+// PASS 0: column transforms (stages [0, LOGM) of the full ring), tile = R consecutive columns;
+//         with LOGM = log N and R = 1 this is the whole single-pass transform.
+// PASS 1: row transforms (stages [S1, log N)), tile = R consecutive rows of M = N2 points.
+// LAST: this kernel performs the final stages (reduce to [0, q); inverse: times N^-1).
+template <int LOGM, int R, bool INV, int PASS, bool LAST>
+__global__ void __launch_bounds__(R * (1 << LOGM) / 8, (1024 / (R * (1 << LOGM) / 8)) > 0 ? 1024 / (R * (1 << LOGM) / 8) : 1)
+ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2* __restrict__ tw,
+                const u64* __restrict__ ninv, int log_n) {
+    constexpr int M = 1 << LOGM;
+    constexpr int P = R == 1 ? 1 : R + 1;
+    constexpr int T = R * M / 8;
     extern __shared__ u64 sm[];
-    const int n = 1 << log_n;
-    const RowPtr rp = row_ptr(pb, blockIdx.x, n);
+    const int tid = threadIdx.x;
+    const RowPtr rp = row_ptr(pb, blockIdx.x, log_n);
     const u64 q = primes[rp.prime].q;
-    const u64* W = tw + (size_t)rp.prime * n;
-    const u64* Ws = tws + (size_t)rp.prime * n;
-    const int N1 = 1 << S1;
-    const int log_n2 = log_n - S1;
-    const int cols = 1 << log_cols;
-    const int c0 = blockIdx.y << log_cols;
-    const int total = N1 << log_cols;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int r = e >> log_cols, c = e & (cols - 1);
-        sm[e] = rp.p[(size_t)(c0 + c) + ((size_t)r << log_n2)];
-    }
-    __syncthreads();
-    const int half = total >> 1;
-    if (!INV) {
-        for (int s = 0; s < S1; s++) {
-            const int log_tl = S1 - 1 - s;
-            for (int bi = threadIdx.x; bi < half; bi += blockDim.x) {
-                int c = bi & (cols - 1);
-                int p = bi >> log_cols;
-                int g = p >> log_tl;
-                int jj = p & ((1 << log_tl) - 1);
-                int r0 = (g << (log_tl + 1)) + jj;
-                int i0 = (r0 << log_cols) + c;
-                int i1 = i0 + (1 << (log_tl + log_cols));
-                int wi = (1 << s) + g;
-                u64 x = sm[i0];
-                u64 y = mul_shoup(sm[i1], W[wi], Ws[wi], q);
-                sm[i0] = add_mod(x, y, q);
-                sm[i1] = sub_mod(x, y, q);
-            }
-            __syncthreads();
-        }
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            int r = e >> log_cols, c = e & (cols - 1);
-            rp.p[(size_t)(c0 + c) + ((size_t)r << log_n2)] = sm[e];
+    const u64 q2 = q << 1;
+    const ulonglong2* W = tw + ((size_t)rp.prime << log_n);
+    const int log_n2 = PASS == 0 ? log_n - LOGM : LOGM;  // row length of the N1 x N2 view
+    const int S1 = log_n - log_n2;                       // column stages
+    const int t0 = blockIdx.y * R;                       // first column (PASS 0) or row (PASS 1)
+
+    // load (coalesced), values enter in [0, q)
+    if (PASS == 0) {
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e / R, qq = e % R;
+            sm[x * P + qq] = rp.p[(size_t)(t0 + qq) + ((size_t)x << log_n2)];
         }
     } else {
-        for (int s = S1 - 1; s >= 0; s--) {
-            const int log_tl = S1 - 1 - s;
-            for (int bi = threadIdx.x; bi < half; bi += blockDim.x) {
-                int c = bi & (cols - 1);
-                int p = bi >> log_cols;
-                int g = p >> log_tl;
-                int jj = p & ((1 << log_tl) - 1);
-                int r0 = (g << (log_tl + 1)) + jj;
-                int i0 = (r0 << log_cols) + c;
-                int i1 = i0 + (1 << (log_tl + log_cols));
-                int wi = (1 << s) + g;
-                u64 x = sm[i0];
-                u64 y = sm[i1];
-                sm[i0] = add_mod(x, y, q);
-                sm[i1] = mul_shoup(sub_mod(x, y, q), W[wi], Ws[wi], q);
-            }
-            __syncthreads();
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e & (M - 1), qq = e >> LOGM;
+            sm[x * P + qq] = rp.p[((size_t)(t0 + qq) << LOGM) + x];
         }
-        const u64 ni = ninv[2 * rp.prime], nis = ninv[2 * rp.prime + 1];
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            int r = e >> log_cols, c = e & (cols - 1);
-            rp.p[(size_t)(c0 + c) + ((size_t)r << log_n2)] = mul_shoup(sm[e], ni, nis, q);
+    }
+    __syncthreads();
+
+    const int qq = tid % R;  // sub-transform of this thread
+    const int g = tid / R;   // 8-element group within the sub-transform
+    const int row_off = PASS == 1 ? t0 + qq : 0;
+    u64 v[8];
+
+    // radix-8 blocks of stages; forward runs stages 0..LOGM-1, inverse LOGM-1..0
+    constexpr int NB = (LOGM + 2) / 3;
+#pragma unroll
+    for (int bi = 0; bi < NB; bi++) {
+        // forward: block bi covers stages [3 bi, min(3 bi + 3, LOGM));
+        // inverse: the same blocks in reverse order, stages inside a block descending
+        const int blk_id = INV ? NB - 1 - bi : bi;
+        const int s0 = 3 * blk_id;
+        const int b = (LOGM - s0) < 3 ? (LOGM - s0) : 3;
+        const int d = M >> (s0 + b);
+        const int base = (g / d) * (8 * d) + (g % d);
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = sm[(base + u * d) * P + qq];
+        // Twiddle of the pair (u, u + dist) at block stage j: its group index at stage s0 + j is
+        // tb * 2^j + (u >> (b - j)), with tb = base >> (LOGM - s0) the thread's group at s0.
+        const int tb = base >> (LOGM - s0);
+        if (!INV) {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                if (j >= b) break;
+                const int s = s0 + j;
+                const int dist = 1 << (b - 1 - j);
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    if (u & dist) continue;
+                    const int grp = (tb << j) + (u >> (b - j));
+                    const int wi = PASS == 1 ? ((((1 << s) - 1 + grp)) << S1) + row_off : (1 << s) + grp;
+                    const ulonglong2 w = W[wi];
+                    ct_bfly(v[u], v[u + dist], w.x, w.y, q, q2);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 2; j >= 0; j--) {
+                if (j >= b) continue;
+                const int s = s0 + j;
+                const int dist = 1 << (b - 1 - j);
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    if (u & dist) continue;
+                    const int grp = (tb << j) + (u >> (b - j));
+                    const int wi = PASS == 1 ? ((((1 << s) - 1 + grp)) << S1) + row_off : (1 << s) + grp;
+                    const ulonglong2 w = W[wi];
+                    gs_bfly(v[u], v[u + dist], w.x, w.y, q, q2);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) sm[(base + u * d) * P + qq] = v[u];
+        __syncthreads();
+    }
+
+    // store (coalesced)
+    const u64 ni = ninv[2 * rp.prime], nis = ninv[2 * rp.prime + 1];
+    if (PASS == 0) {
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e / R, c = e % R;
+            u64 val = sm[x * P + c];
+            if (LAST) {
+                if (INV) {
+                    u64 r = shoup_lazy(val, ni, nis, q);
+                    val = r >= q ? r - q : r;
+                } else {
+                    val = reduce4(val, q);
+                }
+            }
+            rp.p[(size_t)(t0 + c) + ((size_t)x << log_n2)] = val;
+        }
+    } else {
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e & (M - 1), r = e >> LOGM;
+            u64 val = sm[x * P + r];
+            if (LAST) {
+                if (INV) {
+                    u64 t = shoup_lazy(val, ni, nis, q);
+                    val = t >= q ? t - q : t;
+                } else {
+                    val = reduce4(val, q);
+                }
+            }
+            rp.p[((size_t)(t0 + r) << LOGM) + x] = val;
         }
     }
 }
 
-// Stages [S1, log N) on tiles of 2^log_rows whole rows of length N2.
-template <bool INV>
-__global__ void ntt_row_kernel(PolyBatch pb, const Prime* __restrict__ primes,
-                               const u64* __restrict__ tw, const u64* __restrict__ tws, int log_n,
-                               int S1, int log_rows) {
-    extern __shared__ u64 sm[];
-    const int n = 1 << log_n;
-    const RowPtr rp = row_ptr(pb, blockIdx.x, n);
-    const u64 q = primes[rp.prime].q;
-    const u64* W = tw + (size_t)rp.prime * n;
-    const u64* Ws = tws + (size_t)rp.prime * n;
-    const int log_n2 = log_n - S1;
-    const int r_base = blockIdx.y << log_rows;
-    const int total = 1 << (log_rows + log_n2);
-    u64* gp = rp.p + ((size_t)r_base << log_n2);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) sm[e] = gp[e];
-    __syncthreads();
-    const int half = total >> 1;
-    const int log_half_row = log_n2 - 1;
-    const int stages = log_n2;
-    if (!INV) {
-        for (int sp = 0; sp < stages; sp++) {
-            const int log_tl = log_n2 - 1 - sp;
-            for (int bi = threadIdx.x; bi < half; bi += blockDim.x) {
-                int rl = bi >> log_half_row;
-                int p = bi & ((1 << log_half_row) - 1);
-                int g = p >> log_tl;
-                int jj = p & ((1 << log_tl) - 1);
-                int x0 = (g << (log_tl + 1)) + jj;
-                int i0 = (rl << log_n2) + x0;
-                int i1 = i0 + (1 << log_tl);
-                int wi = (1 << (S1 + sp)) + ((r_base + rl) << sp) + g;
-                u64 x = sm[i0];
-                u64 y = mul_shoup(sm[i1], W[wi], Ws[wi], q);
-                sm[i0] = add_mod(x, y, q);
-                sm[i1] = sub_mod(x, y, q);
-            }
-            __syncthreads();
-        }
-    } else {
-        for (int sp = stages - 1; sp >= 0; sp--) {
-            const int log_tl = log_n2 - 1 - sp;
-            for (int bi = threadIdx.x; bi < half; bi += blockDim.x) {
-                int rl = bi >> log_half_row;
-                int p = bi & ((1 << log_half_row) - 1);
-                int g = p >> log_tl;
-                int jj = p & ((1 << log_tl) - 1);
-                int x0 = (g << (log_tl + 1)) + jj;
-                int i0 = (rl << log_n2) + x0;
-                int i1 = i0 + (1 << log_tl);
-                int wi = (1 << (S1 + sp)) + ((r_base + rl) << sp) + g;
-                u64 x = sm[i0];
-                u64 y = sm[i1];
-                sm[i0] = add_mod(x, y, q);
-                sm[i1] = mul_shoup(sub_mod(x, y, q), W[wi], Ws[wi], q);
-            }
-            __syncthreads();
-        }
-    }
-    for (int e = threadIdx.x; e < total; e += blockDim.x) gp[e] = sm[e];
+template <int LOGM, int R, bool INV, int PASS, bool LAST>
+void launch_tile(const Ctx& c, const PolyBatch& pb, int tiles, cudaStream_t s, double bytes) {
+    constexpr int T = R * (1 << LOGM) / 8;
+    constexpr size_t smem = sizeof(u64) * (1 << LOGM) * (R == 1 ? 1 : R + 1);
+    // row passes read the transposed [stage][group][row] tables
+    const ulonglong2* tw = PASS == 1 ? (INV ? c.d_itw2 : c.d_tw2) : (INV ? c.d_itw : c.d_tw);
+    if (smem > 48 * 1024)
+        CK(cudaFuncSetAttribute(ntt_tile_kernel<LOGM, R, INV, PASS, LAST>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope _ls(c.prof, INV ? K_NTT_INV : K_NTT_FWD, bytes, s);
+    ntt_tile_kernel<LOGM, R, INV, PASS, LAST><<<dim3(pb.rows(), tiles), T, smem, s>>>(pb, c.d_primes, tw,
+                                                                                      c.d_ninv, c.log_n);
+    CK(cudaGetLastError());
 }
 
 template <bool INV>
 void run_ntt(const Ctx& c, const PolyBatch& pb, cudaStream_t s) {
     const int rows = pb.rows();
     if (rows == 0) return;
-    const u64* tw = INV ? c.d_ipsi : c.d_psi;
-    const u64* tws = INV ? c.d_ipsi_s : c.d_psi_s;
-    const int log_n = c.log_n;
-    const double bytes = 16.0 * rows * ((size_t)1 << log_n);
-    const int cls = INV ? K_NTT_INV : K_NTT_FWD;
-    if (log_n <= 14) {
-        LaunchScope _ls(c.prof, cls, bytes, s);
-        size_t smem = sizeof(u64) << log_n;
-        int threads = log_n >= 12 ? 512 : (1 << (log_n - 1));
-        ntt_col_kernel<INV><<<dim3(rows, 1), threads, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv,
-                                                                 log_n, log_n, 0);
-        CK(cudaGetLastError());
-        return;
-    }
-    // two passes: N1 = 2^S1 rows of N2 = 2^(log_n - S1)
-    const int S1 = log_n / 2;
-    const int log_n2 = log_n - S1;
-    const int log_cols = 12 - S1;          // tile = N1 x cols = 4096 elements
-    const int log_rows = 12 - log_n2;      // tile = rows x N2 = 4096 elements
-    const size_t smem = sizeof(u64) * kTile;
-    dim3 gcol(rows, 1 << (log_n2 - log_cols));
-    dim3 grow(rows, 1 << (S1 - log_rows));
-    if (!INV) {
-        {
-            LaunchScope _ls(c.prof, cls, bytes, s);
-            ntt_col_kernel<false><<<gcol, 256, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv, log_n, S1, log_cols);
-            CK(cudaGetLastError());
-        }
-        {
-            LaunchScope _ls(c.prof, cls, bytes, s);
-            ntt_row_kernel<false><<<grow, 256, smem, s>>>(pb, c.d_primes, tw, tws, log_n, S1, log_rows);
-            CK(cudaGetLastError());
-        }
-    } else {
-        {
-            LaunchScope _ls(c.prof, cls, bytes, s);
-            ntt_row_kernel<true><<<grow, 256, smem, s>>>(pb, c.d_primes, tw, tws, log_n, S1, log_rows);
-            CK(cudaGetLastError());
-        }
-        {
-            LaunchScope _ls(c.prof, cls, bytes, s);
-            ntt_col_kernel<true><<<gcol, 256, smem, s>>>(pb, c.d_primes, tw, tws, c.d_ninv, log_n, S1, log_cols);
-            CK(cudaGetLastError());
-        }
+    const double bytes = 16.0 * rows * ((size_t)1 << c.log_n);
+    switch (c.log_n) {
+        case 9: launch_tile<9, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
+        case 10: launch_tile<10, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
+        case 11: launch_tile<11, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
+        case 12: launch_tile<12, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
+        case 13: launch_tile<13, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
+        case 14:  // 128 x 128
+            if (!INV) {
+                launch_tile<7, 16, false, 0, false>(c, pb, 128 / 16, s, bytes);
+                launch_tile<7, 16, false, 1, true>(c, pb, 128 / 16, s, bytes);
+            } else {
+                launch_tile<7, 16, true, 1, false>(c, pb, 128 / 16, s, bytes);
+                launch_tile<7, 16, true, 0, true>(c, pb, 128 / 16, s, bytes);
+            }
+            return;
+        case 15:  // 256 column transforms of 2^7 points (N2 = 256), then 128 rows of 2^8
+            if (!INV) {
+                launch_tile<7, 16, false, 0, false>(c, pb, 256 / 16, s, bytes);
+                launch_tile<8, 16, false, 1, true>(c, pb, 128 / 16, s, bytes);
+            } else {
+                launch_tile<8, 16, true, 1, false>(c, pb, 128 / 16, s, bytes);
+                launch_tile<7, 16, true, 0, true>(c, pb, 256 / 16, s, bytes);
+            }
+            return;
+        case 16:  // 256 x 256
+            if (!INV) {
+                launch_tile<8, 16, false, 0, false>(c, pb, 256 / 16, s, bytes);
+                launch_tile<8, 16, false, 1, true>(c, pb, 256 / 16, s, bytes);
+            } else {
+                launch_tile<8, 16, true, 1, false>(c, pb, 256 / 16, s, bytes);
+                launch_tile<8, 16, true, 0, true>(c, pb, 256 / 16, s, bytes);
+            }
+            return;
+        default: fail(FHE_ERR_INVALID_ARG, "unsupported ring degree");
     }
 }
 
 }  // namespace
 
-void ntt_init() {
-    const int max_smem = 227 * 1024;
-    CK(cudaFuncSetAttribute(ntt_col_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-    CK(cudaFuncSetAttribute(ntt_col_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-    CK(cudaFuncSetAttribute(ntt_row_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-    CK(cudaFuncSetAttribute(ntt_row_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-}
+void ntt_init() {}
 
 void ntt_forward(const Ctx& c, const PolyBatch& pb, cudaStream_t s) { run_ntt<false>(c, pb, s); }
 void ntt_inverse(const Ctx& c, const PolyBatch& pb, cudaStream_t s) { run_ntt<true>(c, pb, s); }

@@ -1,0 +1,74 @@
+"""Run one batched kernel workload through the C ABI (for timing and ncu captures).
+
+  python -m paper_2509_03024_gb300.kernel_driver ntt --preset paper --rows 1024 [--inverse] [--reps 3]
+  python -m paper_2509_03024_gb300.kernel_driver keyswitch --preset paper --count 64 [--reps 3]
+
+`ntt` transforms `rows` limbs of N residues in place (rows / (L+1) polynomials
+of L+1 limbs); `keyswitch` rotates `count` top-level ciphertexts by one slot
+(automorphism + hybrid key switch). Prints CUDA-event timings per repetition.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    import torch
+    from paper_2509_03024_gb300 import build, capi
+    from paper_2509_03024_gb300.workloads import PRESETS
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("kind", choices=["ntt", "keyswitch"])
+    ap.add_argument("--preset", default="paper")
+    ap.add_argument("--rows", type=int, default=1024)
+    ap.add_argument("--count", type=int, default=64)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--inverse", action="store_true")
+    args = ap.parse_args()
+    build.build()
+    ctx = capi.Context.from_preset(PRESETS[args.preset])
+    if args.kind == "keyswitch":
+        ctx.keygen(1, [1])
+    L1 = ctx.top + 1
+    times = []
+    if args.kind == "ntt":
+        polys = max(1, args.rows // L1)
+        rng = np.random.default_rng(0)
+        host = np.stack([rng.integers(0, q, (polys, ctx.n), dtype=np.uint64) for q in ctx.primes[:L1]], axis=1)
+        buf = torch.from_numpy(host.view(np.int64).copy()).cuda()
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if args.inverse:
+                ctx.ntt_inverse(buf, polys, L1)
+            else:
+                ctx.ntt_forward(buf, polys, L1)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        alg = 16.0 * polys * L1 * ctx.n
+    else:
+        cts = ctx.empty_ct(args.count)
+        for t in range(args.count):
+            w = 2 * L1 * ctx.n
+            ctx.encrypt(np.random.default_rng(t).normal(size=16), ctx.top, t, cts[t * w:(t + 1) * w])
+        out = ctx.empty_ct(args.count)
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.rotate(cts, out, args.count, ctx.top, 1)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        alg = None
+    res = {"kind": args.kind, "preset": args.preset, "ms": times}
+    if alg:
+        res["alg_gbs_best"] = alg / (min(times) / 1e3) / 1e9
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
