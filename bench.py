@@ -48,6 +48,10 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=96)
+    ap.add_argument("--served-rate", type=float, default=100.0)
+    ap.add_argument("--served-slots", type=int, default=48)
     return ap.parse_args()
 
 
@@ -156,6 +160,83 @@ def oracle_sample(train, U, V, groups_sampled: int = 2):
             f"epoch extrapolated as groups x {t_groups:.2f} s + {3 * nodes} rotation-sized key switches x "
             f"{t_rot:.2f} s = {est:.0f} s")
     return rows.size / est, time.perf_counter() - t0, desc
+
+
+# ----------------------------------------------------------------------------- served workload
+
+SERVED = ("served fold-in + predict: resident encrypted item factors 3706 x k=16 (N=2^16, 13x50-bit + "
+          "3x60-bit primes); Poisson arrivals; per request one user's encrypted CSR row (nnz log-uniform "
+          "5..300, MovieLens rating law), 5 encrypted SGD fold-in steps (lr 0.005, lambda 0.02) then the "
+          "encrypted predicted-rating row over all items")
+
+
+def serve_loop(server, reqs, enc, take_buf):
+    """Wall-clock request loop: admit arrived requests FIFO while slots are free, tick, collect."""
+    import collections
+    queue = collections.deque()
+    arrivals = [r.arrival_s for r in reqs]
+    done_at = [None] * len(reqs)
+    nxt = 0
+    t0 = time.perf_counter()
+    inflight = 0
+    ticks = 0
+    while any(d is None for d in done_at):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            queue.append(nxt)
+            nxt += 1
+        while queue and server.submit(queue[0], reqs[queue[0]].items, *enc[queue[0]]):
+            queue.popleft()
+            inflight += 1
+        if inflight:
+            server.tick()
+            ticks += 1
+            now = time.perf_counter() - t0
+            for rid in server.poll():
+                server.take(rid, take_buf)
+                done_at[rid] = now
+                inflight -= 1
+        elif nxt < len(reqs):
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+    lat = np.array([d - a for d, a in zip(done_at, arrivals)]) * 1e3
+    span = max(done_at) - arrivals[0]
+    nnz = sum(int(r.items.size) for r in reqs)
+    return {"ratings_per_s": nnz / span, "requests_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "ticks": ticks,
+            "wall_s": span}
+
+
+def run_served(args, dev):
+    import torch
+    from paper_2509_03024_gb300 import capi
+    from paper_2509_03024_gb300 import workloads as W
+    m, k, steps, lr, lam = 3706, 16, 5, 0.005, 0.02
+    ctx = capi.Context.from_preset(W.PRESETS["served"], device=dev)
+    ctx.keygen(SEED, ctx.serve_rotation_steps(k))
+    V = W.init_factors(m, k, SEED + 5)
+    plan = capi.MfPlan(ctx, 1, m, k, [0, 1], [0], [1.0])  # item packing of the resident factors
+    n_vb = plan.n_vb
+    VD = ctx.empty_ct(n_vb)
+    plan.encrypt_factors(1, V, VD)
+    reqs = W.served_requests(args.served_requests, args.served_rate, m, k, SEED + 6)
+    enc = []
+    for i, r in enumerate(reqs):  # client-side encryption, before the timed loop
+        UR, R = ctx.empty_ct(1), ctx.empty_ct(n_vb)
+        ctx.encrypt_request(m, k, r.u0, r.items, r.ratings, (1 << 44) + 64 * i, UR, R)
+        enc.append((UR, R))
+    take_buf = ctx.empty_ct(n_vb)
+    server = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=args.served_slots,
+                         memory_budget_bytes=48 << 30)
+    batched = serve_loop(server, reqs, enc, take_buf)
+    batched["slots"] = server.n_slots
+    server.close()
+    single = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=1)
+    one = serve_loop(single, reqs, enc, take_buf)
+    single.close()
+    return {"workload": SERVED, "requests": len(reqs), "arrival_rate_req_s": args.served_rate,
+            "value": batched["ratings_per_s"], "unit": UNIT, "p50_ms": batched["p50_ms"],
+            "p99_ms": batched["p99_ms"], "continuous_batching": batched, "one_by_one": one,
+            "speedup_vs_one_by_one": batched["ratings_per_s"] / one["ratings_per_s"]}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -269,6 +350,10 @@ def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world
             "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d}
 
 
+def torch_device_of(ctx):
+    return ctx.device
+
+
 def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
            train, U, V, dist):
     # roofline of the dominant kernel class (longest summed device time)
@@ -296,6 +381,8 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
            "accuracy": {"max_abs_vs_fp64": err, "rmse_gap_test": rmse_gap},
            "kernels": {k: {"launches": v[0], "device_ms": round(v[1], 3), "alg_gb": round(v[2] / 1e9, 3)}
                        for k, v in stats.items() if v[0]}}
+    if not args.no_served:
+        out["served"] = run_served(args, torch_device_of(ctx))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rps, secs, desc = oracle_sample(train, U, V)
         out["cpu_baseline"] = {"value": rps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,

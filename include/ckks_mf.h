@@ -246,6 +246,65 @@ int fhe_mf_sgd_epoch(fhe_ctx* ctx, fhe_mf_plan* plan, uint64_t* U, uint64_t* V, 
 int fhe_predict(fhe_ctx* ctx, const fhe_mf_plan* plan, const uint64_t* U, const uint64_t* V,
                 int32_t level, int32_t user, uint64_t* out, void* stream);
 
+/* ------------------------------------------------------------------ serving (continuous batching) */
+
+/* A request loop over resident encrypted item factors. Each request carries one
+ * user's encrypted rating row and initial factor and is answered with the
+ * encrypted predicted-rating row after `steps` fold-in steps (Alg. 1 error and
+ * gradient lines applied to the user's ratings, Alg. 2's accumulated update;
+ * item factors stay fixed). Layout: the user's k-vector in every slot block;
+ * item j = c*B + d in block d of item batch c (the packing of
+ * fhe_mf_encrypt_factors with which = 1).
+ *
+ * Step at level l (two levels): for each item batch c holding a rated item,
+ * S_c = rotsum_kp(rescale(relin(UR (x) V_c))), E_c = R_c - S_c,
+ * T += E_c (x) rescale(V_c (.) mask_c) (mask_c = lr on the first k slots of the
+ * rated blocks); G = rescale(relin(T)); G += rot(G, 2^t w) for t < log2 B;
+ * G += rot(G, -kp); UR <- drop(rescale(UR * round((1 - lr lambda nnz) Delta))) + G.
+ * The prediction pass computes S_c for every batch at the final level (one
+ * level): slot d*w of output c is <u, v_(cB+d)>.
+ *
+ * Admission is memory based: the server owns `max_slots` request slots (each
+ * holding a request's inputs and its share of the batched work area), capped
+ * so that all slots fit in `memory_budget_bytes` of device memory. A submit
+ * that finds no free slot returns FHE_ERR_STATE and changes nothing; the
+ * caller keeps the request queued and retries after a tick frees a slot.
+ * Every tick advances every admitted request by one step in shared batched
+ * launches (requests at different levels are grouped per level); a request
+ * admitted between ticks joins at the next tick. Results do not depend on
+ * which other requests share a tick. */
+typedef struct fhe_server fhe_server;
+
+/* Rotation steps a server for rank k needs. Same return convention as fhe_mf_rotation_steps. */
+int fhe_serve_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t cap);
+/* V: device, ceil(m / B) item-batch ciphertexts at the top level (copied; the
+ * server keeps its own resident copy). Needs top level >= 2 * steps + 1. */
+int fhe_serve_create(fhe_ctx* ctx, const uint64_t* V, int32_t m, int32_t k, int32_t steps, double lr,
+                     double lambda, int32_t max_slots, size_t memory_budget_bytes, fhe_server** out);
+void fhe_serve_destroy(fhe_server* server);
+/* Slots the server actually allocated (after the memory cap) and slots now free. */
+int fhe_serve_slots(const fhe_server* server, int32_t* total, int32_t* free_slots);
+/* Admit a request if a slot is free. items: host int32 [nnz] distinct item
+ * indices < m; UR: device ciphertext (u in every block), R: device, ceil(m/B)
+ * ciphertexts (rating of item c*B+d on the first k slots of block d of R_c);
+ * both at the top level; copied on `stream`. FHE_ERR_STATE if no slot is free. */
+int fhe_serve_submit(fhe_server* server, int64_t request_id, const int32_t* items, int32_t nnz,
+                     const uint64_t* UR, const uint64_t* R, void* stream);
+/* Advance every admitted request by one step; synchronises `stream` at the
+ * end. Returns the number of requests still in flight (>= 0) or an error. */
+int fhe_serve_tick(fhe_server* server, void* stream);
+/* Ids of requests completed since the last poll (up to cap; host). Returns the count. */
+int fhe_serve_poll(fhe_server* server, int64_t* ids, int32_t cap);
+/* Client-side helper: pack and encrypt one request at the top level. u0: host
+ * double [k]; items/ratings: host [nnz]. UR receives u0 in every block (nonce
+ * nonce_base), R receives ceil(m/B) rating ciphertexts (nonces nonce_base+1+c). */
+int fhe_serve_encrypt_request(fhe_ctx* ctx, int32_t m, int32_t k, const double* u0, const int32_t* items,
+                              const double* ratings, int32_t nnz, uint64_t nonce_base, uint64_t* UR,
+                              uint64_t* R, void* stream);
+/* Copy a completed request's prediction (ceil(m/B) ciphertexts at *level) to
+ * device `out` and free its slot. */
+int fhe_serve_take(fhe_server* server, int64_t request_id, uint64_t* out, int32_t* level, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

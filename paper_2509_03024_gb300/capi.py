@@ -31,7 +31,9 @@ EXPORTS = [
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale",
     "fhe_rotate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
-    "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict",
+    "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
+    "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
+    "fhe_serve_poll", "fhe_serve_encrypt_request", "fhe_serve_take",
 ]
 
 
@@ -114,6 +116,15 @@ def lib() -> ctypes.CDLL:
             "fhe_mf_decrypt_factors": [vp, vp, i32, vp, i32, vp, i32, vp],
             "fhe_mf_sgd_epoch": [vp, vp, vp, vp, i32, dbl, dbl, vp],
             "fhe_predict": [vp, vp, vp, vp, i32, i32, vp, vp],
+            "fhe_serve_rotation_steps": [vp, i32, vp, sz],
+            "fhe_serve_create": [vp, vp, i32, i32, i32, dbl, dbl, i32, sz, ctypes.POINTER(vp)],
+            "fhe_serve_destroy": [vp],
+            "fhe_serve_slots": [vp, vp, vp],
+            "fhe_serve_submit": [vp, i64, vp, i32, vp, vp, vp],
+            "fhe_serve_tick": [vp, vp],
+            "fhe_serve_poll": [vp, vp, i32],
+            "fhe_serve_encrypt_request": [vp, i32, i32, vp, vp, vp, i32, u64, vp, vp, vp],
+            "fhe_serve_take": [vp, i64, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -121,6 +132,7 @@ def lib() -> ctypes.CDLL:
             f.restype = ctypes.c_int
         L.fhe_ctx_destroy.restype = None
         L.fhe_mf_plan_destroy.restype = None
+        L.fhe_serve_destroy.restype = None
         L.fhe_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -259,6 +271,21 @@ class Context:
     def rotate(self, ct, out, count: int, level: int, step: int, stream=None):
         self._check(lib().fhe_rotate(self.h, _ptr(ct), _ptr(out), count, level, step, _stream(stream)))
 
+    def serve_rotation_steps(self, k: int):
+        buf = np.zeros(256, dtype=np.int32)
+        rc = lib().fhe_serve_rotation_steps(self.h, k, buf.ctypes.data, buf.size)
+        if rc < 0:
+            self._check(rc)
+        return [int(x) for x in buf[:rc]]
+
+    def encrypt_request(self, m: int, k: int, u0, items, ratings, nonce_base: int, UR, R, stream=None):
+        u = np.ascontiguousarray(u0, dtype=np.float64)
+        it = np.ascontiguousarray(items, dtype=np.int32)
+        rt = np.ascontiguousarray(ratings, dtype=np.float64)
+        self._check(lib().fhe_serve_encrypt_request(self.h, m, k, u.ctypes.data, it.ctypes.data if it.size else None,
+                                                    rt.ctypes.data if rt.size else None, it.size, nonce_base,
+                                                    _ptr(UR), _ptr(R), _stream(stream)))
+
     # ---- launch accounting
     def profile_begin(self, time_kernels: bool = False):
         self._check(lib().fhe_profile_begin(self.h, 1 if time_kernels else 0))
@@ -338,3 +365,62 @@ class MfPlan:
     def predict(self, U, V, level: int, user: int, out, stream=None):
         self.ctx._check(lib().fhe_predict(self.ctx.h, self.h, _ptr(U), _ptr(V), level, user, _ptr(out),
                                           _stream(stream)))
+
+
+class Server:
+    """Owns one fhe_server: continuous-batching fold-in + predict over resident item factors."""
+
+    def __init__(self, ctx: Context, V, m: int, k: int, steps: int, lr: float, lam: float, max_slots: int,
+                 memory_budget_bytes: int = 0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(lib().fhe_serve_create(ctx.h, _ptr(V), m, k, steps, lr, lam, max_slots, memory_budget_bytes,
+                                          ctypes.byref(h)))
+        self.h = h
+        tot, fr = ctypes.c_int32(), ctypes.c_int32()
+        ctx._check(lib().fhe_serve_slots(self.h, ctypes.byref(tot), ctypes.byref(fr)))
+        self.n_slots = tot.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fhe_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def free_slots(self) -> int:
+        tot, fr = ctypes.c_int32(), ctypes.c_int32()
+        self.ctx._check(lib().fhe_serve_slots(self.h, ctypes.byref(tot), ctypes.byref(fr)))
+        return fr.value
+
+    def submit(self, request_id: int, items, UR, R, stream=None) -> bool:
+        """True if admitted; False if no slot is free (FHE_ERR_STATE)."""
+        it = np.ascontiguousarray(items, dtype=np.int32)
+        rc = lib().fhe_serve_submit(self.h, request_id, it.ctypes.data if it.size else None, it.size, _ptr(UR),
+                                    _ptr(R), _stream(stream))
+        if rc == -8:
+            return False
+        self.ctx._check(rc)
+        return True
+
+    def tick(self, stream=None) -> int:
+        rc = lib().fhe_serve_tick(self.h, _stream(stream))
+        if rc < 0:
+            self.ctx._check(rc)
+        return rc
+
+    def poll(self):
+        ids = np.zeros(4096, dtype=np.int64)
+        n = lib().fhe_serve_poll(self.h, ids.ctypes.data, ids.size)
+        if n < 0:
+            self.ctx._check(n)
+        return [int(x) for x in ids[:n]]
+
+    def take(self, request_id: int, out, stream=None) -> int:
+        lv = ctypes.c_int32()
+        self.ctx._check(lib().fhe_serve_take(self.h, request_id, _ptr(out), ctypes.byref(lv), _stream(stream)))
+        return lv.value

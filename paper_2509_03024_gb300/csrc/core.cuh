@@ -327,6 +327,13 @@ void items_tensor_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vecto
 // target.out (`parts` components) += sum over contributors of a (b unused)
 void items_sum_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<BinItem>& contrib,
                    int parts, int limbs, cudaStream_t s);
+// out = in * value (a signed integer constant, reduced modulo each limb's prime)
+struct ConstItem {
+    const u64* in;
+    u64* out;
+    long long value;
+};
+void items_mul_const(Ctx& c, const std::vector<ConstItem>& it, int parts, int limbs, cudaStream_t s);
 // rescale components [0, parts) from level l to l-1 (out may alias in)
 void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s);
 

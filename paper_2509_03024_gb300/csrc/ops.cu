@@ -183,6 +183,29 @@ __global__ void mul_plain_items_kernel(const BinItem* __restrict__ tab, int item
     }
 }
 
+__device__ __forceinline__ u64 signed_mod_q(long long v, u64 q) {
+    if (v >= 0) return (u64)v % q;
+    u64 m = (u64)(-(v + 1)) % q;
+    return q - 1 - m;
+}
+
+__global__ void mul_const_items_kernel(const ConstItem* __restrict__ tab, int items, int parts, int limbs,
+                                       int log_n, size_t part_words, const Prime* __restrict__ pr) {
+    const size_t per = (size_t)parts * limbs << (log_n - 1);
+    ITEM_LOOP(items) {
+        const ConstItem t = tab[it];
+        PIdx x = pidx(e, log_n - 1, limbs);
+        size_t o = off2(x.part, x.limb, log_n, part_words);
+        const Prime P = pr[x.limb];
+        const u64 cv = signed_mod_q(t.value, P.q);
+        ulonglong2 va = reinterpret_cast<const ulonglong2*>(t.in + o)[x.k2];
+        ulonglong2 r;
+        r.x = mul_mod(va.x, cv, P);
+        r.y = mul_mod(va.y, cv, P);
+        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = r;
+    }
+}
+
 __device__ __forceinline__ void tensor_pair(const u64* a, const u64* b, size_t o, size_t pw, int k2,
                                             const Prime& P, ulonglong2& d0, ulonglong2& d1, ulonglong2& d2) {
     ulonglong2 a0 = reinterpret_cast<const ulonglong2*>(a + o)[k2];
@@ -540,6 +563,18 @@ void items_mul_plain(Ctx& c, const std::vector<BinItem>& it, int parts, int limb
                                                                            c.log_n, (size_t)(c.L + 1) * c.n,
                                                                            c.d_primes);
     CK(cudaGetLastError());
+    }
+}
+
+void items_mul_const(Ctx& c, const std::vector<ConstItem>& it, int parts, int limbs, cudaStream_t s) {
+    if (it.empty()) return;
+    const ConstItem* d = upload(c, it, s);
+    size_t per = (size_t)parts * limbs * c.n / 2;
+    {
+        LaunchScope _ls(c.prof, K_ELEMENTWISE, 2.0 * 8 * per * 2 * it.size(), s);
+        mul_const_items_kernel<<<grid2(per, (int)it.size()), kThreads, 0, s>>>(d, (int)it.size(), parts, limbs, c.log_n,
+                                                                              (size_t)(c.L + 1) * c.n, c.d_primes);
+        CK(cudaGetLastError());
     }
 }
 

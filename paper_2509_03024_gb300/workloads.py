@@ -48,6 +48,7 @@ PRESETS = {
     "t10": CkksPreset("t10", 10, (60, 40, 40), (60,), 40),
     "t11a2": CkksPreset("t11a2", 11, (50,) * 5, (60, 60), 50),
     "t12": CkksPreset("t12", 12, (60, 40, 40, 40, 40), (60,), 40),
+    "t10s": CkksPreset("t10s", 10, (50,) * 13, (60, 60, 60), 50),
 }
 
 

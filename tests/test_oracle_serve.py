@@ -1,0 +1,52 @@
+"""Pins of the oracle's served fold-in + predict (CPU)."""
+import numpy as np
+
+from oracle import ckks, mf, serve
+
+
+def test_fold_in_fp64_hand_checked():
+    V = np.array([[1.0, 0.0], [0.0, 2.0], [1.0, 1.0]])
+    u0 = np.array([0.5, 0.0])
+    items, ratings = [0, 1], [1.0, 2.0]
+    # e = (1 - 0.5, 2 - 0) = (0.5, 2); u <- u (1 - .1 * .5 * 2) + .1 (0.5 v0 + 2 v1) = (0.45, 0) + (0.05, 0.4)
+    u, pred = serve.fold_in_fp64(u0, V, items, ratings, 1, 0.1, 0.5)
+    assert np.allclose(u, [0.5, 0.4], atol=1e-15)
+    assert np.allclose(pred, V @ np.array([0.5, 0.4]), atol=1e-15)
+
+
+def test_fold_in_fp64_is_the_mf_user_update_with_items_fixed():
+    rng = np.random.default_rng(1)
+    V = rng.normal(size=(9, 3))
+    u0 = rng.normal(size=3)
+    items = np.array([1, 4, 7])
+    ratings = np.array([3.0, 5.0, 1.0])
+    u, _ = serve.fold_in_fp64(u0, V, items, ratings, 1, 0.05, 0.1)
+    U2, _ = mf.mf_epoch_fp64(u0[None], V, [0, 0, 0], items, ratings, 0.05, 0.1)
+    assert np.allclose(u, U2[0], atol=1e-14)
+
+
+def test_encrypted_request_matches_fp64():
+    prm = ckks.Params(9, (50,) * 8, (60, 60), 50)
+    he = ckks.Ckks(prm)
+    k, m = 3, 90
+    kp, w, B = serve.layout(k, prm.slots)
+    n_vb = -(-m // B)
+    steps = [1 << t for t in range(mf.highest_bit(kp))] + [(1 << t) * w for t in range(mf.highest_bit(B))] + [-kp]
+    he.keygen(3, steps)
+    rng = np.random.default_rng(2)
+    V = rng.normal(0, 0.3, (m, k))
+    dummy = mf.build_plan(1, m, k, [0], [0], [1.0], prm.slots)
+    VD = [he.encrypt(mf.pack_factors(V, dummy, c), prm.top, 1000 + c) for c in range(n_vb)]
+    items = np.sort(rng.choice(m, 12, replace=False))
+    ratings = rng.integers(1, 6, 12).astype(float)
+    u0 = rng.normal(0, 0.1, k)
+    UR, R = serve.encrypt_request(he, u0, items, ratings, k, n_vb, 77)
+    Uf, P = serve.serve_request(he, UR, R, VD, items, k, 3, 0.05, 0.02)
+    assert Uf.level == prm.top - 6 and P[0].level == prm.top - 7
+    u_ref, pred_ref = serve.fold_in_fp64(u0, V, items, ratings, 3, 0.05, 0.02)
+    z = he.decrypt(Uf)
+    for a in (0, B // 2, B - 1):   # every block holds the doubled user vector
+        assert np.abs(z[a * w: a * w + k] - u_ref).max() < 1e-6
+        assert np.abs(z[a * w + kp: a * w + kp + k] - u_ref).max() < 1e-6
+    pred = np.concatenate([he.decrypt(P[c])[::w][:B] for c in range(n_vb)])[:m]
+    assert np.abs(pred - pred_ref).max() < 1e-6
