@@ -155,6 +155,23 @@ int fhe_relinearize(fhe_ctx* ctx, const uint64_t* in3, uint64_t* out, int32_t co
 /* Exact rescale (divide-and-round by q_level): level -> level-1. out may equal ct. */
 int fhe_rescale(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, int32_t level,
                 void* stream);
+/* Rescale of ONE ciphertext (as fhe_rescale with count = 1, same result)
+ * without any allocation. The paper has no counterpart: this entry point is
+ * for callers that cannot let a library allocate while they run, e.g. an
+ * application that owns all device memory through its own allocator, or a
+ * latency-critical loop where a cudaMalloc / cudaFree (which may synchronise
+ * the device) is not acceptable. It calls no cudaMalloc, cudaFree or other
+ * allocating routine; its scratch space is a 16 MiB array compiled into the
+ * library (held on every GPU that loads the library until the process exits).
+ * Limit: 2 * N * (level + 1) <= 2^21, e.g. level <= 15 at N = 2^15 or level <= 7
+ * at N = 2^16; larger inputs are rejected with FHE_ERR_INVALID_ARG. The first
+ * call on a device looks up the scratch array's device address (once per
+ * device); make that first call before any stream capture. All calls share
+ * the one scratch array: two calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and corrupt each other's results;
+ * order them on one stream. ct: device, level `level`; out: device, receives
+ * level - 1 (may equal ct). */
+int fhe_rescale_noalloc(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t level, void* stream);
 /* Left slot rotation by `step` (negative = right): automorphism X -> X^(5^step)
  * then key switching with that step's rotation key. out must not alias ct. */
 int fhe_rotate(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, int32_t level,

@@ -28,7 +28,7 @@ EXPORTS = [
     "fhe_ctx_create", "fhe_ctx_destroy", "fhe_last_error", "fhe_ctx_get_info", "fhe_ctx_get_primes",
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
-    "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale",
+    "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
     "fhe_rotate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
             "fhe_tensor": [vp, vp, vp, vp, i32, i32, vp],
             "fhe_relinearize": [vp, vp, vp, i32, i32, vp],
             "fhe_rescale": [vp, vp, vp, i32, i32, vp],
+            "fhe_rescale_noalloc": [vp, vp, vp, i32, vp],
             "fhe_rotate": [vp, vp, vp, i32, i32, i32, vp],
             "fhe_profile_begin": [vp, i32],
             "fhe_profile_end": [vp, vp, i32],
@@ -263,6 +264,10 @@ class Context:
 
     def rescale(self, ct, out, count: int, level: int, stream=None):
         self._check(lib().fhe_rescale(self.h, _ptr(ct), _ptr(out), count, level, _stream(stream)))
+
+    def rescale_noalloc(self, ct, out, level: int, stream=None):
+        """Rescale one ciphertext using only the library's static scratch (no allocation)."""
+        self._check(lib().fhe_rescale_noalloc(self.h, _ptr(ct), _ptr(out), level, _stream(stream)))
 
     def mul_relin_rescale(self, a, b, out, count: int, level: int, stream=None):
         self._check(lib().fhe_mul_relin_rescale(self.h, _ptr(a), _ptr(b), _ptr(out), count, level,
