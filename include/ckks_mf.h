@@ -121,6 +121,16 @@ int fhe_encrypt_coeffs(fhe_ctx* ctx, const int64_t* coeffs_dev, int32_t level, u
 int fhe_decrypt(fhe_ctx* ctx, const uint64_t* ct, int32_t level, double* slots, size_t n_slots,
                 void* stream);
 
+/* Key-holder refresh (the CSP role of Sec. III-B; the paper's runs of 20
+ * iterations exceed one leveled chain): each of `count` ciphertexts at `level`
+ * is decrypted to its exact integer plaintext (centred, from limbs 0..min(level,1),
+ * as fhe_decrypt) and encrypted again at the top level with nonce
+ * nonce_base + t. No floating-point decode is involved, so the result is
+ * reproducible bit for bit. out (device, count ciphertexts) may equal ct.
+ * FHE_ERR_INVALID_ARG if a plaintext coefficient does not fit in int64. */
+int fhe_refresh(fhe_ctx* ctx, const uint64_t* ct, int32_t count, int32_t level, uint64_t nonce_base, uint64_t* out,
+                void* stream);
+
 /* ------------------------------------------------------------------ ring and ciphertext primitives */
 
 /* In-place forward / inverse negacyclic NTT of `count` polynomials of

@@ -407,6 +407,12 @@ class Ckks:
                 out.append(v - Q if v > Q // 2 else v)
         return out
 
+    def refresh(self, ct: Ciphertext, nonce: int) -> Ciphertext:
+        """Key-holder refresh: the exact integer plaintext m = c0 + c1 s (centred, from the
+        lowest two limbs as in decryption) re-encrypted at the top level with `nonce`."""
+        m = np.array(self.decrypt_coeffs(ct), dtype=object)
+        return self.encrypt_coeffs(m, self.prm.top, nonce)
+
     def decrypt(self, ct: Ciphertext, count: Optional[int] = None) -> np.ndarray:
         return self.enc.decode(self.decrypt_coeffs(ct), count=count)
 

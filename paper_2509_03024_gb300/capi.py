@@ -27,7 +27,7 @@ ERRORS = {
 EXPORTS = [
     "fhe_ctx_create", "fhe_ctx_destroy", "fhe_last_error", "fhe_ctx_get_info", "fhe_ctx_get_primes",
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
-    "fhe_decrypt", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
+    "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
     "fhe_rotate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "fhe_encrypt": [vp, vp, sz, i32, u64, vp, vp],
             "fhe_encrypt_coeffs": [vp, vp, i32, u64, vp, vp],
             "fhe_decrypt": [vp, vp, i32, vp, sz, vp],
+            "fhe_refresh": [vp, vp, i32, i32, u64, vp, vp],
             "fhe_ntt_forward": [vp, vp, i32, i32, vp],
             "fhe_ntt_inverse": [vp, vp, i32, i32, vp],
             "fhe_ct_to_coeff": [vp, vp, i32, i32, vp, vp],
@@ -236,6 +237,9 @@ class Context:
         out = np.zeros(n_slots, dtype=np.float64)
         self._check(lib().fhe_decrypt(self.h, _ptr(ct), level, out.ctypes.data, n_slots, _stream(stream)))
         return out
+
+    def refresh(self, ct, count: int, level: int, nonce_base: int, out, stream=None):
+        self._check(lib().fhe_refresh(self.h, _ptr(ct), count, level, nonce_base, _ptr(out), _stream(stream)))
 
     # ---- primitives
     def ntt_forward(self, polys, count: int, n_limbs: int, stream=None):

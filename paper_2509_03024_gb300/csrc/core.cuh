@@ -43,6 +43,7 @@ void cuda_check(cudaError_t e, const char* what);
 struct Prime {
     u64 q;
     u64 mu;
+    u64 one_s;  // floor(2^64 / q): Shoup companion of 1, for lazy reduction of any 64-bit value
     u32 b;
     u32 pad;
 };
@@ -250,6 +251,8 @@ struct Ctx {
     u64* d_resc = nullptr;            // [L+1][L+1][2] q_l^-1 mod q_i (+ Shoup)
     u64* d_up_inv = nullptr;          // [L+1][L+1][2] digit-local qhat_i^-1 mod q_i at level l
     u64* d_up_hat = nullptr;          // [L+1][L+1][n_ext][2] digit-local qhat_i mod prime t at level l
+    u64* d_up_ninv = nullptr;         // [L+1][L+1][2] N^-1 * qhat_i^-1 mod q_i (ModUp input scaling)
+    u64* d_down_ninv = nullptr;       // [alpha][2]   N^-1 * Phat_k^-1 mod p_k (ModDown input scaling)
     u64* d_down_inv = nullptr;        // [alpha][2]   Phat_k^-1 mod p_k
     u64* d_down_hat = nullptr;        // [alpha][L+1][2] Phat_k mod q_i
     u64* d_pinv = nullptr;            // [L+1][2]     P^-1 mod q_i
@@ -375,6 +378,7 @@ void encrypt_coeffs_device(Ctx& c, const i64* m_dev, size_t m_stride, int count,
 // plaintext materialisation: int64 coefficients -> evaluation domain limbs [0, limbs)
 void materialize_plain(Ctx& c, const i64* m_dev, size_t m_stride, int count, int limbs, u64* out,
                        size_t out_stride, cudaStream_t s);
+void refresh_device(Ctx& c, const u64* ct, int count, int level, u64 nonce_base, u64* out, cudaStream_t s);
 void decrypt_to_slots(Ctx& c, const u64* ct, int level, double* host_slots, size_t n_slots,
                       cudaStream_t s);
 

@@ -63,7 +63,7 @@ u64* Ctx::scratch_u64(const std::string& name, size_t words) {
 Ctx::~Ctx() {
     cudaSetDevice(device);
     cudaDeviceSynchronize();
-    void* bufs[] = {d_primes, d_psi, d_psi_s, d_ipsi, d_ipsi_s, d_ninv, d_tw, d_itw, d_tw2, d_itw2, d_resc, d_up_inv, d_up_hat,
+    void* bufs[] = {d_primes, d_psi, d_psi_s, d_ipsi, d_ipsi_s, d_ninv, d_tw, d_itw, d_tw2, d_itw2, d_up_ninv, d_down_ninv, d_resc, d_up_inv, d_up_hat,
                     d_down_inv, d_down_hat, d_pinv, d_pmod, d_cos, d_sin, d_pow5, d_sk, d_pk, rlk.d};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -143,6 +143,7 @@ static Prime make_prime(u64 q) {
     p.q = q;
     p.b = 64 - __builtin_clzll(q);
     p.mu = (u64)(((u128)1 << (2 * p.b)) / q);
+    p.one_s = h_shoup(1, q);
     p.pad = 0;
     return p;
 }
@@ -320,6 +321,16 @@ static void build_tables(Ctx& c) {
         }
     c.d_up_inv = dupload(up_inv);
     c.d_up_hat = dupload(up_hat);
+    std::vector<u64> up_ninv(up_inv.size(), 0);
+    for (int l = 0; l <= L; l++)
+        for (int i = 0; i <= l; i++) {
+            size_t o = (size_t)l * (L + 1) + i;
+            u64 qi = c.primes[i];
+            u64 v = h_mul(up_inv[2 * o], h_inv((u64)n % qi, qi), qi);
+            up_ninv[2 * o] = v;
+            up_ninv[2 * o + 1] = h_shoup(v, qi);
+        }
+    c.d_up_ninv = dupload(up_ninv);
 
     // ModDown constants
     std::vector<u64> dinv(2 * A), dhat((size_t)2 * A * (L + 1)), pinv(2 * (L + 1)), pmod(L + 1);
@@ -350,6 +361,14 @@ static void build_tables(Ctx& c) {
         pinv[2 * i + 1] = h_shoup(inv, q);
     }
     c.d_down_inv = dupload(dinv);
+    std::vector<u64> dninv(2 * A);
+    for (int k = 0; k < A; k++) {
+        u64 pk = c.primes[L + 1 + k];
+        u64 v = h_mul(dinv[2 * k], h_inv((u64)n % pk, pk), pk);
+        dninv[2 * k] = v;
+        dninv[2 * k + 1] = h_shoup(v, pk);
+    }
+    c.d_down_ninv = dupload(dninv);
     c.d_down_hat = dupload(dhat);
     c.d_pinv = dupload(pinv);
     c.d_pmod = dupload(pmod);
@@ -504,6 +523,32 @@ __global__ void crt_kernel(double* out, const u64* __restrict__ m, int nl, int l
             u128 v = (u128)k * q0 + x0;
             u128 Q = (u128)q0 * q1;
             out[j] = v > Q / 2 ? -(double)(Q - v) : (double)v;
+        }
+    }
+}
+
+// exact centred lift of 1 or 2 limbs to int64 (refresh); flags values outside int64
+__global__ void crt_int64_kernel(i64* out, const u64* __restrict__ m, int nl, int log_n, u64 q0, u64 q1,
+                                 u64 q0inv_mod_q1, int* overflow) {
+    const int n = 1 << log_n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        if (nl == 1) {
+            u64 x = m[j];
+            out[j] = x > q0 / 2 ? -(i64)(q0 - x) : (i64)x;
+        } else {
+            u64 x0 = m[j], x1 = m[n + j];
+            u64 d = x1 >= x0 % q1 ? x1 - x0 % q1 : x1 + q1 - x0 % q1;
+            u64 k = (u64)(((u128)d * q0inv_mod_q1) % q1);
+            u128 v = (u128)k * q0 + x0;
+            u128 Q = (u128)q0 * q1;
+            bool neg = v > Q / 2;
+            u128 mag = neg ? Q - v : v;
+            if (mag >> 63) {
+                atomicOr(overflow, 1);
+                out[j] = 0;
+            } else {
+                out[j] = neg ? -(i64)mag : (i64)mag;
+            }
         }
     }
 }
@@ -674,6 +719,41 @@ void decrypt_to_slots(Ctx& c, const u64* ct, int level, double* host_slots, size
         CK(cudaMemcpyAsync(host_slots, z, sizeof(double) * n_slots, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
+}
+
+// Key-holder refresh of `count` ciphertexts at `level`: exact integer plaintexts (two-limb CRT,
+// as in decryption) re-encrypted at the top level with nonces nonce_base + t. out may equal ct.
+void refresh_device(Ctx& c, const u64* ct, int count, int level, u64 nonce_base, u64* out, cudaStream_t s) {
+    if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
+    if (level < 0 || level > c.L) fail(FHE_ERR_INVALID_ARG, "level out of range");
+    const int n = c.n, nl = std::min(level, 1) + 1;
+    i64* mi = (i64*)c.scratch_bytes("ref_m", sizeof(i64) * (size_t)std::max(count, 1) * n);
+    u64* m = c.scratch_u64("dec_m", (size_t)nl * n);
+    int* flag = (int*)c.scratch_bytes("ref_flag", sizeof(int));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    u64 q0 = c.primes[0], q1 = c.primes[1 % (c.L + 1)];
+    u64 q0i = nl == 2 ? h_inv(q0 % q1, q1) : 0;
+    for (int t = 0; t < count; t++) {
+        {
+            LaunchScope _ls(c.prof, K_ELEMENTWISE, 32.0 * nl * n, s);
+            dec_kernel<<<blocks_for((size_t)nl * n), kT, 0, s>>>(m, ct + (size_t)t * c.ct_words(), (size_t)(c.L + 1) * n,
+                                                                 c.d_sk, nl, c.log_n, c.d_primes);
+            CK(cudaGetLastError());
+        }
+        ntt_inverse(c, poly_batch(m, (size_t)nl * n, 0, 1, 1, 0, nl), s);
+        {
+            LaunchScope _ls(c.prof, K_ENCODE, 8.0 * (nl + 1) * n, s);
+            crt_int64_kernel<<<blocks_for(n), kT, 0, s>>>(mi + (size_t)t * n, m, nl, c.log_n, q0, q1, q0i, flag);
+            CK(cudaGetLastError());
+        }
+    }
+    int h_flag = 0;
+    CK(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h_flag) fail(FHE_ERR_INVALID_ARG, "plaintext coefficient outside int64: cannot refresh");
+    std::vector<u64> nonces;
+    for (int t = 0; t < count; t++) nonces.push_back(nonce_base + (u64)t);
+    encrypt_coeffs_device(c, mi, n, count, c.L, nonces, out, s);
 }
 
 // Hybrid key-switching key for target secret s2 (evaluation domain, [n_ext][N]).
@@ -933,6 +1013,16 @@ int fhe_decrypt(fhe_ctx* ctx, const uint64_t* ct, int32_t level, double* slots, 
         check_ptr(ct, "ct");
         if (n_slots) check_ptr(slots, "slots");
         decrypt_to_slots(ctx->c, ct, level, slots, n_slots, S(stream));
+    });
+}
+
+int fhe_refresh(fhe_ctx* ctx, const uint64_t* ct, int32_t count, int32_t level, uint64_t nonce_base, uint64_t* out,
+                void* stream) {
+    return guarded(ctx, [&] {
+        check_ptr(ct, "ct");
+        check_ptr(out, "out");
+        if (count < 0) fail(FHE_ERR_INVALID_ARG, "negative count");
+        refresh_device(ctx->c, ct, count, level, nonce_base, out, S(stream));
     });
 }
 

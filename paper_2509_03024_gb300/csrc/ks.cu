@@ -1,0 +1,399 @@
+// ks.cu — fused hybrid key switching (Han-Ki 2020) over a batch of items.
+//
+// For one polynomial d at level l (l1 = l+1 limbs, evaluation domain) and a key
+// of dnum digits of alpha limbs, with ext = Q_l u P (next = l1 + alpha limbs):
+//
+//   K1  inverse NTT of d (read through the automorphism of the item); the last
+//       pass stores y_i = c_i * N^-1 * qhat_i^-1 mod q_i (ModUp's first factor),
+//   K2  for every digit j and every target limb x outside D_j: the first pass
+//       of a forward NTT loads sum_{i in D_j} y_i * qhat_i mod p_x (fast base
+//       conversion, Bajard et al. 2016) and the transform yields ModUp_j(d)_x;
+//       the limbs of D_j are d itself and are read from d in K3,
+//   K3  acc_h = sum_j ModUp_j(d) * evk_j[h] over ext (key inner product),
+//   K4  inverse NTT of the alpha special limbs of acc_h; the last pass stores
+//       y_k = c_k * N^-1 * Phat_k^-1 mod p_k,
+//   K5  for every limb i < l1: the first pass of a forward NTT loads
+//       sum_k y_k * Phat_k mod q_i (Conv_{P->Q}); the last pass stores
+//       out_h = (acc_h - conv) * P^-1 + the item's add terms (ModDown).
+//
+// K1, K2, K4, K5 run the register-blocked NTT tiles of ntt_core.cuh over row
+// tables (one descriptor per limb row), so the conversions happen while the
+// tiles are loaded and the combinations while they are stored.
+#include <algorithm>
+#include <cstring>
+
+#include "ntt_core.cuh"
+
+namespace fhe {
+
+namespace {
+
+using nttc::reduce4;
+using nttc::shoup_lazy;
+
+enum LoadMode { LD_PLAIN = 0, LD_GATHER = 1, LD_CONV = 2 };
+enum StoreMode { ST_LAZY = 0, ST_LAST = 1, ST_SCALE = 2, ST_COMBINE = 3 };
+
+struct KsRow {
+    u64* dst;        // the row's buffer (N residues)
+    const u64* src;  // LD_GATHER: source row; LD_CONV: first source limb (limb stride N)
+    const u64* cst;  // LD_CONV: Shoup pair of the first source limb for this row's prime; ST_SCALE: (w, ws)
+    int prime;       // prime index of the row
+    int galois;      // LD_GATHER: automorphism applied on load (1 = none)
+    int src_cnt;     // LD_CONV: number of source limbs
+    int cst_stride;  // LD_CONV: words between consecutive source limbs' constant pairs
+    int item, half, limb;  // ST_COMBINE: output item, component and limb
+    int pad;
+};
+
+// Evaluation slot k holds a(psi^(2 brev(k) + 1)); X -> X^g moves slot k' to slot k
+// with 2 brev(k') + 1 = g (2 brev(k) + 1) mod 2N.
+__device__ __forceinline__ int auto_src(int k, int g, int log_n) {
+    const unsigned sh = 32 - log_n;
+    unsigned bk = __brev((unsigned)k) >> sh;
+    unsigned e = (unsigned)(((unsigned long long)g * (2ull * bk + 1ull)) & ((2ull << log_n) - 1ull));
+    return (int)(__brev((e - 1u) >> 1) >> sh);
+}
+
+struct CombineArgs {
+    const KsItem* items;
+    const u64* acc;  // [items][2][next][N]
+    const u64* pinv; // [L+1][2]
+    int next;
+};
+
+template <int LOAD>
+__device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, const Prime* __restrict__ pr) {
+    if (LOAD == LD_PLAIN) return r.dst[k];
+    if (LOAD == LD_GATHER) return r.src[r.galois == 1 ? (int)k : auto_src((int)k, r.galois, log_n)];
+    // LD_CONV: fully reduced sum of the converted source limbs
+    const u64 p = pr[r.prime].q;
+    u64 acc = 0;
+    for (int i = 0; i < r.src_cnt; i++) {
+        const u64* c = r.cst + (size_t)i * r.cst_stride;
+        u64 t = shoup_lazy(r.src[((size_t)i << log_n) + k], c[0], c[1], p);
+        t = t >= p ? t - p : t;
+        acc += t;
+        acc = acc >= p ? acc - p : acc;
+    }
+    return acc;
+}
+
+template <bool INV, int STORE>
+__device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, u64 q, u64 one_s,
+                                           const u64* __restrict__ ninv, const CombineArgs& ca, int log_n) {
+    if (STORE == ST_LAZY) {
+        r.dst[k] = v;
+        return;
+    }
+    if (STORE == ST_LAST) {
+        if (INV) {
+            u64 t = shoup_lazy(v, ninv[2 * r.prime], ninv[2 * r.prime + 1], q);
+            r.dst[k] = t >= q ? t - q : t;
+        } else {
+            r.dst[k] = nttc::reduce_any(v, q, one_s);
+        }
+        return;
+    }
+    if (STORE == ST_SCALE) {  // inverse transforms only: times the row's constant instead of N^-1
+        u64 t = shoup_lazy(v, r.cst[0], r.cst[1], q);
+        r.dst[k] = t >= q ? t - q : t;
+        return;
+    }
+    // ST_COMBINE (forward): out_h = (acc_h - v) * P^-1 + add terms
+    const KsItem& it = ca.items[r.item];
+    const size_t row_off = (size_t)r.limb << log_n;
+    u64 conv = nttc::reduce_any(v, q, one_s);
+    u64 a = ca.acc[((((size_t)r.item * 2 + r.half) * ca.next + r.limb) << log_n) + k];
+    u64 d = a >= conv ? a - conv : a + q - conv;
+    u64 t = shoup_lazy(d, ca.pinv[2 * r.limb], ca.pinv[2 * r.limb + 1], q);
+    t = t >= q ? t - q : t;
+    if (r.half == 0) {
+        if (it.addP0) {
+            int src = it.galois == 1 ? (int)k : auto_src((int)k, (int)it.galois, log_n);
+            t = add_mod(t, it.addP0[row_off + src], q);
+        }
+        if (it.addI0) t = add_mod(t, it.addI0[row_off + k], q);
+        it.out0[row_off + k] = t;
+    } else {
+        if (it.addI1) t = add_mod(t, it.addI1[row_off + k], q);
+        it.out1[row_off + k] = t;
+    }
+}
+
+// One NTT pass over a row table (PASS 0: column tiles / single pass; PASS 1: row tiles).
+template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE>
+__global__ void __launch_bounds__(R * (1 << LOGM) / 8, (1024 / (R * (1 << LOGM) / 8)) > 0 ? 1024 / (R * (1 << LOGM) / 8) : 1)
+ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, const ulonglong2* __restrict__ tw,
+              const u64* __restrict__ ninv, CombineArgs ca, int log_n) {
+    constexpr int M = 1 << LOGM;
+    constexpr int P = R == 1 ? 1 : R + 1;
+    constexpr int T = R * M / 8;
+    extern __shared__ u64 sm[];
+    const int tid = threadIdx.x;
+    const KsRow r = rows[blockIdx.x];
+    const u64 q = primes[r.prime].q;
+    const ulonglong2* W = tw + ((size_t)r.prime << log_n);
+    const int log_n2 = PASS == 0 ? log_n - LOGM : LOGM;
+    const int S1 = log_n - log_n2;
+    const int t0 = blockIdx.y * R;
+    if (PASS == 0) {
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e / R, qq = e % R;
+            sm[x * P + qq] = load_elem<LOAD>(r, (size_t)(t0 + qq) + ((size_t)x << log_n2), log_n, primes);
+        }
+    } else {
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e & (M - 1), qq = e >> LOGM;
+            sm[x * P + qq] = load_elem<LOAD>(r, ((size_t)(t0 + qq) << LOGM) + x, log_n, primes);
+        }
+    }
+    __syncthreads();
+    if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false>(sm, W, q, S1, t0);
+    else nttc::tile_stages<LOGM, R, INV, PASS, true>(sm, W, q, S1, t0);
+    const u64 one_s = primes[r.prime].one_s;
+    if (PASS == 0) {
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e / R, c = e % R;
+            store_elem<INV, STORE>(r, (size_t)(t0 + c) + ((size_t)x << log_n2), sm[x * P + c], q, one_s, ninv, ca, log_n);
+        }
+    } else {
+#pragma unroll 4
+        for (int e = tid; e < R * M; e += T) {
+            int x = e & (M - 1), c = e >> LOGM;
+            store_elem<INV, STORE>(r, ((size_t)(t0 + c) << LOGM) + x, sm[x * P + c], q, one_s, ninv, ca, log_n);
+        }
+    }
+}
+
+template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE>
+void launch_pass(const Ctx& c, const KsRow* rows, int n_rows, int tiles, const CombineArgs& ca, int cls, double bytes,
+                 cudaStream_t s) {
+    if (n_rows == 0) return;
+    constexpr int T = R * (1 << LOGM) / 8;
+    constexpr size_t smem = sizeof(u64) * (1 << LOGM) * (R == 1 ? 1 : R + 1);
+    const ulonglong2* tw = PASS == 1 ? (INV ? c.d_itw2 : c.d_tw2) : (INV ? c.d_itw : c.d_tw);
+    if (smem > 48 * 1024)
+        CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope _ls(c.prof, cls, bytes, s);
+    ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE><<<dim3(n_rows, tiles), T, smem, s>>>(rows, c.d_primes, tw, c.d_ninv,
+                                                                                        ca, c.log_n);
+    CK(cudaGetLastError());
+}
+
+// A full forward (INV = false) or inverse transform over a row table: the first pass applies
+// LOAD, the last pass applies STORE (single-pass rings do both in one kernel).
+template <bool INV, int LOAD, int STORE>
+void ks_transform(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs& ca, int cls, double bytes,
+                  cudaStream_t s) {
+    constexpr int FIRST_ST = ST_LAZY;
+    switch (c.log_n) {
+#define SINGLE(LG)                                                                        \
+    case LG:                                                                              \
+        launch_pass<LG, 1, INV, 0, LOAD, STORE>(c, rows, n_rows, 1, ca, cls, bytes, s);   \
+        return;
+        SINGLE(9)
+        SINGLE(10)
+        SINGLE(11)
+        SINGLE(12)
+        SINGLE(13)
+#undef SINGLE
+        case 14:
+            if (!INV) {
+                launch_pass<7, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<7, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
+            } else {
+                launch_pass<7, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<7, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
+            }
+            return;
+        case 15:
+            if (!INV) {
+                launch_pass<7, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<8, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
+            } else {
+                launch_pass<8, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<7, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
+            }
+            return;
+        case 16:
+            if (!INV) {
+                launch_pass<8, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<8, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
+            } else {
+                launch_pass<8, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<8, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
+            }
+            return;
+        default: fail(FHE_ERR_INVALID_ARG, "unsupported ring degree");
+    }
+}
+
+// acc[t][h][x][k] = sum_j M_j[x][k] * key_t[j][h][px][k], where M_j[x] = ext[t][j][x] for x
+// outside digit j and the item's input d (through its automorphism) for x in digit j.
+__global__ void ks_inner_kernel(u64* acc, const u64* __restrict__ ext, const KsItem* __restrict__ tab, int items,
+                                int dn, int alpha, int next, int level, int L, int n_ext, int log_n,
+                                const Prime* __restrict__ pr) {
+    const size_t total = (size_t)items * next << (log_n - 1);
+    const int l1 = level + 1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        int k2 = (int)(e & ((1u << (log_n - 1)) - 1));
+        size_t row = e >> (log_n - 1);
+        int x = (int)(row % next), t = (int)(row / next);
+        int px = x < l1 ? x : x + (L - level);
+        const Prime P = pr[px];
+        const KsItem it = tab[t];
+        const int own = x < l1 ? x / alpha : -1;
+        u64 s0x = 0, s0y = 0, s1x = 0, s1y = 0;
+        for (int j = 0; j < dn; j++) {
+            ulonglong2 v;
+            if (j == own) {
+                const u64* d = it.d + ((size_t)x << log_n);
+                int k = 2 * k2;
+                if (it.galois == 1) {
+                    v = reinterpret_cast<const ulonglong2*>(d)[k2];
+                } else {
+                    v.x = d[auto_src(k, (int)it.galois, log_n)];
+                    v.y = d[auto_src(k + 1, (int)it.galois, log_n)];
+                }
+            } else {
+                v = reinterpret_cast<const ulonglong2*>(ext + ((size_t)((t * dn + j) * next + x) << log_n))[k2];
+            }
+            ulonglong2 kb = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
+            ulonglong2 ka = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
+            s0x = add_mod(s0x, mul_mod(v.x, kb.x, P), P.q);
+            s0y = add_mod(s0y, mul_mod(v.y, kb.y, P), P.q);
+            s1x = add_mod(s1x, mul_mod(v.x, ka.x, P), P.q);
+            s1y = add_mod(s1y, mul_mod(v.y, ka.y, P), P.q);
+        }
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] = make_ulonglong2(s0x, s0y);
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] = make_ulonglong2(s1x, s1y);
+    }
+}
+
+inline unsigned grid1(size_t work) {
+    size_t b = (work + 255) / 256;
+    return (unsigned)std::min<size_t>(std::max<size_t>(b, 1), (size_t)1 << 30);
+}
+
+}  // namespace
+
+void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
+    if (all.empty()) return;
+    const int n = c.n, L = c.L, A = c.alpha, l1 = level + 1, next = l1 + A, dn = c.dnum(level);
+    // bound the work area to ~6 GiB per sub-batch
+    const size_t per_item = (size_t)(l1 + dn * next + 2 * next + 2 * A + 2 * l1) * n * sizeof(u64);
+    const int max_items = (int)std::max<size_t>(1, ((size_t)6 << 30) / per_item);
+    for (size_t b0 = 0; b0 < all.size(); b0 += max_items) {
+        const int items = (int)std::min<size_t>(max_items, all.size() - b0);
+        std::vector<KsItem> it(all.begin() + b0, all.begin() + b0 + items);
+        const KsItem* d_items = c.arena.push_vec(it, s);
+        size_t nkeys = 0;
+        {
+            std::vector<const u64*> ks;
+            for (auto& x : it) ks.push_back(x.key);
+            std::sort(ks.begin(), ks.end());
+            nkeys = std::unique(ks.begin(), ks.end()) - ks.begin();
+        }
+        u64* y = c.scratch_u64("ks_y", (size_t)items * l1 * n);
+        u64* ext = c.scratch_u64("ks_ext", (size_t)items * dn * next * n);
+        u64* acc = c.scratch_u64("ks_acc", (size_t)items * 2 * next * n);
+        u64* yP = c.scratch_u64("ks_yp", (size_t)items * 2 * A * n);
+        u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
+        CombineArgs ca{d_items, acc, c.d_pinv, next};
+        const CombineArgs none{nullptr, nullptr, nullptr, 0};
+
+        // K1: y_i = INTT(perm(d_i)) * qhat_i^-1
+        std::vector<KsRow> r1;
+        r1.reserve((size_t)items * l1);
+        for (int t = 0; t < items; t++)
+            for (int i = 0; i < l1; i++) {
+                KsRow r{};
+                r.dst = y + ((size_t)t * l1 + i) * n;
+                r.src = it[t].d + (size_t)i * n;
+                r.cst = c.d_up_ninv + 2 * ((size_t)level * (L + 1) + i);
+                r.prime = i;
+                r.galois = (int)it[t].galois;
+                r1.push_back(r);
+            }
+        const KsRow* d_r1 = c.arena.push_vec(r1, s);
+        ks_transform<true, LD_GATHER, ST_SCALE>(c, d_r1, (int)r1.size(), none, K_NTT_INV, 16.0 * r1.size() * n, s);
+
+        // K2: ModUp_j(d)_x for x outside D_j
+        std::vector<KsRow> r2;
+        r2.reserve((size_t)items * dn * next);
+        for (int t = 0; t < items; t++)
+            for (int j = 0; j < dn; j++) {
+                const int lo = j * A, cnt = std::min(A, l1 - lo);
+                for (int x = 0; x < next; x++) {
+                    if (x >= lo && x < lo + cnt) continue;
+                    const int px = x < l1 ? x : x + (L - level);
+                    KsRow r{};
+                    r.dst = ext + (((size_t)t * dn + j) * next + x) * n;
+                    r.src = y + ((size_t)t * l1 + lo) * n;
+                    r.cst = c.d_up_hat + 2 * (((size_t)level * (L + 1) + lo) * c.n_ext + px);
+                    r.cst_stride = 2 * c.n_ext;
+                    r.src_cnt = cnt;
+                    r.prime = px;
+                    r.galois = 1;
+                    r2.push_back(r);
+                }
+            }
+        const KsRow* d_r2 = c.arena.push_vec(r2, s);
+        ks_transform<false, LD_CONV, ST_LAST>(c, d_r2, (int)r2.size(), none, K_NTT_FWD, 16.0 * r2.size() * n, s);
+
+        // K3: key inner product
+        {
+            LaunchScope _ls(c.prof, K_KS_INNER,
+                            8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next),
+                            s);
+            ks_inner_kernel<<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(acc, ext, d_items, items, dn, A,
+                                                                                     next, level, L, c.n_ext, c.log_n,
+                                                                                     c.d_primes);
+            CK(cudaGetLastError());
+        }
+
+        // K4: y_k = INTT(acc_h special limb k) * Phat_k^-1
+        std::vector<KsRow> r4;
+        for (int t = 0; t < items; t++)
+            for (int h = 0; h < 2; h++)
+                for (int kk = 0; kk < A; kk++) {
+                    KsRow r{};
+                    r.dst = yP + (((size_t)t * 2 + h) * A + kk) * n;
+                    r.src = acc + (((size_t)t * 2 + h) * next + l1 + kk) * n;
+                    r.cst = c.d_down_ninv + 2 * kk;
+                    r.prime = L + 1 + kk;
+                    r.galois = 1;
+                    r4.push_back(r);
+                }
+        const KsRow* d_r4 = c.arena.push_vec(r4, s);
+        ks_transform<true, LD_GATHER, ST_SCALE>(c, d_r4, (int)r4.size(), none, K_NTT_INV, 16.0 * r4.size() * n, s);
+
+        // K5: out_h = (acc_h - NTT(Conv_{P->Q}(y))) * P^-1 + add terms
+        std::vector<KsRow> r5;
+        for (int t = 0; t < items; t++)
+            for (int h = 0; h < 2; h++)
+                for (int i = 0; i < l1; i++) {
+                    KsRow r{};
+                    r.dst = conv + (((size_t)t * 2 + h) * l1 + i) * n;
+                    r.src = yP + ((size_t)t * 2 + h) * A * n;
+                    r.cst = c.d_down_hat + 2 * (size_t)i;
+                    r.cst_stride = 2 * (L + 1);
+                    r.src_cnt = A;
+                    r.prime = i;
+                    r.galois = 1;
+                    r.item = t;
+                    r.half = h;
+                    r.limb = i;
+                    r5.push_back(r);
+                }
+        const KsRow* d_r5 = c.arena.push_vec(r5, s);
+        ks_transform<false, LD_CONV, ST_COMBINE>(c, d_r5, (int)r5.size(), ca, K_NTT_FWD, 16.0 * r5.size() * n, s);
+    }
+}
+
+}  // namespace fhe

@@ -19,11 +19,14 @@
 // lazy in the style of Harvey (2014): forward values stay in [0, 4q), inverse
 // values in [0, 2q); twiddle products use Shoup's precomputed quotient and no
 // final correction; the last pass reduces to [0, q).
-#include "core.cuh"
+#include "ntt_core.cuh"
 
 namespace fhe {
 
 namespace {
+
+using nttc::reduce4;
+using nttc::shoup_lazy;
 
 struct RowPtr {
     u64* p;
@@ -43,35 +46,6 @@ __device__ __forceinline__ RowPtr row_ptr(const PolyBatch& pb, int row, int log_
     return r;
 }
 
-// Shoup product without the final correction: a * w mod q in [0, 2q) for any a < 2^64.
-__device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
-    u64 qh = __umul64hi(a, ws);
-    return a * w - qh * q;
-}
-
-// Forward CT butterfly on values in [0, 4q): X <- X + W Y, Y <- X - W Y (lazy, outputs in [0, 4q)).
-__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 ws, u64 q, u64 q2) {
-    u64 a = x >= q2 ? x - q2 : x;
-    u64 t = shoup_lazy(y, w, ws, q);
-    x = a + t;
-    y = a + q2 - t;
-}
-
-// Inverse GS butterfly on values in [0, 2q): X <- X + Y, Y <- (X - Y) W (outputs in [0, 2q)).
-__device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 ws, u64 q, u64 q2) {
-    u64 s = x + y;
-    s = s >= q2 ? s - q2 : s;
-    u64 d = x + q2 - y;
-    x = s;
-    y = shoup_lazy(d, w, ws, q);
-}
-
-__device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
-    u64 q2 = q << 1;
-    x = x >= q2 ? x - q2 : x;
-    return x >= q ? x - q : x;
-}
-
 // One tile: R sub-transforms of M = 2^LOGM points.
 // PASS 0: column transforms (stages [0, LOGM) of the full ring), tile = R consecutive columns;
 //         with LOGM = log N and R = 1 this is the whole single-pass transform.
@@ -88,7 +62,6 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     const int tid = threadIdx.x;
     const RowPtr rp = row_ptr(pb, blockIdx.x, log_n);
     const u64 q = primes[rp.prime].q;
-    const u64 q2 = q << 1;
     const ulonglong2* W = tw + ((size_t)rp.prime << log_n);
     const int log_n2 = PASS == 0 ? log_n - LOGM : LOGM;  // row length of the N1 x N2 view
     const int S1 = log_n - log_n2;                       // column stages
@@ -110,62 +83,10 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     }
     __syncthreads();
 
-    const int qq = tid % R;  // sub-transform of this thread
-    const int g = tid / R;   // 8-element group within the sub-transform
-    const int row_off = PASS == 1 ? t0 + qq : 0;
-    u64 v[8];
-
-    // radix-8 blocks of stages; forward runs stages 0..LOGM-1, inverse LOGM-1..0
-    constexpr int NB = (LOGM + 2) / 3;
-#pragma unroll
-    for (int bi = 0; bi < NB; bi++) {
-        // forward: block bi covers stages [3 bi, min(3 bi + 3, LOGM));
-        // inverse: the same blocks in reverse order, stages inside a block descending
-        const int blk_id = INV ? NB - 1 - bi : bi;
-        const int s0 = 3 * blk_id;
-        const int b = (LOGM - s0) < 3 ? (LOGM - s0) : 3;
-        const int d = M >> (s0 + b);
-        const int base = (g / d) * (8 * d) + (g % d);
-#pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = sm[(base + u * d) * P + qq];
-        // Twiddle of the pair (u, u + dist) at block stage j: its group index at stage s0 + j is
-        // tb * 2^j + (u >> (b - j)), with tb = base >> (LOGM - s0) the thread's group at s0.
-        const int tb = base >> (LOGM - s0);
-        if (!INV) {
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                if (j >= b) break;
-                const int s = s0 + j;
-                const int dist = 1 << (b - 1 - j);
-#pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    if (u & dist) continue;
-                    const int grp = (tb << j) + (u >> (b - j));
-                    const int wi = PASS == 1 ? ((((1 << s) - 1 + grp)) << S1) + row_off : (1 << s) + grp;
-                    const ulonglong2 w = W[wi];
-                    ct_bfly(v[u], v[u + dist], w.x, w.y, q, q2);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 2; j >= 0; j--) {
-                if (j >= b) continue;
-                const int s = s0 + j;
-                const int dist = 1 << (b - 1 - j);
-#pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    if (u & dist) continue;
-                    const int grp = (tb << j) + (u >> (b - j));
-                    const int wi = PASS == 1 ? ((((1 << s) - 1 + grp)) << S1) + row_off : (1 << s) + grp;
-                    const ulonglong2 w = W[wi];
-                    gs_bfly(v[u], v[u + dist], w.x, w.y, q, q2);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++) sm[(base + u * d) * P + qq] = v[u];
-        __syncthreads();
-    }
+    // forward transforms of primes below 2^58 skip the per-butterfly reduction (values < 33 q)
+    if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false>(sm, W, q, S1, t0);
+    else nttc::tile_stages<LOGM, R, INV, PASS, true>(sm, W, q, S1, t0);
+    const u64 one_s = primes[rp.prime].one_s;
 
     // store (coalesced)
     const u64 ni = ninv[2 * rp.prime], nis = ninv[2 * rp.prime + 1];
@@ -179,7 +100,7 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
                     u64 r = shoup_lazy(val, ni, nis, q);
                     val = r >= q ? r - q : r;
                 } else {
-                    val = reduce4(val, q);
+                    val = nttc::reduce_any(val, q, one_s);
                 }
             }
             rp.p[(size_t)(t0 + c) + ((size_t)x << log_n2)] = val;
@@ -194,7 +115,7 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
                     u64 t = shoup_lazy(val, ni, nis, q);
                     val = t >= q ? t - q : t;
                 } else {
-                    val = reduce4(val, q);
+                    val = nttc::reduce_any(val, q, one_s);
                 }
             }
             rp.p[((size_t)(t0 + r) << LOGM) + x] = val;

@@ -391,140 +391,6 @@ __global__ void rescale_combine_kernel(const UnItem* __restrict__ tab, const u64
     }
 }
 
-// ---------------------------------------------------------------- key switching
-
-// coef[t][i][k] = d_t[i][perm(k)]
-__global__ void ks_gather_kernel(u64* coef, const KsItem* __restrict__ tab, int items, int l1, int log_n) {
-    const size_t per = (size_t)l1 << log_n;
-    ITEM_LOOP(items) {
-        const KsItem t = tab[it];
-        int k = (int)(e & ((1u << log_n) - 1));
-        int i = (int)(e >> log_n);
-        int src = t.galois == 1 ? k : auto_src(k, t.galois, log_n);
-        coef[(size_t)it * per + e] = t.d[((size_t)i << log_n) + src];
-    }
-}
-
-// ext[t][j][x][k] = sum_{i in D_j} [coef_i * qhat_i^-1]_{q_i} * qhat_i  mod p_x, x < next
-__global__ void modup_kernel(u64* ext, const u64* __restrict__ coef, int items, int level, int dn, int alpha,
-                             int next, int L, int log_n, const Prime* __restrict__ pr,
-                             const u64* __restrict__ up_inv, const u64* __restrict__ up_hat, int n_ext) {
-    const size_t total = (size_t)items * dn << log_n;
-    const int l1 = level + 1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int k = (int)(e & ((1u << log_n) - 1));
-        size_t row = e >> log_n;
-        int j = (int)(row % dn), t = (int)(row / dn);
-        int i0 = j * alpha;
-        int i1 = min(i0 + alpha, l1);
-        u64 y[8];
-        for (int i = i0; i < i1; i++) {
-            const u64* ui = up_inv + 2 * ((size_t)level * (L + 1) + i);
-            y[i - i0] = mul_shoup(coef[(((size_t)t * l1 + i) << log_n) + k], ui[0], ui[1], pr[i].q);
-        }
-        u64* dst = ext + ((size_t)(t * dn + j) * next << log_n) + k;
-        for (int x = 0; x < next; x++) {
-            int px = x < l1 ? x : x + (L - level);
-            u64 p = pr[px].q;
-            u64 acc = 0;
-            for (int i = i0; i < i1; i++) {
-                const u64* h = up_hat + 2 * (((size_t)level * (L + 1) + i) * n_ext + px);
-                acc = add_mod(acc, mul_shoup(y[i - i0], h[0], h[1], p), p);
-            }
-            dst[(size_t)x << log_n] = acc;
-        }
-    }
-}
-
-// acc[t][h][x][k] = sum_j ext[t][j][x][k] * key_t[j][h][px][k]
-__global__ void ks_inner_kernel(u64* acc, const u64* __restrict__ ext, const KsItem* __restrict__ tab, int items,
-                                int dn, int next, int level, int L, int n_ext, int log_n,
-                                const Prime* __restrict__ pr) {
-    const size_t total = (size_t)items * next << (log_n - 1);
-    const int l1 = level + 1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int k2 = (int)(e & ((1u << (log_n - 1)) - 1));
-        size_t row = e >> (log_n - 1);
-        int x = (int)(row % next), t = (int)(row / next);
-        int px = x < l1 ? x : x + (L - level);
-        const Prime P = pr[px];
-        const u64* key = tab[t].key;
-        u64 s0x = 0, s0y = 0, s1x = 0, s1y = 0;
-        for (int j = 0; j < dn; j++) {
-            ulonglong2 v = reinterpret_cast<const ulonglong2*>(ext + ((size_t)((t * dn + j) * next + x) << log_n))[k2];
-            ulonglong2 kb = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
-            ulonglong2 ka = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
-            s0x = add_mod(s0x, mul_mod(v.x, kb.x, P), P.q);
-            s0y = add_mod(s0y, mul_mod(v.y, kb.y, P), P.q);
-            s1x = add_mod(s1x, mul_mod(v.x, ka.x, P), P.q);
-            s1y = add_mod(s1y, mul_mod(v.y, ka.y, P), P.q);
-        }
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] = make_ulonglong2(s0x, s0y);
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] = make_ulonglong2(s1x, s1y);
-    }
-}
-
-// conv[t][h][i][k] = sum_kk [accP_kk * Phat_kk^-1]_{p_kk} * Phat_kk  mod q_i, i <= level
-__global__ void moddown_kernel(u64* conv, const u64* __restrict__ acc, int items, int level, int alpha, int next,
-                               int L, int log_n, const Prime* __restrict__ pr, const u64* __restrict__ down_inv,
-                               const u64* __restrict__ down_hat) {
-    const size_t total = (size_t)items * 2 << log_n;
-    const int l1 = level + 1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int k = (int)(e & ((1u << log_n) - 1));
-        size_t th = e >> log_n;  // t*2 + h
-        u64 y[8];
-        for (int kk = 0; kk < alpha; kk++) {
-            u64 p = pr[L + 1 + kk].q;
-            y[kk] = mul_shoup(acc[((th * next + l1 + kk) << log_n) + k], down_inv[2 * kk], down_inv[2 * kk + 1], p);
-        }
-        for (int i = 0; i < l1; i++) {
-            u64 q = pr[i].q;
-            u64 s = 0;
-            for (int kk = 0; kk < alpha; kk++) {
-                const u64* h = down_hat + 2 * ((size_t)kk * (L + 1) + i);
-                s = add_mod(s, mul_shoup(y[kk], h[0], h[1], q), q);
-            }
-            conv[((th * l1 + i) << log_n) + k] = s;
-        }
-    }
-}
-
-// out_h = (acc_h - conv_h) * P^-1 + add terms
-__global__ void ks_final_kernel(const KsItem* __restrict__ tab, const u64* __restrict__ acc,
-                                const u64* __restrict__ conv, int items, int level, int next, int log_n,
-                                const Prime* __restrict__ pr, const u64* __restrict__ pinv) {
-    const int l1 = level + 1;
-    const size_t per = (size_t)2 * l1 << log_n;
-    ITEM_LOOP(items) {
-        const KsItem t = tab[it];
-        int k = (int)(e & ((1u << log_n) - 1));
-        size_t row = e >> log_n;
-        int i = (int)(row % l1);
-        int h = (int)(row / l1);
-        size_t th = (size_t)it * 2 + h;
-        u64 q = pr[i].q;
-        u64 a = acc[((th * next + i) << log_n) + k];
-        u64 cv = conv[((th * l1 + i) << log_n) + k];
-        u64 v = mul_shoup(sub_mod(a, cv, q), pinv[2 * i], pinv[2 * i + 1], q);
-        size_t o = ((size_t)i << log_n);
-        if (h == 0) {
-            if (t.addP0) {
-                int src = t.galois == 1 ? k : auto_src(k, t.galois, log_n);
-                v = add_mod(v, t.addP0[o + src], q);
-            }
-            if (t.addI0) v = add_mod(v, t.addI0[o + k], q);
-            t.out0[o + k] = v;
-        } else {
-            if (t.addI1) v = add_mod(v, t.addI1[o + k], q);
-            t.out1[o + k] = v;
-        }
-    }
-}
-
 }  // namespace
 
 // ============================================================================ launchers
@@ -676,73 +542,6 @@ void k_automorphism_poly(const Ctx& c, u64* out, const u64* in, int limbs, int g
         LaunchScope _ls(c.prof, K_OTHER, 16.0 * limbs * c.n, s);
         automorphism_kernel<<<grid1((size_t)limbs * c.n), kThreads, 0, s>>>(out, in, limbs, c.log_n, galois);
     CK(cudaGetLastError());
-    }
-}
-
-void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
-    if (all.empty()) return;
-    if (c.alpha > 8) fail(FHE_ERR_INVALID_ARG, "at most 8 special primes are supported");
-    const int n = c.n, l1 = level + 1, next = l1 + c.alpha, dn = c.dnum(level);
-    // bound the ModUp expansion buffer to ~2 GiB per sub-batch
-    const size_t per_item = (size_t)(dn * next + 2 * next + 2 * l1 + l1) * n * sizeof(u64);
-    const int max_items = (int)std::max<size_t>(1, ((size_t)6 << 30) / per_item);
-    for (size_t b0 = 0; b0 < all.size(); b0 += max_items) {
-        const int items = (int)std::min<size_t>(max_items, all.size() - b0);
-        std::vector<KsItem> it(all.begin() + b0, all.begin() + b0 + items);
-        const KsItem* d = upload(c, it, s);
-        size_t nkeys = 0;
-        {
-            std::vector<const u64*> ks;
-            for (auto& x : it) ks.push_back(x.key);
-            std::sort(ks.begin(), ks.end());
-            nkeys = std::unique(ks.begin(), ks.end()) - ks.begin();
-        }
-        u64* coef = c.scratch_u64("ks_coef", (size_t)items * l1 * n);
-        u64* ext = c.scratch_u64("ks_ext", (size_t)items * dn * next * n);
-        u64* acc = c.scratch_u64("ks_acc", (size_t)items * 2 * next * n);
-        u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
-        {
-        LaunchScope _ls(c.prof, K_KS_GATHER, 16.0 * items * l1 * n, s);
-        ks_gather_kernel<<<grid2((size_t)l1 * n, items), kThreads, 0, s>>>(coef, d, items, l1, c.log_n);
-        CK(cudaGetLastError());
-    }
-        ntt_inverse(c, poly_batch(coef, (size_t)l1 * n, 0, items, 1, 0, l1), s);
-        {
-        LaunchScope _ls(c.prof, K_MODUP, 8.0 * items * n * (l1 + (double)dn * next), s);
-        modup_kernel<<<grid1((size_t)items * dn * n), kThreads, 0, s>>>(ext, coef, items, level, dn, c.alpha, next,
-                                                                        c.L, c.log_n, c.d_primes, c.d_up_inv,
-                                                                        c.d_up_hat, c.n_ext);
-        CK(cudaGetLastError());
-    }
-        PolyBatch pe = poly_batch(ext, (size_t)dn * next * n, (size_t)next * n, items, dn, 0, next);
-        pe.split = l1;
-        pe.jump = c.L - level;
-        ntt_forward(c, pe, s);
-        {
-        LaunchScope _ls(c.prof, K_KS_INNER, 8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next), s);
-        ks_inner_kernel<<<grid1((size_t)items * next * n / 2), kThreads, 0, s>>>(acc, ext, d, items, dn, next,
-                                                                                 level, c.L, c.n_ext, c.log_n,
-                                                                                 c.d_primes);
-        CK(cudaGetLastError());
-    }
-        PolyBatch pa = poly_batch(acc, (size_t)2 * next * n, (size_t)next * n, items, 2, l1, c.alpha);
-        pa.split = l1;
-        pa.jump = c.L - level;
-        ntt_inverse(c, pa, s);
-        {
-        LaunchScope _ls(c.prof, K_MODDOWN, 8.0 * items * 2 * n * (c.alpha + l1), s);
-        moddown_kernel<<<grid1((size_t)items * 2 * n), kThreads, 0, s>>>(conv, acc, items, level, c.alpha, next,
-                                                                         c.L, c.log_n, c.d_primes, c.d_down_inv,
-                                                                         c.d_down_hat);
-        CK(cudaGetLastError());
-    }
-        ntt_forward(c, poly_batch(conv, (size_t)2 * l1 * n, (size_t)l1 * n, items, 2, 0, l1), s);
-        {
-        LaunchScope _ls(c.prof, K_KS_FINAL, 8.0 * items * 2 * l1 * n * 3, s);
-        ks_final_kernel<<<grid2((size_t)2 * l1 * n, items), kThreads, 0, s>>>(d, acc, conv, items, level, next,
-                                                                              c.log_n, c.d_primes, c.d_pinv);
-        CK(cudaGetLastError());
-    }
     }
 }
 

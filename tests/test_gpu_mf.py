@@ -165,3 +165,34 @@ def test_csr_pack_rejects_bad_input():
     # an empty matrix is a valid plan with no groups
     p = capi.MfPlan(ctx, 3, 3, 2, [0, 0, 0, 0], [], [])
     assert p.info.n_groups == 0
+
+
+def test_refresh_then_epoch_bit_exact():
+    """epoch, epoch, key-holder refresh, epoch: every ciphertext equals the oracle's."""
+    from paper_2509_03024_gb300 import train as T
+    csr, U, V = _small_case(seed=9, n=45, m=35, density=0.07, k=3)
+    ctx, plan, he, oplan, emf, UD0, VD0, oUD, oVD = _setup("t11a2", csr, 3, U, V)
+    lr, lam = 0.02, 0.01
+    UD, VD, level, times, refreshes = T.run(ctx, plan, U, V, 3, lr, lam)
+    assert refreshes == 1 and level == ctx.top - 2
+    per = plan.n_ub + plan.n_vb
+    lv = he.prm.top
+    for ep in range(3):
+        if lv < 2:
+            base = T.REFRESH_NONCE_BASE + 1 * per
+            oUD = [he.refresh(c, base + b) for b, c in enumerate(oUD)]
+            oVD = [he.refresh(c, base + plan.n_ub + j) for j, c in enumerate(oVD)]
+            lv = he.prm.top
+        oUD, oVD = emf.epoch(oUD, oVD, lr, lam)
+        lv -= 2
+    got = to_coeff(ctx, UD, level, plan.n_ub)
+    for t, o in enumerate(oUD):
+        assert_ct_equal(got[t], o, f"U[{t}] after refresh")
+    got = to_coeff(ctx, VD, level, plan.n_vb)
+    for t, o in enumerate(oVD):
+        assert_ct_equal(got[t], o, f"V[{t}] after refresh")
+    rows, cols, vals = csr.triples()
+    Ur, Vr = U, V
+    for _ in range(3):
+        Ur, Vr = mf.mf_epoch_fp64(Ur, Vr, rows, cols, vals, lr, lam)
+    assert np.abs(plan.decrypt_factors(0, UD, level, csr.n) - Ur).max() < 1e-3
