@@ -35,6 +35,9 @@ METRIC = "encrypted MF ratings/sec, served vs one-by-one on 1 GB300; p50/p99 lat
 # at 20 32-bit instructions per lazy 64-bit Shoup butterfly (product high half 5, two low halves 6,
 # subtraction 2, range reduction 4, sum and difference 3)
 ALU_PEAK_GBFLY = 152 * 128 * 2.07 / 20.0
+# DRAM bytes per limb row of a forward NTT pass at N = 2^15, from one ncu capture of the fused
+# ModUp passes (64 rotations at level 7, 2048 rows per pass): (614 MB + 1020 MB) / 2 passes / 2048
+NCU_FWD_DRAM_BYTES_PER_ROW = (614.0e6 + 1020.0e6) / 2 / 2048
 UNIT = "ratings/s"
 SEED = 20250903
 LR, LAM, K_RANK = 0.005, 0.02, 10
@@ -377,8 +380,12 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
         bfly = (alg_bytes / launches) / 16.0 * (log_n / 4.0)
         achieved = bfly / avg_s / 1e9
         peak = ALU_PEAK_GBFLY
+        rows_per_launch = (alg_bytes / launches) / (16.0 * 2 ** log_n)
+        traffic = NCU_FWD_DRAM_BYTES_PER_ROW * rows_per_launch if name == "ntt_forward" else None
         roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Gbfly/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic,
+                    "traffic_source": "ncu dram__bytes_read+write per row of the fused forward passes, scaled "
+                                      "by the rows of the average launch",
                     "peak_source": ("derived: 152 SMs x 128 lanes x 2.07 GHz / 20 32-bit instructions per lazy "
                                     "64-bit Shoup butterfly"),
                     "launches": launches, "avg_launch_us": avg_s * 1e6, "butterflies_per_launch": bfly,
