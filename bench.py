@@ -124,7 +124,7 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
 
-def oracle_sample(train, U, V, groups_sampled: int = 2):
+def oracle_sample(train, U, V, groups_sampled: int = 1):
     """Time the oracle (as it stands) on a bounded sample of the epoch and extrapolate.
 
     Sample: the per-group work (product, relinearise, rescale, rotate-and-sum,
@@ -137,7 +137,7 @@ def oracle_sample(train, U, V, groups_sampled: int = 2):
     rows, cols, vals = train.triples()
     he = ckks.Ckks(ckks.Params.from_preset(PRESETS["paper"]))
     plan = mf.build_plan(train.n, train.m, K_RANK, rows, cols, vals, he.prm.slots)
-    steps = [1 << t for t in range(mf.highest_bit(plan.kp))] + [plan.w]
+    steps = mf.rotsum_steps(plan.kp) + [plan.w]
     he.keygen(SEED, steps)
     emf = mf.EncryptedMF(he, plan)
     top = he.prm.top

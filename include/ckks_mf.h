@@ -186,6 +186,17 @@ int fhe_rescale_noalloc(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t
  * then key switching with that step's rotation key. out must not alias ct. */
 int fhe_rotate(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, int32_t level,
                int32_t step, void* stream);
+/* In-block rotate-and-sum: out = sum_{r=0}^{kp-1} rot(ct, r), the inner-product step of the
+ * paper's encrypted error e = r - <u, v> (Alg. 1) on vectors written twice per block of 2 kp
+ * slots, where every slot x < kp of a block receives the block's sum. For 2 <= kp <= 16 the key
+ * switches are hoisted (Halevi and Shoup 2018): one ModUp of c1, kp - 1 key inner products over
+ * the rotated raised digits, one ModDown. Its bits then differ from a sum of fhe_rotate results
+ * (same plaintext; the noise of one key switch). A power of two kp > 16 runs log2(kp)
+ * rotate-and-adds. Needs the rotation keys of steps 1..kp-1 (kp <= 16) or of the powers of two
+ * below kp. ct, out: device, `count` ciphertexts at `level`. For kp <= 16 out may equal ct;
+ * for kp > 16 ct is overwritten and must not alias out. Other kp: FHE_ERR_INVALID_ARG. */
+int fhe_rotate_sum(fhe_ctx* ctx, uint64_t* ct, uint64_t* out, int32_t count, int32_t level, int32_t kp,
+                   void* stream);
 
 /* ------------------------------------------------------------------ launch accounting */
 

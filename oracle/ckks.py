@@ -460,6 +460,34 @@ class Ckks:
         out = np.stack([ring.rescale(a.c[t], pr) for t in range(a.c.shape[0])])
         return Ciphertext(out, a.level - 1)
 
+    def _key_rows(self, level: int) -> List[int]:
+        """Rows of a key (stored over Q_L u P) that belong to the basis Q_level u P."""
+        prm = self.prm
+        return list(range(level + 1)) + [prm.top + 1 + k for k in range(prm.alpha)]
+
+    def _modup(self, d: np.ndarray, level: int) -> np.ndarray:
+        """ModUp_j(d) for every digit j: fast conversion of the digit-j residues of d to every
+        prime of Q_level u P (Bajard et al. 2016). Shape [dnum, |basis|, N]."""
+        prm = self.prm
+        basis = prm.q[: level + 1] + prm.p
+        ups = []
+        for j in range(prm.dnum(level)):
+            Dj = prm.digit(j, level)
+            ups.append(ring.fast_base_conv(d[Dj], [prm.q[i] for i in Dj], basis))
+        return np.stack(ups)
+
+    def _moddown(self, acc: np.ndarray, level: int) -> np.ndarray:
+        """ModDown(x) = (x_Q - Conv_{P->Q}(x_P)) * P^{-1} mod each q_i."""
+        prm = self.prm
+        qs = prm.q[: level + 1]
+        xq, xp = acc[: level + 1], acc[level + 1:]
+        conv = ring.fast_base_conv(xp, prm.p, qs)
+        diff = self._sub(xq, conv, qs)
+        out = np.empty_like(diff)
+        for i, q in enumerate(qs):
+            out[i] = ring.scalar_mul(diff[i], pow(prm.P % q, -1, q), q)
+        return out
+
     def keyswitch(self, d: np.ndarray, level: int, key: EvalKey) -> Tuple[np.ndarray, np.ndarray]:
         """Hybrid key switch of one polynomial d (level l, [l+1, N]) under key (Han-Ki 2020).
 
@@ -467,27 +495,16 @@ class Ckks:
         acc = sum_j ModUp_j(d) * evk_j; ModDown(x) = (x_Q - Conv_{P->Q}(x_P)) * P^{-1}.
         """
         prm = self.prm
-        qs = prm.q[: level + 1]
-        basis = qs + prm.p
-        key_rows = list(range(level + 1)) + [prm.top + 1 + k for k in range(prm.alpha)]
+        basis = prm.q[: level + 1] + prm.p
+        rows = self._key_rows(level)
         dn = prm.dnum(level)
-        ups = []
-        for j in range(dn):
-            Dj = prm.digit(j, level)
-            ups.append(ring.fast_base_conv(d[Dj], [prm.q[i] for i in Dj], basis))
-        ups = np.stack(ups)  # [dnum, |basis|, N]
+        ups = self._modup(d, level)  # [dnum, |basis|, N]
         halves = []
         for K in (key.b, key.a):
-            Kx = K[:dn][:, key_rows]  # [dnum, |basis|, N]
+            Kx = K[:dn][:, rows]  # [dnum, |basis|, N]
             acc = ring.polydot_rows(np.ascontiguousarray(ups.transpose(1, 0, 2)),
                                     np.ascontiguousarray(Kx.transpose(1, 0, 2)), basis)
-            xq, xp = acc[: level + 1], acc[level + 1:]
-            conv = ring.fast_base_conv(xp, prm.p, qs)
-            diff = self._sub(xq, conv, qs)
-            out = np.empty_like(diff)
-            for i, q in enumerate(qs):
-                out[i] = ring.scalar_mul(diff[i], pow(prm.P % q, -1, q), q)
-            halves.append(out)
+            halves.append(self._moddown(acc, level))
         return halves[0], halves[1]
 
     def relinearize(self, t: Ciphertext) -> Ciphertext:
@@ -508,6 +525,55 @@ class Ckks:
         c1 = np.stack([ring.automorphism(a.c[1][i], g, q) for i, q in enumerate(pr)])
         k0, k1 = self.keyswitch(c1, a.level, self.rot[g])
         return Ciphertext(np.stack([self._add(c0, k0, pr), k1]), a.level)
+
+    def rotate_sum_hoisted(self, a: Ciphertext, steps: Sequence[int]) -> Ciphertext:
+        """sum over r in steps of rot(a, r), with the key switches hoisted (Halevi-Shoup 2018).
+
+        ModUp of c1 is computed once; rotation r applies phi_g (g = 5^r) to the raised digits
+        instead of raising phi_g(c1); the inner products with every rotation key are summed in
+        Q_l u P and one ModDown ends the sum:
+          out0 = sum_r phi_g(c0) + ModDown(sum_r sum_j phi_g(ModUp_j(c1)) * b_{r,j}),
+          out1 = [0 in steps] c1 + ModDown(sum_r sum_j phi_g(ModUp_j(c1)) * a_{r,j}),
+        where a step with g = 1 contributes (c0, c1) itself and no key switch. phi_g of a raised
+        digit differs from the digit of phi_g(c1) by multiples of the digit modulus (the fast
+        conversion is not odd), which the key switch tolerates like the conversion's own
+        overflow; the result is therefore not bit-identical to summing rotate()."""
+        prm = self.prm
+        lv = a.level
+        pr = prm.q[: lv + 1]
+        basis = pr + prm.p
+        rows = self._key_rows(lv)
+        dn = prm.dnum(lv)
+        c0 = np.zeros((lv + 1, prm.n), dtype=np.uint64)
+        c1 = np.zeros_like(c0)
+        ups = None
+        terms, kb, ka = [], [], []
+        for r in steps:
+            g = prm.galois(r)
+            if g == 1:
+                c0 = self._add(c0, a.c[0][: lv + 1], pr)
+                c1 = self._add(c1, a.c[1][: lv + 1], pr)
+                continue
+            if g not in self.rot:
+                raise KeyError(f"missing rotation key for step {r}")
+            if ups is None:
+                ups = self._modup(a.c[1][: lv + 1], lv)
+            c0 = self._add(c0, np.stack([ring.automorphism(a.c[0][i], g, q) for i, q in enumerate(pr)]), pr)
+            key = self.rot[g]
+            for j in range(dn):
+                terms.append(np.stack([ring.automorphism(ups[j][x], g, q) for x, q in enumerate(basis)]))
+                kb.append(key.b[j][rows])
+                ka.append(key.a[j][rows])
+        if terms:
+            T = np.ascontiguousarray(np.stack(terms).transpose(1, 0, 2))  # [|basis|, terms, N]
+            for h, K in enumerate((kb, ka)):
+                acc = ring.polydot_rows(T, np.ascontiguousarray(np.stack(K).transpose(1, 0, 2)), basis)
+                part = self._moddown(acc, lv)
+                if h == 0:
+                    c0 = self._add(c0, part, pr)
+                else:
+                    c1 = self._add(c1, part, pr)
+        return Ciphertext(np.stack([c0, c1]), lv)
 
     def mul_relin_rescale(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
         return self.rescale(self.relinearize(self.tensor(a, b)))

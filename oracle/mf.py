@@ -99,11 +99,33 @@ class Plan:
 
     def rotation_steps(self) -> List[int]:
         """Every left-rotation amount an epoch uses (negative = right)."""
-        steps = [1 << t for t in range(highest_bit(self.kp))]
+        steps = rotsum_steps(self.kp)
         steps += [(1 << t) * self.w for t in range(highest_bit(self.B))]
         steps += [-(1 << t) * self.w for t in range(highest_bit(self.B))]
         steps += [-self.kp]
         return steps
+
+
+# The in-block rotate-and-sum over kp slots is hoisted (one ModUp, kp - 1 key inner products,
+# one ModDown) for 2 <= kp <= HOIST_MAX_KP; wider blocks use log2(kp) rotate-and-adds.
+HOIST_MAX_KP = 16
+
+
+def rotsum_steps(kp: int) -> List[int]:
+    """Rotation amounts of the rotate-and-sum over kp slots."""
+    if 2 <= kp <= HOIST_MAX_KP:
+        return list(range(1, kp))
+    return [1 << t for t in range(highest_bit(kp))]
+
+
+def block_sum(he: Ckks, P: Ciphertext, kp: int) -> Ciphertext:
+    """S = sum_{j < kp} rot(P, j): every slot x < kp of a doubled block gets the block's sum."""
+    if 2 <= kp <= HOIST_MAX_KP:
+        return he.rotate_sum_hoisted(P, range(kp))
+    S = P
+    for t in range(highest_bit(kp)):
+        S = he.add(S, he.rotate(S, 1 << t))
+    return S
 
 
 def delta_closure(deltas) -> List[int]:
@@ -292,10 +314,7 @@ class EncryptedMF:
     def group_terms(self, t: int, UD_b: Ciphertext, vr: Ciphertext, lr: float):
         he, p = self.he, self.plan
         g = p.groups[t]
-        P = he.mul_relin_rescale(UD_b, vr)
-        S = P
-        for s in range(highest_bit(p.kp)):
-            S = he.add(S, he.rotate(S, 1 << s))
+        S = block_sum(he, he.mul_relin_rescale(UD_b, vr), p.kp)
         E = he.sub(he.drop(self.R[t], S.level), S)
         mask = he.enc.encode(mask_slots(g, p, lr))
         M = he.rescale(he.mul_plain(vr, mask))
@@ -367,8 +386,5 @@ class EncryptedMF:
             X = he.add(X, he.rotate(X, (1 << t) * p.w))
         out = []
         for c in range(p.n_vb):
-            P = he.rescale(he.relinearize(he.tensor(X, VD[c])))
-            for t in range(highest_bit(p.kp)):
-                P = he.add(P, he.rotate(P, 1 << t))
-            out.append(P)
+            out.append(block_sum(he, he.rescale(he.relinearize(he.tensor(X, VD[c]))), p.kp))
         return out

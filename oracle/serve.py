@@ -28,7 +28,7 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 from .ckks import Ciphertext, Ckks
-from .mf import highest_bit, next_pow2
+from .mf import block_sum, highest_bit, next_pow2, rotsum_steps
 
 REQ_NONCE_STRIDE = 64
 
@@ -37,6 +37,12 @@ def layout(k: int, slots: int):
     kp = next_pow2(k)
     w = 2 * kp
     return kp, w, slots // w
+
+
+def rotation_steps(k: int, slots: int) -> List[int]:
+    """Every left-rotation amount a request uses: the in-block sum, the block sum, the half-fill."""
+    kp, w, B = layout(k, slots)
+    return rotsum_steps(kp) + [(1 << t) * w for t in range(highest_bit(B))] + [-kp]
 
 
 def replicate_user(u: np.ndarray, k: int, slots: int) -> np.ndarray:
@@ -96,10 +102,7 @@ def encrypt_request(he: Ckks, u0, items, ratings, k: int, n_vb: int, nonce_base:
 def inner_products(he: Ckks, UR: Ciphertext, V: Sequence[Ciphertext], batches, kp: int) -> List[Ciphertext]:
     out = []
     for c in batches:
-        S = he.rescale(he.relinearize(he.tensor(UR, V[c])))
-        for t in range(highest_bit(kp)):
-            S = he.add(S, he.rotate(S, 1 << t))
-        out.append(S)
+        out.append(block_sum(he, he.rescale(he.relinearize(he.tensor(UR, V[c]))), kp))
     return out
 
 

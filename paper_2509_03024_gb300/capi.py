@@ -29,7 +29,7 @@ EXPORTS = [
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
-    "fhe_rotate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
+    "fhe_rotate", "fhe_rotate_sum", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
             "fhe_rescale": [vp, vp, vp, i32, i32, vp],
             "fhe_rescale_noalloc": [vp, vp, vp, i32, vp],
             "fhe_rotate": [vp, vp, vp, i32, i32, i32, vp],
+            "fhe_rotate_sum": [vp, vp, vp, i32, i32, i32, vp],
             "fhe_profile_begin": [vp, i32],
             "fhe_profile_end": [vp, vp, i32],
             "fhe_mf_rotation_steps": [vp, i32, vp, sz],
@@ -279,6 +280,10 @@ class Context:
 
     def rotate(self, ct, out, count: int, level: int, step: int, stream=None):
         self._check(lib().fhe_rotate(self.h, _ptr(ct), _ptr(out), count, level, step, _stream(stream)))
+
+    def rotate_sum(self, ct, out, count: int, level: int, kp: int, stream=None):
+        """out = sum_{r < kp} rot(ct, r) (hoisted for kp <= 16)."""
+        self._check(lib().fhe_rotate_sum(self.h, _ptr(ct), _ptr(out), count, level, kp, _stream(stream)))
 
     def serve_rotation_steps(self, k: int):
         buf = np.zeros(256, dtype=np.int32)

@@ -364,6 +364,15 @@ struct KsItem {
 };
 void keyswitch_items(Ctx& c, const std::vector<KsItem>& it, int level, cudaStream_t s);
 
+// In-block rotate-and-sum: out_i = sum_{r < kp} rot(in_i, r). Hoisted (one ModUp, kp - 1 key inner
+// products, one ModDown; in_i may equal out_i) for 2 <= kp <= kHoistMaxKp, else log2(kp)
+// rotate-and-adds (in_i and out_i distinct; in_i is overwritten).
+constexpr int kHoistMaxKp = 16;
+void rotsum_items(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& out, int kp, int level,
+                  cudaStream_t s);
+// Left-rotation amounts of that rotate-and-sum.
+std::vector<int> rotsum_steps(int kp);
+
 // ----------------------------------------------------------------------------- ctx helpers (ctx.cu)
 
 const EvalKey& rotation_key(const Ctx& c, int step);

@@ -1222,6 +1222,29 @@ int fhe_rotate(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, i
     });
 }
 
+int fhe_rotate_sum(fhe_ctx* ctx, uint64_t* ct, uint64_t* out, int32_t count, int32_t level, int32_t kp,
+                   void* stream) {
+    return guarded(ctx, [&] {
+        check_ptr(ct, "ct");
+        check_ptr(out, "out");
+        Ctx& c = ctx->c;
+        check_level(c, level);
+        check_keys(c);
+        if (count < 0) fail(FHE_ERR_INVALID_ARG, "negative count");
+        if (kp < 1 || (kp > kHoistMaxKp && (kp & (kp - 1)) != 0))
+            fail(FHE_ERR_INVALID_ARG, "rotate-and-sum needs 1 <= kp <= 16 or a power of two");
+        if (kp > kHoistMaxKp && ct == out) fail(FHE_ERR_INVALID_ARG, "rotate-and-sum over more than 16 slots needs out != ct");
+        c.arena.reset(S(stream));
+        const size_t w = c.ct_words();
+        std::vector<u64*> in, o;
+        for (int t = 0; t < count; t++) {
+            in.push_back(ct + t * w);
+            o.push_back(out + t * w);
+        }
+        rotsum_items(c, in, o, kp, level, S(stream));
+    });
+}
+
 int fhe_profile_begin(fhe_ctx* ctx, int32_t time_kernels) {
     return guarded(ctx, [&] {
         check_ptr(ctx, "ctx");

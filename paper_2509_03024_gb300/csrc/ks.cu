@@ -19,6 +19,14 @@
 // K1, K2, K4, K5 run the register-blocked NTT tiles of ntt_core.cuh over row
 // tables (one descriptor per limb row), so the conversions happen while the
 // tiles are loaded and the combinations while they are stored.
+//
+// Hoisted rotate-and-sum (Halevi-Shoup 2018): S = sum_{r < kp} rot(c, r) runs
+// K1 and K2 once on c1, replaces K3 by a kernel that applies each rotation's
+// automorphism to the raised digits while it reads them and sums the inner
+// products with all kp - 1 rotation keys (and the rotated c0's) into one
+// accumulator, then K4 and K5 once. An automorphism maps every aligned run of
+// 2^s evaluation slots onto an aligned run of 2^s slots, so the permuted reads
+// stay coalesced (pairs of slots are read as one 128-bit load).
 #include <algorithm>
 #include <cstring>
 
@@ -54,6 +62,15 @@ __device__ __forceinline__ int auto_src(int k, int g, int log_n) {
     unsigned e = (unsigned)(((unsigned long long)g * (2ull * bk + 1ull)) & ((2ull << log_n) - 1ull));
     return (int)(__brev((e - 1u) >> 1) >> sh);
 }
+
+constexpr int kMaxHoist = 31;
+
+// Rotation keys of a hoisted rotate-and-sum (passed by value as a kernel parameter).
+struct HoistKeys {
+    const u64* key[kMaxHoist];
+    int galois[kMaxHoist];
+    int count;
+};
 
 struct CombineArgs {
     const KsItem* items;
@@ -233,45 +250,127 @@ void ks_transform(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs
     }
 }
 
+// (hi * 2^64 + lo) mod q for hi, lo < 2^64: hi and lo reduced with floor(2^64 / q), then
+// hi * (2^64 mod q) + lo.
+__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const Prime& P) {
+    const u64 q = P.q;
+    const u64 h = nttc::reduce_any(hi, q, P.one_s);
+    const u64 l = nttc::reduce_any(lo, q, P.one_s);
+    const u64 r64 = (u64)0 - q * P.one_s;  // 2^64 mod q
+    return add_mod(mul_mod(h, r64, P), l, q);
+}
+
+__device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 a, u64 b) {
+    const u64 pl = a * b;
+    const u64 ph = __umul64hi(a, b);
+    lo += pl;
+    hi += ph + (lo < pl ? 1 : 0);
+}
+
+// Slots (2 k2, 2 k2 + 1) of phi_g(row): the automorphism maps the aligned pair onto an aligned pair.
+__device__ __forceinline__ void load_pair_auto(const u64* __restrict__ row, int k2, int g, int log_n, u64& vx, u64& vy) {
+    const int src = auto_src(2 * k2, g, log_n);
+    const ulonglong2 v = reinterpret_cast<const ulonglong2*>(row)[src >> 1];
+    vx = (src & 1) ? v.y : v.x;
+    vy = (src & 1) ? v.x : v.y;
+}
+
 // acc[t][h][x][k] = sum_j M_j[x][k] * key_t[j][h][px][k], where M_j[x] = ext[t][j][x] for x
-// outside digit j and the item's input d (through its automorphism) for x in digit j.
-__global__ void ks_inner_kernel(u64* acc, const u64* __restrict__ ext, const KsItem* __restrict__ tab, int items,
-                                int dn, int alpha, int next, int level, int L, int n_ext, int log_n,
-                                const Prime* __restrict__ pr) {
-    const size_t total = (size_t)items * next << (log_n - 1);
+// outside digit j and the item's input d (through its automorphism) for x in digit j. The
+// products are summed in 128 bits and reduced once; the limb index is the slowest, so one limb's
+// rows of a shared key stay in L2 while every item reads them.
+__global__ void __launch_bounds__(256, 4) ks_inner_kernel(u64* acc, const u64* __restrict__ ext,
+                                                          const KsItem* __restrict__ tab, int items, int dn, int alpha,
+                                                          int next, int level, int L, int n_ext, int log_n,
+                                                          const Prime* __restrict__ pr) {
+    const size_t half = (size_t)1 << (log_n - 1);
+    const size_t total = (size_t)items * next * half;
     const int l1 = level + 1;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        int k2 = (int)(e & ((1u << (log_n - 1)) - 1));
-        size_t row = e >> (log_n - 1);
-        int x = (int)(row % next), t = (int)(row / next);
-        int px = x < l1 ? x : x + (L - level);
+        const int k2 = (int)(e & (half - 1));
+        const size_t row = e >> (log_n - 1);
+        const int t = (int)(row % items), x = (int)(row / items);
+        const int px = x < l1 ? x : x + (L - level);
         const Prime P = pr[px];
         const KsItem it = tab[t];
         const int own = x < l1 ? x / alpha : -1;
-        u64 s0x = 0, s0y = 0, s1x = 0, s1y = 0;
+        u64 a0x = 0, h0x = 0, a0y = 0, h0y = 0, a1x = 0, h1x = 0, a1y = 0, h1y = 0;
         for (int j = 0; j < dn; j++) {
-            ulonglong2 v;
-            if (j == own) {
-                const u64* d = it.d + ((size_t)x << log_n);
-                int k = 2 * k2;
-                if (it.galois == 1) {
-                    v = reinterpret_cast<const ulonglong2*>(d)[k2];
-                } else {
-                    v.x = d[auto_src(k, (int)it.galois, log_n)];
-                    v.y = d[auto_src(k + 1, (int)it.galois, log_n)];
-                }
+            u64 vx, vy;
+            if (j == own && it.galois != 1) {
+                load_pair_auto(it.d + ((size_t)x << log_n), k2, (int)it.galois, log_n, vx, vy);
             } else {
-                v = reinterpret_cast<const ulonglong2*>(ext + ((size_t)((t * dn + j) * next + x) << log_n))[k2];
+                const u64* src = j == own ? it.d + ((size_t)x << log_n) : ext + ((size_t)((t * dn + j) * next + x) << log_n);
+                const ulonglong2 v = reinterpret_cast<const ulonglong2*>(src)[k2];
+                vx = v.x;
+                vy = v.y;
             }
-            ulonglong2 kb = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
-            ulonglong2 ka = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
-            s0x = add_mod(s0x, mul_mod(v.x, kb.x, P), P.q);
-            s0y = add_mod(s0y, mul_mod(v.y, kb.y, P), P.q);
-            s1x = add_mod(s1x, mul_mod(v.x, ka.x, P), P.q);
-            s1y = add_mod(s1y, mul_mod(v.y, ka.y, P), P.q);
+            const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
+            const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
+            mac128(a0x, h0x, vx, kb.x);
+            mac128(a0y, h0y, vy, kb.y);
+            mac128(a1x, h1x, vx, ka.x);
+            mac128(a1y, h1y, vy, ka.y);
         }
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] = make_ulonglong2(s0x, s0y);
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] = make_ulonglong2(s1x, s1y);
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] =
+            make_ulonglong2(reduce128(a0x, h0x, P), reduce128(a0y, h0y, P));
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] =
+            make_ulonglong2(reduce128(a1x, h1x, P), reduce128(a1y, h1y, P));
+    }
+}
+
+// Hoisted inner product: acc[t][h][x][k] = sum_r sum_j M_j[x][pi_r(k)] * key_r[j][h][px][k], where
+// pi_r is the slot map of rotation r and M_j[x] is ext[t][j][x] outside digit j and the item's c1
+// inside it; the 128-bit sums are reduced once. For x < l1 also c0sum[t][x][k] = c0[x][k] +
+// sum_r c0[x][pi_r(k)]. The limb index is the slowest, so one limb's rows of all kp - 1 keys stay in
+// L2 while every item reads them.
+__global__ void __launch_bounds__(256, 4) ks_hoist_inner_kernel(u64* acc, u64* c0sum, const u64* __restrict__ ext, const KsItem* __restrict__ tab,
+                                      HoistKeys hk, int items, int dn, int alpha, int next, int level, int L,
+                                      int n_ext, int log_n, const Prime* __restrict__ pr) {
+    const size_t half = (size_t)1 << (log_n - 1);
+    const size_t total = (size_t)items * next * half;
+    const int l1 = level + 1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int k2 = (int)(e & (half - 1));
+        const size_t row = e >> (log_n - 1);
+        const int t = (int)(row % items), x = (int)(row / items);
+        const int px = x < l1 ? x : x + (L - level);
+        const Prime P = pr[px];
+        const KsItem it = tab[t];
+        const int own = x < l1 ? x / alpha : -1;
+        u64 a0x = 0, h0x = 0, a0y = 0, h0y = 0, a1x = 0, h1x = 0, a1y = 0, h1y = 0;
+        for (int r = 0; r < hk.count; r++) {
+            const int g = hk.galois[r];
+            const u64* key = hk.key[r];
+            for (int j = 0; j < dn; j++) {
+                const u64* src = j == own ? it.d + ((size_t)x << log_n)
+                                          : ext + ((size_t)((t * dn + j) * next + x) << log_n);
+                u64 vx, vy;
+                load_pair_auto(src, k2, g, log_n, vx, vy);
+                const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
+                const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
+                mac128(a0x, h0x, vx, kb.x);
+                mac128(a0y, h0y, vy, kb.y);
+                mac128(a1x, h1x, vx, ka.x);
+                mac128(a1y, h1y, vy, ka.y);
+            }
+        }
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] =
+            make_ulonglong2(reduce128(a0x, h0x, P), reduce128(a0y, h0y, P));
+        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] =
+            make_ulonglong2(reduce128(a1x, h1x, P), reduce128(a1y, h1y, P));
+        if (x < l1) {
+            const u64* c0 = it.addP0 + ((size_t)x << log_n);
+            const ulonglong2 self = reinterpret_cast<const ulonglong2*>(c0)[k2];
+            u64 sx = self.x, sy = self.y;
+            for (int r = 0; r < hk.count; r++) {
+                u64 vx, vy;
+                load_pair_auto(c0, k2, hk.galois[r], log_n, vx, vy);
+                sx = add_mod(sx, vx, P.q);
+                sy = add_mod(sy, vy, P.q);
+            }
+            reinterpret_cast<ulonglong2*>(c0sum + ((size_t)(t * l1 + x) << log_n))[k2] = make_ulonglong2(sx, sy);
+        }
     }
 }
 
@@ -282,11 +381,16 @@ inline unsigned grid1(size_t work) {
 
 }  // namespace
 
-void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
+namespace {
+
+// K1-K5 over a batch of items; with hk, K3 is the hoisted inner product (items' galois must be 1,
+// addP0 holds c0, d holds c1) and the outputs are sum_r rot(c, r) over r = 0 and hk's rotations.
+void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* hk, cudaStream_t s) {
     if (all.empty()) return;
     const int n = c.n, L = c.L, A = c.alpha, l1 = level + 1, next = l1 + A, dn = c.dnum(level);
     // bound the work area to ~6 GiB per sub-batch
-    const size_t per_item = (size_t)(l1 + dn * next + 2 * next + 2 * A + 2 * l1) * n * sizeof(u64);
+    const size_t per_item =
+        (size_t)(l1 + dn * next + 2 * next + 2 * A + 2 * l1 + (hk ? l1 : 0)) * n * sizeof(u64);
     const int max_items = (int)std::max<size_t>(1, ((size_t)6 << 30) / per_item);
     for (size_t b0 = 0; b0 < all.size(); b0 += max_items) {
         const int items = (int)std::min<size_t>(max_items, all.size() - b0);
@@ -347,7 +451,7 @@ void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStre
         ks_transform<false, LD_CONV, ST_LAST>(c, d_r2, (int)r2.size(), none, K_NTT_FWD, 16.0 * r2.size() * n, s);
 
         // K3: key inner product
-        {
+        if (!hk) {
             LaunchScope _ls(c.prof, K_KS_INNER,
                             8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next),
                             s);
@@ -355,6 +459,24 @@ void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStre
                                                                                      next, level, L, c.n_ext, c.log_n,
                                                                                      c.d_primes);
             CK(cudaGetLastError());
+        } else {
+            // reads: the raised digits and c0 once per item, every key once; writes acc and c0sum
+            u64* c0sum = c.scratch_u64("ks_c0sum", (size_t)items * l1 * n);
+            LaunchScope _ls(c.prof, K_KS_INNER,
+                            8.0 * n * ((double)items * (dn * next + l1) + (double)hk->count * dn * 2 * next +
+                                       (double)items * (2 * next + l1)),
+                            s);
+            ks_hoist_inner_kernel<<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(
+                acc, c0sum, ext, d_items, *hk, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
+            CK(cudaGetLastError());
+            // the combine adds c0sum to component 0 and c1 to component 1
+            std::vector<KsItem> it5(it);
+            for (int t = 0; t < items; t++) {
+                it5[t].addP0 = nullptr;
+                it5[t].addI0 = c0sum + (size_t)t * l1 * n;
+                it5[t].addI1 = it[t].d;
+            }
+            ca.items = c.arena.push_vec(it5, s);
         }
 
         // K4: y_k = INTT(acc_h special limb k) * Phat_k^-1
@@ -394,6 +516,73 @@ void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStre
         const KsRow* d_r5 = c.arena.push_vec(r5, s);
         ks_transform<false, LD_CONV, ST_COMBINE>(c, d_r5, (int)r5.size(), ca, K_NTT_FWD, 16.0 * r5.size() * n, s);
     }
+}
+
+}  // namespace
+
+void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
+    ks_run(c, all, level, nullptr, s);
+}
+
+std::vector<int> rotsum_steps(int kp) {
+    std::vector<int> st;
+    if (kp >= 2 && kp <= kHoistMaxKp)
+        for (int r = 1; r < kp; r++) st.push_back(r);
+    else
+        for (int t = 0; (1 << t) < kp; t++) st.push_back(1 << t);
+    return st;
+}
+
+void rotsum_items(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& out, int kp, int level,
+                  cudaStream_t s) {
+    if (in.size() != out.size()) fail(FHE_ERR_INVALID_ARG, "rotate-and-sum: input and output counts differ");
+    if (in.empty() || kp < 1) return;
+    const size_t lw = c.ct_words() / 2;
+    const int l1 = level + 1;
+    if (kp == 1) {
+        std::vector<UnItem> cp;
+        for (size_t i = 0; i < in.size(); i++)
+            if (in[i] != out[i]) cp.push_back({in[i], out[i]});
+        items_copy(c, cp, 2, l1, s);
+        return;
+    }
+    if (kp <= kHoistMaxKp) {
+        HoistKeys hk{};
+        hk.count = kp - 1;
+        int max_bits = 0;
+        for (int i = 0; i <= c.L + c.alpha; i++) max_bits = std::max(max_bits, (int)c.hprimes[i].b);
+        // the 128-bit sums hold count * dnum products below 2^(2 max_bits)
+        int terms = hk.count * c.dnum(level), lg = 0;
+        while ((1 << lg) < terms) lg++;
+        if (2 * max_bits + lg > 128) fail(FHE_ERR_INVALID_ARG, "hoisted rotate-and-sum: primes too wide for 128-bit sums");
+        for (int r = 1; r < kp; r++) {
+            hk.key[r - 1] = rotation_key(c, r).d;
+            hk.galois[r - 1] = (int)c.galois(r);
+        }
+        std::vector<KsItem> ks;
+        for (size_t i = 0; i < in.size(); i++) ks.push_back({in[i] + lw, nullptr, in[i], nullptr, nullptr, out[i], out[i] + lw, 1});
+        ks_run(c, ks, level, &hk, s);
+        return;
+    }
+    // wider blocks: log2(kp) rotate-and-adds, alternating between `in` (overwritten) and `out`
+    for (size_t i = 0; i < in.size(); i++)
+        if (in[i] == out[i]) fail(FHE_ERR_INVALID_ARG, "rotate-and-sum over more than 16 slots needs distinct buffers");
+    int rounds = 0;
+    while ((1 << rounds) < kp) rounds++;
+    std::vector<u64*> cur(in), nxt(out);
+    for (int t = 0; t < rounds; t++) {
+        std::vector<KsItem> ks;
+        const EvalKey& key = rotation_key(c, 1 << t);
+        const int g = (int)c.galois(1 << t);
+        for (size_t i = 0; i < in.size(); i++)
+            ks.push_back({cur[i] + lw, key.d, cur[i], cur[i], cur[i] + lw, nxt[i], nxt[i] + lw, g});
+        ks_run(c, ks, level, nullptr, s);
+        std::swap(cur, nxt);
+    }
+    std::vector<UnItem> cp;
+    for (size_t i = 0; i < in.size(); i++)
+        if (cur[i] != out[i]) cp.push_back({cur[i], out[i]});
+    items_copy(c, cp, 2, l1, s);
 }
 
 }  // namespace fhe

@@ -179,7 +179,7 @@ void ensure_workspace(fhe_mf_plan& p) {
 void check_plan_keys(const fhe_mf_plan& p) {
     Ctx& c = *p.c;
     if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
-    for (int t = 0; t < p.log_kp; t++) rotation_key(c, 1 << t);
+    for (int r : rotsum_steps(p.kp)) rotation_key(c, r);
     for (int t = 0; t < p.beta; t++) {
         rotation_key(c, (1 << t) * p.w);
         rotation_key(c, -(1 << t) * p.w);
@@ -277,20 +277,16 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
         items_tensor(c, tens, l0 + 1, s);
         relin_inplace(c, t3s, l0, s);
         items_rescale(c, resc_p, 2, l0, s);
-        // rotate-and-sum over kp slots
-        u64* cur = Sb;
-        u64* nxt = Tb;
-        for (int t = 0; t < p.log_kp; t++) {
-            std::vector<const u64*> in;
-            std::vector<u64*> out;
-            std::vector<int> steps(cnt, 1 << t);
+        // rotate-and-sum over kp slots: S (in Tb) from P (in Sb)
+        {
+            std::vector<u64*> in, out;
             for (int i = 0; i < cnt; i++) {
-                in.push_back(cur + (size_t)i * w);
-                out.push_back(nxt + (size_t)i * w);
+                in.push_back(Sb + (size_t)i * w);
+                out.push_back(Tb + (size_t)i * w);
             }
-            rotate_items(c, in, out, steps, l1, true, s);
-            std::swap(cur, nxt);
+            rotsum_items(c, in, out, p.kp, l1, s);
         }
+        u64* cur = Tb;
         // E = R - S
         std::vector<BinItem> esub;
         for (int i = 0; i < cnt; i++) esub.push_back({p.d_R + (size_t)(g0 + i) * w, cur + (size_t)i * w, Eb + (size_t)i * w});
@@ -430,7 +426,7 @@ void run_predict(const fhe_mf_plan& p, const u64* U, const u64* V, int level, in
     if (level > c.L) fail(FHE_ERR_INVALID_ARG, "level out of range");
     if (user < 0 || user >= p.n) fail(FHE_ERR_INVALID_ARG, "user out of range");
     if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
-    for (int t = 0; t < p.log_kp; t++) rotation_key(c, 1 << t);
+    for (int r : rotsum_steps(p.kp)) rotation_key(c, r);
     for (int t = 0; t < p.beta; t++) rotation_key(c, (1 << t) * p.w);
     c.arena.reset(s);
     const size_t w = c.ct_words(), lw = w / 2;
@@ -451,31 +447,21 @@ void run_predict(const fhe_mf_plan& p, const u64* U, const u64* V, int level, in
         std::swap(X, Y);
     }
     u64* T3 = c.scratch_u64("pred_t3", (size_t)p.n_vb * 3 * lw);
+    u64* tmp = c.scratch_u64("pred_tmp", (size_t)p.n_vb * w);
     std::vector<BinItem> tens;
-    std::vector<u64*> t3s;
+    std::vector<u64*> t3s, prod, res;
     std::vector<UnItem> rs;
     for (int cb = 0; cb < p.n_vb; cb++) {
         tens.push_back({X, V + (size_t)cb * w, T3 + (size_t)cb * 3 * lw});
         t3s.push_back(T3 + (size_t)cb * 3 * lw);
-        rs.push_back({T3 + (size_t)cb * 3 * lw, out + (size_t)cb * w});
+        rs.push_back({T3 + (size_t)cb * 3 * lw, tmp + (size_t)cb * w});
+        prod.push_back(tmp + (size_t)cb * w);
+        res.push_back(out + (size_t)cb * w);
     }
     items_tensor(c, tens, level, s);
     relin_inplace(c, t3s, level - 1, s);
     items_rescale(c, rs, 2, level - 1, s);
-    u64* tmp = c.scratch_u64("pred_tmp", (size_t)p.n_vb * w);
-    for (int t = 0; t < p.log_kp; t++) {
-        std::vector<const u64*> in;
-        std::vector<u64*> o;
-        std::vector<int> steps(p.n_vb, 1 << t);
-        for (int cb = 0; cb < p.n_vb; cb++) {
-            in.push_back(out + (size_t)cb * w);
-            o.push_back(tmp + (size_t)cb * w);
-        }
-        rotate_items(c, in, o, steps, level - 2, true, s);
-        std::vector<UnItem> cp;
-        for (int cb = 0; cb < p.n_vb; cb++) cp.push_back({tmp + (size_t)cb * w, out + (size_t)cb * w});
-        items_copy(c, cp, 2, level - 1, s);
-    }
+    rotsum_items(c, prod, res, p.kp, level - 2, s);
 }
 
 template <typename F>
@@ -509,8 +495,7 @@ int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t ca
     int kp = next_pow2(k), w = 2 * kp;
     if (w > c.slots) return FHE_ERR_INVALID_ARG;
     int B = c.slots / w;
-    std::vector<int> st;
-    for (int t = 0; (1 << t) < kp; t++) st.push_back(1 << t);
+    std::vector<int> st = rotsum_steps(kp);
     for (int t = 0; (1 << t) < B; t++) st.push_back((1 << t) * w);
     for (int t = 0; (1 << t) < B; t++) st.push_back(-(1 << t) * w);
     st.push_back(-kp);

@@ -110,30 +110,19 @@ void inner_products(fhe_server& sv, const std::vector<std::pair<Slot*, int>>& pa
     std::vector<BinItem> tens;
     std::vector<u64*> t3;
     std::vector<UnItem> rs;
+    std::vector<u64*> prod, res;
     for (auto& pr : pairs) {
         SlotWork wk = work_of(sv, *pr.first, pr.second);
         tens.push_back({pr.first->UR, sv.V + (size_t)pr.second * w, wk.T3});
         t3.push_back(wk.T3);
-        rs.push_back({wk.T3, wk.S});
+        rs.push_back({wk.T3, wk.tmp});
+        prod.push_back(wk.tmp);
+        res.push_back(wk.S);
     }
     items_tensor(c, tens, level + 1, s);
     relin_inplace3(c, t3, level, s);
     items_rescale(c, rs, 2, level, s);
-    for (int t = 0; t < sv.log_kp; t++) {
-        std::vector<u64*> in, out;
-        for (auto& pr : pairs) {
-            SlotWork wk = work_of(sv, *pr.first, pr.second);
-            in.push_back(wk.S);
-            out.push_back(wk.tmp);
-        }
-        rot_add(c, in, out, 1 << t, level - 1, s);
-        std::vector<UnItem> cp;
-        for (auto& pr : pairs) {
-            SlotWork wk = work_of(sv, *pr.first, pr.second);
-            cp.push_back({wk.tmp, wk.S});
-        }
-        items_copy(c, cp, 2, level, s);
-    }
+    rotsum_items(c, prod, res, sv.kp, level - 1, s);
 }
 
 void fold_in_step(fhe_server& sv, const std::vector<Slot*>& group, int level, cudaStream_t s) {
@@ -266,8 +255,7 @@ int fhe_serve_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t
     int kp = npow2(k), w = 2 * kp;
     if (w > c.slots) return FHE_ERR_INVALID_ARG;
     int B = c.slots / w;
-    std::vector<int> st;
-    for (int t = 0; (1 << t) < kp; t++) st.push_back(1 << t);
+    std::vector<int> st = rotsum_steps(kp);
     for (int t = 0; (1 << t) < B; t++) st.push_back((1 << t) * w);
     st.push_back(-kp);
     if (out) {
@@ -302,7 +290,7 @@ int fhe_serve_create(fhe_ctx* ctx, const uint64_t* V, int32_t m, int32_t k, int3
         sv->steps = steps;
         sv->lr = lr;
         sv->lam = lam;
-        for (int t = 0; t < sv->log_kp; t++) rotation_key(c, 1 << t);
+        for (int r : rotsum_steps(sv->kp)) rotation_key(c, r);
         for (int t = 0; t < sv->beta; t++) rotation_key(c, (1 << t) * sv->w);
         rotation_key(c, -sv->kp);
         const size_t w = c.ct_words(), lw = w / 2;

@@ -157,6 +157,34 @@ def test_rotate_bit_exact(preset, steps):
     assert_ct_equal(to_coeff(ctx, out, L)[0], oa, "rotate by N/2")
 
 
+@pytest.mark.parametrize("preset,kp,level_off", [("t10", 4, 0), ("t10", 16, 1), ("t11a2", 3, 0), ("t11a2", 8, 2),
+                                                  ("t11a2", 32, 0), ("paper", 16, 1)])
+def test_rotate_sum_bit_exact(preset, kp, level_off):
+    """sum_{r < kp} rot(ct, r) over two ciphertexts: hoisted for kp <= 16, rotate-and-adds above."""
+    from oracle import mf
+    steps = mf.rotsum_steps(kp)
+    ctx = gpu_ctx(preset, SEED, steps)
+    he = oracle_ctx(preset, SEED, steps)
+    level = ctx.top - level_off
+    xs = [_slots(ctx.slots, 40 + i) for i in range(2)]
+    a = ctx.empty_ct(2)
+    for i, x in enumerate(xs):
+        ctx.encrypt(x, ctx.top, 50 + i, ct_slice(ctx, a, i))
+    want = [mf.block_sum(he, he.drop(he.encrypt(x, he.prm.top, 50 + i), level), kp) for i, x in enumerate(xs)]
+    out = ctx.empty_ct(2)
+    keep = a.clone()
+    ctx.rotate_sum(a, out, 2, level, kp)
+    got = to_coeff(ctx, out, level, 2)
+    for i in range(2):
+        assert_ct_equal(got[i], want[i], f"rotate_sum kp={kp} item {i}")
+        dec = ctx.decrypt(ct_slice(ctx, out, i), level)
+        ref = sum(np.roll(xs[i], -r) for r in range(kp))
+        assert np.abs(dec - ref).max() < 1e-4
+    if kp <= 16:   # in place gives the same bits
+        ctx.rotate_sum(keep, keep, 2, level, kp)
+        assert (to_coeff(ctx, keep, level, 2) == got).all()
+
+
 def test_errors_are_reported_and_context_survives():
     ctx = gpu_ctx("t10", SEED, [1])
     from paper_2509_03024_gb300.capi import FheError

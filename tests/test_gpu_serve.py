@@ -57,12 +57,18 @@ def _run(server, ctx, n_vb, reqs, schedule):
     return out
 
 
+def test_rotation_steps_match_oracle():
+    ctx = gpu_ctx("t10s", SEED)
+    for k in (1, 2, 3, 8, 16, 20):
+        assert sorted(ctx.serve_rotation_steps(k)) == sorted(serve.rotation_steps(k, ctx.slots))
+
+
 def test_single_request_bit_exact_with_oracle():
     ctx, V, VD, n_vb, reqs = _fixture()
     server = capi.Server(ctx, VD, M, K, STEPS, LR, LAM, max_slots=4)
     out = _run(server, ctx, n_vb, reqs, [(0, 1)])
     buf, lv = out[1]
-    he = oracle_ctx("t10s", SEED, ctx.serve_rotation_steps(K))
+    he = oracle_ctx("t10s", SEED, serve.rotation_steps(K, ctx.slots))
     kp, w, B = serve.layout(K, ctx.slots)
     dummy = mf.build_plan(1, M, K, [0], [0], [1.0], he.prm.slots)
     oVD = [he.encrypt(mf.pack_factors(V, dummy, c), he.prm.top, mf.V_NONCE_BASE + c) for c in range(n_vb)]

@@ -203,3 +203,63 @@ def test_rotation_key_switches_from_rotated_secret():
     s_g = ring.automorphism(s, g, q)
     lhs = (c0g.astype(object) + ring.polymul(c1g, s_g, q).astype(object)) % q
     assert [int(v) for v in lhs] == [int(v) for v in m_g]
+
+
+def _int_automorphism(a, g):
+    """a(X^g) in Z[X]/(X^N + 1), written out from the definition: X^i -> (+/-) X^(g i mod N)."""
+    n = len(a)
+    out = [0] * n
+    for i, v in enumerate(a):
+        e = (g * i) % (2 * n)
+        if e < n:
+            out[e] += v
+        else:
+            out[e - n] -= v
+    return out
+
+
+def _hoist_setup(log_n=6, steps=range(1, 8), seed=29):
+    prm = ckks.Params(log_n, (50,) * 4, (60, 60), 50)   # alpha = 2: two digits at the top level
+    he = ckks.Ckks(prm)
+    he.keygen(seed, list(steps))
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=prm.slots)
+    return prm, he, x, he.encrypt(x, prm.top, 1)
+
+
+def test_hoisted_rotate_sum_is_sum_of_automorphisms_plus_small_noise():
+    """decrypt(rotate_sum_hoisted(ct, 0..7)) = sum_r phi_(5^r)(decrypt(ct)) + key-switch noise, in Z[X]/(X^N+1).
+
+    A wrong permutation, key, digit or ModDown term leaves an error of the order of the modulus."""
+    prm, he, x, ct = _hoist_setup()
+    steps = list(range(8))
+    m = he.decrypt_coeffs(ct)
+    want = [0] * prm.n
+    for r in steps:
+        for i, v in enumerate(_int_automorphism(m, pow(5, r, 2 * prm.n))):
+            want[i] += v
+    for lv in (prm.top, 2):
+        got = he.decrypt_coeffs(he.rotate_sum_hoisted(he.drop(ct, lv), steps))
+        err = max(abs(a - b) for a, b in zip(got, want))
+        assert err < (1 << 16), (lv, err)
+
+
+def test_hoisted_rotate_sum_slots_and_special_cases():
+    prm, he, x, ct = _hoist_setup()
+    S = he.rotate_sum_hoisted(ct, range(8))
+    want = sum(np.roll(x, -r) for r in range(8))
+    assert np.abs(he.decrypt(S) - want).max() < 1e-6
+    # step 0 alone is the ciphertext itself, bit for bit
+    I = he.rotate_sum_hoisted(ct, [0])
+    assert (I.c == ct.c).all()
+    # one step: the same plaintext as rotate() (the bits differ: phi is applied after ModUp)
+    one = he.rotate_sum_hoisted(ct, [3])
+    assert np.abs(he.decrypt(one) - np.roll(x, -3)).max() < 1e-6
+    # the sum is order-free: modular additions commute exactly
+    perm = he.rotate_sum_hoisted(ct, [5, 0, 7, 2, 1, 6, 3, 4])
+    assert (perm.c == S.c).all()
+    # hoisting changes only noise: against sequential rotate-and-adds
+    seq = ct
+    for t in range(3):
+        seq = he.add(seq, he.rotate(seq, 1 << t))
+    assert np.abs(he.decrypt(seq) - he.decrypt(S)).max() < 1e-6

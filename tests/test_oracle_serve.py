@@ -31,7 +31,8 @@ def test_encrypted_request_matches_fp64():
     k, m = 3, 90
     kp, w, B = serve.layout(k, prm.slots)
     n_vb = -(-m // B)
-    steps = [1 << t for t in range(mf.highest_bit(kp))] + [(1 << t) * w for t in range(mf.highest_bit(B))] + [-kp]
+    steps = serve.rotation_steps(k, prm.slots)
+    assert sorted(steps) == sorted([1, 2, 3] + [(1 << t) * w for t in range(mf.highest_bit(B))] + [-kp])
     he.keygen(3, steps)
     rng = np.random.default_rng(2)
     V = rng.normal(0, 0.3, (m, k))
