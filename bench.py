@@ -59,6 +59,7 @@ def _args():
     ap.add_argument("--served-requests", type=int, default=96)
     ap.add_argument("--served-rate", type=float, default=100.0)
     ap.add_argument("--served-slots", type=int, default=48)
+    ap.add_argument("--served-sweep", default="", help="comma-separated arrival rates (req/s) to sweep")
     return ap.parse_args()
 
 
@@ -214,6 +215,8 @@ def serve_loop(server, reqs, enc, take_buf):
 
 
 def run_served(args, dev):
+    """Served fold-in + predict at --served-rate (and at every rate of --served-sweep): continuous
+    batching against the same server with one slot (one request at a time)."""
     import torch
     from paper_2509_03024_gb300 import capi
     from paper_2509_03024_gb300 import workloads as W
@@ -225,25 +228,39 @@ def run_served(args, dev):
     n_vb = plan.n_vb
     VD = ctx.empty_ct(n_vb)
     plan.encrypt_factors(1, V, VD)
-    reqs = W.served_requests(args.served_requests, args.served_rate, m, k, SEED + 6)
-    enc = []
-    for i, r in enumerate(reqs):  # client-side encryption, before the timed loop
-        UR, R = ctx.empty_ct(1), ctx.empty_ct(n_vb)
-        ctx.encrypt_request(m, k, r.u0, r.items, r.ratings, (1 << 44) + 64 * i, UR, R)
-        enc.append((UR, R))
     take_buf = ctx.empty_ct(n_vb)
-    server = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=args.served_slots,
-                         memory_budget_bytes=48 << 30)
-    batched = serve_loop(server, reqs, enc, take_buf)
-    batched["slots"] = server.n_slots
-    server.close()
-    single = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=1)
-    one = serve_loop(single, reqs, enc, take_buf)
-    single.close()
-    return {"workload": SERVED, "requests": len(reqs), "arrival_rate_req_s": args.served_rate,
-            "value": batched["ratings_per_s"], "unit": UNIT, "p50_ms": batched["p50_ms"],
-            "p99_ms": batched["p99_ms"], "continuous_batching": batched, "one_by_one": one,
-            "speedup_vs_one_by_one": batched["ratings_per_s"] / one["ratings_per_s"]}
+
+    def at_rate(rate):
+        reqs = W.served_requests(args.served_requests, rate, m, k, SEED + 6)
+        enc = []
+        for i, r in enumerate(reqs):  # client-side encryption, before the timed loop
+            UR, R = ctx.empty_ct(1), ctx.empty_ct(n_vb)
+            ctx.encrypt_request(m, k, r.u0, r.items, r.ratings, (1 << 44) + 64 * i, UR, R)
+            enc.append((UR, R))
+        server = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=args.served_slots,
+                             memory_budget_bytes=48 << 30)
+        batched = serve_loop(server, reqs, enc, take_buf)
+        batched["slots"] = server.n_slots
+        server.close()
+        single = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=1)
+        one = serve_loop(single, reqs, enc, take_buf)
+        single.close()
+        return len(reqs), batched, one
+
+    n, batched, one = at_rate(args.served_rate)
+    out = {"workload": SERVED, "requests": n, "arrival_rate_req_s": args.served_rate,
+           "value": batched["ratings_per_s"], "unit": UNIT, "p50_ms": batched["p50_ms"],
+           "p99_ms": batched["p99_ms"], "continuous_batching": batched, "one_by_one": one,
+           "speedup_vs_one_by_one": batched["ratings_per_s"] / one["ratings_per_s"]}
+    if args.served_sweep:
+        sweep = []
+        for rate in (float(x) for x in args.served_sweep.split(",")):
+            _, b, o = at_rate(rate)
+            sweep.append({"rate_req_s": rate,
+                          "batched": {k2: b[k2] for k2 in ("ratings_per_s", "p50_ms", "p99_ms")},
+                          "one_by_one": {k2: o[k2] for k2 in ("ratings_per_s", "p50_ms", "p99_ms")}})
+        out["sweep"] = sweep
+    return out
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -379,15 +396,21 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
         log_n = 15
         bfly = (alg_bytes / launches) / 16.0 * (log_n / 4.0)
         achieved = bfly / avg_s / 1e9
-        peak = ALU_PEAK_GBFLY
         rows_per_launch = (alg_bytes / launches) / (16.0 * 2 ** log_n)
         traffic = NCU_FWD_DRAM_BYTES_PER_ROW * rows_per_launch if name == "ntt_forward" else None
+        # peak: the same butterfly arithmetic on register-resident values, measured now on this GPU
+        peak = ctx.probe_butterfly_rate(2000)
         roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Gbfly/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "traffic_source": "ncu dram__bytes_read+write per row of the fused forward passes, scaled "
                                       "by the rows of the average launch",
-                    "peak_source": ("derived: 152 SMs x 128 lanes x 2.07 GHz / 20 32-bit instructions per lazy "
-                                    "64-bit Shoup butterfly"),
+                    "peak_source": ("measured by fhe_probe_butterfly_rate: the forward transform's lazy Shoup "
+                                    "butterflies on register-resident values (no shared-memory, twiddle or HBM "
+                                    "traffic), 152 SMs x 3 CTAs of 256 threads"),
+                    "nominal_peak": {"value": ALU_PEAK_GBFLY, "frac": achieved / ALU_PEAK_GBFLY,
+                                     "source": "152 SMs x 128 lanes x 2.07 GHz / 20 32-bit instructions per "
+                                               "butterfly at full issue (not reached: the probe issues 23.8 "
+                                               "instructions per butterfly at 53 % issue)"},
                     "launches": launches, "avg_launch_us": avg_s * 1e6, "butterflies_per_launch": bfly,
                     "hbm_view": hbm_view}
     else:

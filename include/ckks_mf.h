@@ -200,6 +200,15 @@ int fhe_rotate_sum(fhe_ctx* ctx, uint64_t* ct, uint64_t* out, int32_t count, int
 
 /* ------------------------------------------------------------------ launch accounting */
 
+/* Measurement helper (no counterpart in the paper): the rate, in 10^9 butterflies per second,
+ * at which this GPU runs the forward NTT's butterfly arithmetic (lazy Shoup Cooley-Tukey
+ * butterflies, three stages per radix-8 block, a reduction every 15 stages) on values held in
+ * registers, with no memory traffic inside the loop. It is the integer-pipe ceiling of the
+ * NTT passes. reps: loop trips (each thread does 60 butterflies per trip; ~2000 takes tens of
+ * milliseconds). Runs on the default stream and synchronises. Errors: FHE_ERR_INVALID_ARG for
+ * reps < 1 or a null output. */
+int fhe_probe_butterfly_rate(fhe_ctx* ctx, int32_t reps, double* gbfly_per_s);
+
 /* Per kernel class: launches, summed device time (only when timing was
  * requested) and the algorithmic bytes those launches must move (inputs read
  * once plus outputs written once). `name` points to a static string. */

@@ -29,7 +29,7 @@ EXPORTS = [
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
-    "fhe_rotate", "fhe_rotate_sum", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
+    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
             "fhe_rescale_noalloc": [vp, vp, vp, i32, vp],
             "fhe_rotate": [vp, vp, vp, i32, i32, i32, vp],
             "fhe_rotate_sum": [vp, vp, vp, i32, i32, i32, vp],
+            "fhe_probe_butterfly_rate": [vp, i32, vp],
             "fhe_profile_begin": [vp, i32],
             "fhe_profile_end": [vp, vp, i32],
             "fhe_mf_rotation_steps": [vp, i32, vp, sz],
@@ -301,6 +302,12 @@ class Context:
                                                     _ptr(UR), _ptr(R), _stream(stream)))
 
     # ---- launch accounting
+    def probe_butterfly_rate(self, reps: int = 2000) -> float:
+        """Register-only rate of the NTT butterfly arithmetic on this GPU, in 10^9 butterflies/s."""
+        out = ctypes.c_double(0.0)
+        self._check(lib().fhe_probe_butterfly_rate(self.h, reps, ctypes.byref(out)))
+        return out.value
+
     def profile_begin(self, time_kernels: bool = False):
         self._check(lib().fhe_profile_begin(self.h, 1 if time_kernels else 0))
 

@@ -65,11 +65,17 @@ __device__ __forceinline__ int auto_src(int k, int g, int log_n) {
 
 constexpr int kMaxHoist = 31;
 
-// Rotation keys of a hoisted rotate-and-sum (passed by value as a kernel parameter).
+// Rotation keys of a hoisted rotate-and-sum (host side).
 struct HoistKeys {
     const u64* key[kMaxHoist];
     int galois[kMaxHoist];
     int count;
+};
+
+// One rotation of a hoisted rotate-and-sum, as the kernel reads it from a device table.
+struct HoistStep {
+    const u64* key;
+    long long galois;
 };
 
 struct CombineArgs {
@@ -260,11 +266,16 @@ __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const Prime& P) {
     return add_mod(mul_mod(h, r64, P), l, q);
 }
 
+// (hi, lo) += a * b: mac128 in C, mac128_cc as one PTX multiply-add with carry. The hoisted kernel
+// runs faster with the former and the plain key inner product with the latter (measured).
 __device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 a, u64 b) {
     const u64 pl = a * b;
     const u64 ph = __umul64hi(a, b);
     lo += pl;
     hi += ph + (lo < pl ? 1 : 0);
+}
+__device__ __forceinline__ void mac128_cc(u64& lo, u64& hi, u64 a, u64 b) {
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
 }
 
 // Slots (2 k2, 2 k2 + 1) of phi_g(row): the automorphism maps the aligned pair onto an aligned pair.
@@ -307,10 +318,10 @@ __global__ void __launch_bounds__(256, 4) ks_inner_kernel(u64* acc, const u64* _
             }
             const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
             const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
-            mac128(a0x, h0x, vx, kb.x);
-            mac128(a0y, h0y, vy, kb.y);
-            mac128(a1x, h1x, vx, ka.x);
-            mac128(a1y, h1y, vy, ka.y);
+            mac128_cc(a0x, h0x, vx, kb.x);
+            mac128_cc(a0y, h0y, vy, kb.y);
+            mac128_cc(a1x, h1x, vx, ka.x);
+            mac128_cc(a1y, h1y, vy, ka.y);
         }
         reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] =
             make_ulonglong2(reduce128(a0x, h0x, P), reduce128(a0y, h0y, P));
@@ -324,9 +335,10 @@ __global__ void __launch_bounds__(256, 4) ks_inner_kernel(u64* acc, const u64* _
 // inside it; the 128-bit sums are reduced once. For x < l1 also c0sum[t][x][k] = c0[x][k] +
 // sum_r c0[x][pi_r(k)]. The limb index is the slowest, so one limb's rows of all kp - 1 keys stay in
 // L2 while every item reads them.
-__global__ void __launch_bounds__(256, 4) ks_hoist_inner_kernel(u64* acc, u64* c0sum, const u64* __restrict__ ext, const KsItem* __restrict__ tab,
-                                      HoistKeys hk, int items, int dn, int alpha, int next, int level, int L,
-                                      int n_ext, int log_n, const Prime* __restrict__ pr) {
+__global__ void __launch_bounds__(256, 3) ks_hoist_inner_kernel(
+    u64* acc, u64* c0sum, const u64* __restrict__ ext, const KsItem* __restrict__ tab,
+    const HoistStep* __restrict__ steps, int n_steps, int items, int dn, int alpha, int next, int level, int L, int n_ext,
+    int log_n, const Prime* __restrict__ pr) {
     const size_t half = (size_t)1 << (log_n - 1);
     const size_t total = (size_t)items * next * half;
     const int l1 = level + 1;
@@ -335,37 +347,43 @@ __global__ void __launch_bounds__(256, 4) ks_hoist_inner_kernel(u64* acc, u64* c
         const size_t row = e >> (log_n - 1);
         const int t = (int)(row % items), x = (int)(row / items);
         const int px = x < l1 ? x : x + (L - level);
-        const Prime P = pr[px];
-        const KsItem it = tab[t];
         const int own = x < l1 ? x / alpha : -1;
+        // digit j's row of this limb, in pairs: ext rows (stride next*N) and the item's c1 for its own digit
+        const ulonglong2* ext0 = reinterpret_cast<const ulonglong2*>(ext) + (((size_t)t * dn * next + x) << (log_n - 1));
+        const ulonglong2* own_row = reinterpret_cast<const ulonglong2*>(tab[t].d) + ((size_t)x << (log_n - 1));
+        const size_t dstride = (size_t)next << (log_n - 1);
+        const size_t kstride = (size_t)n_ext << (log_n - 1);
+        const size_t koff = ((size_t)px << (log_n - 1)) + k2;
         u64 a0x = 0, h0x = 0, a0y = 0, h0y = 0, a1x = 0, h1x = 0, a1y = 0, h1y = 0;
-        for (int r = 0; r < hk.count; r++) {
-            const int g = hk.galois[r];
-            const u64* key = hk.key[r];
+        for (int r = 0; r < n_steps; r++) {
+            const HoistStep st = steps[r];
+            const int src = auto_src(2 * k2, (int)st.galois, log_n);
+            const int sp = src >> 1;
+            const bool sw = src & 1;
+            const ulonglong2* kr = reinterpret_cast<const ulonglong2*>(st.key) + koff;
             for (int j = 0; j < dn; j++) {
-                const u64* src = j == own ? it.d + ((size_t)x << log_n)
-                                          : ext + ((size_t)((t * dn + j) * next + x) << log_n);
-                u64 vx, vy;
-                load_pair_auto(src, k2, g, log_n, vx, vy);
-                const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
-                const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
+                const ulonglong2 v = (j == own ? own_row : ext0 + (size_t)j * dstride)[sp];
+                const u64 vx = sw ? v.y : v.x, vy = sw ? v.x : v.y;
+                const ulonglong2 kb = kr[(size_t)(2 * j) * kstride];
+                const ulonglong2 ka = kr[(size_t)(2 * j + 1) * kstride];
                 mac128(a0x, h0x, vx, kb.x);
                 mac128(a0y, h0y, vy, kb.y);
                 mac128(a1x, h1x, vx, ka.x);
                 mac128(a1y, h1y, vy, ka.y);
             }
         }
+        const Prime P = pr[px];
         reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] =
             make_ulonglong2(reduce128(a0x, h0x, P), reduce128(a0y, h0y, P));
         reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] =
             make_ulonglong2(reduce128(a1x, h1x, P), reduce128(a1y, h1y, P));
         if (x < l1) {
-            const u64* c0 = it.addP0 + ((size_t)x << log_n);
+            const u64* c0 = tab[t].addP0 + ((size_t)x << log_n);
             const ulonglong2 self = reinterpret_cast<const ulonglong2*>(c0)[k2];
             u64 sx = self.x, sy = self.y;
-            for (int r = 0; r < hk.count; r++) {
+            for (int r = 0; r < n_steps; r++) {
                 u64 vx, vy;
-                load_pair_auto(c0, k2, hk.galois[r], log_n, vx, vy);
+                load_pair_auto(c0, k2, (int)steps[r].galois, log_n, vx, vy);
                 sx = add_mod(sx, vx, P.q);
                 sy = add_mod(sy, vy, P.q);
             }
@@ -466,8 +484,11 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
                             8.0 * n * ((double)items * (dn * next + l1) + (double)hk->count * dn * 2 * next +
                                        (double)items * (2 * next + l1)),
                             s);
+            std::vector<HoistStep> hs;
+            for (int r = 0; r < hk->count; r++) hs.push_back({hk->key[r], (long long)hk->galois[r]});
+            const HoistStep* d_hs = c.arena.push_vec(hs, s);
             ks_hoist_inner_kernel<<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(
-                acc, c0sum, ext, d_items, *hk, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
+                acc, c0sum, ext, d_items, d_hs, hk->count, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
             CK(cudaGetLastError());
             // the combine adds c0sum to component 0 and c1 to component 1
             std::vector<KsItem> it5(it);

@@ -2,10 +2,16 @@
 
   python -m paper_2509_03024_gb300.kernel_driver ntt --preset paper --rows 1024 [--inverse] [--reps 3]
   python -m paper_2509_03024_gb300.kernel_driver keyswitch --preset paper --count 64 [--reps 3]
+  python -m paper_2509_03024_gb300.kernel_driver rotsum --preset paper --count 64 --kp 16 [--reps 3]
+  python -m paper_2509_03024_gb300.kernel_driver probe --preset paper [--reps 2000]
 
 `ntt` transforms `rows` limbs of N residues in place (rows / (L+1) polynomials
 of L+1 limbs); `keyswitch` rotates `count` top-level ciphertexts by one slot
-(automorphism + hybrid key switch). Prints CUDA-event timings per repetition.
+(automorphism + hybrid key switch); `rotsum` runs the in-block rotate-and-sum over kp
+slots on `count` ciphertexts one level below the top (the level of the per-group
+product in an epoch). Prints CUDA-event timings per repetition and, for the last
+repetition, the device time of each kernel class; `probe` prints the register-only
+butterfly rate of fhe_probe_butterfly_rate (`reps` loop trips).
 """
 from __future__ import annotations
 
@@ -21,7 +27,8 @@ def main():
     from paper_2509_03024_gb300.workloads import PRESETS
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("kind", choices=["ntt", "keyswitch"])
+    ap.add_argument("kind", choices=["ntt", "keyswitch", "rotsum", "probe"])
+    ap.add_argument("--kp", type=int, default=16)
     ap.add_argument("--preset", default="paper")
     ap.add_argument("--rows", type=int, default=1024)
     ap.add_argument("--count", type=int, default=64)
@@ -30,8 +37,14 @@ def main():
     args = ap.parse_args()
     build.build()
     ctx = capi.Context.from_preset(PRESETS[args.preset])
+    if args.kind == "probe":
+        print(json.dumps({"kind": "probe", "preset": args.preset, "reps": args.reps,
+                          "gbfly_per_s": ctx.probe_butterfly_rate(args.reps)}))
+        return
     if args.kind == "keyswitch":
         ctx.keygen(1, [1])
+    elif args.kind == "rotsum":
+        ctx.keygen(1, list(range(1, args.kp)) if args.kp <= 16 else [1 << t for t in range(args.kp.bit_length() - 1)])
     L1 = ctx.top + 1
     times = []
     if args.kind == "ntt":
@@ -50,21 +63,31 @@ def main():
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         alg = 16.0 * polys * L1 * ctx.n
-    else:
+    if args.kind != "ntt":
         cts = ctx.empty_ct(args.count)
         for t in range(args.count):
             w = 2 * L1 * ctx.n
             ctx.encrypt(np.random.default_rng(t).normal(size=16), ctx.top, t, cts[t * w:(t + 1) * w])
         out = ctx.empty_ct(args.count)
-        for _ in range(args.reps):
+        for r in range(args.reps):
+            last = r == args.reps - 1
+            if last:
+                ctx.profile_begin(True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            ctx.rotate(cts, out, args.count, ctx.top, 1)
+            if args.kind == "keyswitch":
+                ctx.rotate(cts, out, args.count, ctx.top, 1)
+            else:
+                ctx.rotate_sum(cts, out, args.count, ctx.top - 1, args.kp)
             e1.record()
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
+            if last:
+                per_class = {k: v[1] for k, v in ctx.profile_end().items()}
         alg = None
     res = {"kind": args.kind, "preset": args.preset, "ms": times}
+    if args.kind != "ntt":
+        res["kernel_ms"] = per_class
     if alg:
         res["alg_gbs_best"] = alg / (min(times) / 1e3) / 1e9
     print(json.dumps(res))
