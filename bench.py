@@ -143,9 +143,10 @@ def oracle_sample(train, U, V, groups_sampled: int = 1):
     emf = mf.EncryptedMF(he, plan)
     top = he.prm.top
     pick = list(range(0, len(plan.groups), max(1, len(plan.groups) // groups_sampled)))[:groups_sampled]
-    emf.R = [None] * len(plan.groups)
+    emf.R = [None] * len(plan.bin_batch)
     for t in pick:
-        emf.R[t] = he.encrypt(mf.rating_slots(plan.groups[t], plan), top, mf.R_NONCE_BASE + t)
+        bt = plan.bin_of[t]
+        emf.R[bt] = he.encrypt(mf.bin_slots(bt, plan), top, mf.R_NONCE_BASE + bt)
     UD = {g.b: None for g in (plan.groups[t] for t in pick)}
     for b in UD:
         UD[b] = he.encrypt(mf.pack_factors(U, plan, b), top, mf.U_NONCE_BASE + b)
@@ -425,7 +426,8 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "ratings_per_step": ratings, "parallelism": "replicas",
-                      "l2": "inputs larger than L2 (rating ciphertexts alone are ~16 GiB)",
+                      "l2": "inputs larger than L2 (the rating ciphertexts alone are ~8 GiB)",
+                      "rating_bins": int(plan.info.n_bins),
                       "groups": int(plan.info.n_groups), "tree_nodes": int(plan.info.n_tree_nodes),
                       "plan_device_gib": plan.info.device_bytes / 2 ** 30},
            "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,

@@ -234,6 +234,7 @@ typedef struct {
     int32_t n_user_batches, n_item_batches;
     int64_t n_ratings, n_groups;         /* M and the number of (b, c, delta) groups */
     int64_t n_tree_nodes;                /* delta-tree nodes over all item batches   */
+    int64_t n_bins;                      /* rating ciphertexts (bins)                */
     size_t device_bytes;                 /* device memory owned by the plan          */
 } fhe_mf_plan_info;
 
@@ -246,8 +247,11 @@ int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t ca
  * Input: the n x m rating matrix in CSR form (host: row_ptr[n+1] int64,
  * col_idx[M] int32, vals[M] double; Sec. II-A.3), rank k. Users and items are
  * cut into batches of B; a rating (i, j) joins group (i div B, j div B,
- * (j mod B - i mod B) mod B). Each group's ratings are encrypted at the top
- * level (nonce 2^40 + group index, groups in (b, c, delta) order) and kept on
+ * (j mod B - i mod B) mod B), groups in (b, c, delta) order. The ratings are
+ * stored in bins (the paper packs many ratings per ciphertext, Sec. III-C):
+ * within each user batch, each group goes to the first bin (in creation order)
+ * that holds none of its users, else to a new bin; bins are numbered batch by
+ * batch. Each bin is encrypted at the top level (nonce 2^40 + bin) and kept on
  * the device by the plan. Duplicate (i, j) pairs are rejected. */
 int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* row_ptr,
                  const int32_t* col_idx, const double* vals, fhe_mf_plan** out);
@@ -257,6 +261,8 @@ int fhe_mf_plan_get_info(const fhe_mf_plan* plan, fhe_mf_plan_info* out);
  * user batch b, item batch c, delta, and the number of ratings in the group. */
 int fhe_mf_plan_get_groups(const fhe_mf_plan* plan, int32_t* b, int32_t* c, int32_t* delta,
                            int32_t* count);
+/* Copy the rating bin of each group (host int32[n_groups]). */
+int fhe_mf_plan_get_bins(const fhe_mf_plan* plan, int32_t* bin_of_group);
 
 /* Tuning: process at most `groups_per_chunk` groups per launch set of the
  * epoch (default: as many as fit a 6 GiB work area). Results do not depend on it. */

@@ -96,6 +96,8 @@ class Plan:
     closure: List[List[int]]   # per item batch c: sorted delta tree nodes (0 included)
     nnz_u: np.ndarray
     nnz_v: np.ndarray
+    bin_of: List[int]          # rating bin of each group
+    bin_batch: List[int]       # user batch of each bin
 
     def rotation_steps(self) -> List[int]:
         """Every left-rotation amount an epoch uses (negative = right)."""
@@ -139,6 +141,33 @@ def delta_closure(deltas) -> List[int]:
     return sorted(nodes)
 
 
+def assign_bins(groups: Sequence[Group], n_ub: int) -> Tuple[List[int], List[int]]:
+    """Rating bins: the ciphertexts that store the ratings (the paper packs L ratings per
+    ciphertext, Sec. III-C). Within each user batch, groups in plan order go to the first bin
+    (in creation order) that holds none of their users; if every bin does, a new bin opens. A
+    bin therefore holds at most one rating per user block, and a group's ratings all lie in
+    one bin. Bins are numbered batch by batch. Returns (bin of each group, batch of each bin)."""
+    bin_of = [0] * len(groups)
+    bin_batch: List[int] = []
+    for b in range(n_ub):
+        first = len(bin_batch)
+        users_in: List[set] = []
+        for t, g in enumerate(groups):
+            if g.b != b:
+                continue
+            users = set(int(a) for a in g.a)
+            for i, taken in enumerate(users_in):
+                if not (taken & users):
+                    taken |= users
+                    bin_of[t] = first + i
+                    break
+            else:
+                users_in.append(users)
+                bin_batch.append(b)
+                bin_of[t] = first + len(users_in) - 1
+    return bin_of, bin_batch
+
+
 def batch_pairs(rows, cols, B: int) -> Dict[Tuple[int, int], List[Tuple[int, int]]]:
     """Alg. 2 / Fig. 5 grouping: ratings keyed by (user batch i div B, item batch j div B)."""
     out: Dict[Tuple[int, int], List[Tuple[int, int]]] = {}
@@ -174,7 +203,8 @@ def build_plan(n: int, m: int, k: int, rows, cols, vals, slots: int) -> Plan:
         closure.append(delta_closure([g.delta for g in glist if g.c == c]))
     nnz_u = np.bincount(rows, minlength=n).astype(np.int64)
     nnz_v = np.bincount(cols, minlength=m).astype(np.int64)
-    return Plan(n, m, k, kp, w, B, n_ub, n_vb, glist, closure, nnz_u, nnz_v)
+    bin_of, bin_batch = assign_bins(glist, n_ub)
+    return Plan(n, m, k, kp, w, B, n_ub, n_vb, glist, closure, nnz_u, nnz_v, bin_of, bin_batch)
 
 
 def pack_factors(X: np.ndarray, plan: Plan, batch: int) -> np.ndarray:
@@ -205,6 +235,15 @@ def rating_slots(g: Group, plan: Plan) -> np.ndarray:
     z = np.zeros(plan.B * plan.w)
     for a, r in zip(g.a.tolist(), g.r.tolist()):
         z[a * plan.w: a * plan.w + plan.k] = r
+    return z
+
+
+def bin_slots(t: int, plan: Plan) -> np.ndarray:
+    """Slot vector of rating bin t: every group of the bin in its own user blocks."""
+    z = np.zeros(plan.B * plan.w)
+    for g, bt in zip(plan.groups, plan.bin_of):
+        if bt == t:
+            z += rating_slots(g, plan)
     return z
 
 
@@ -289,10 +328,11 @@ class EncryptedMF:
         self.R: List[Ciphertext] = []
 
     def encrypt_ratings(self) -> None:
-        """The CSP's EncryptCsrMatrix step (Alg. 1): R_g at the top level, nonce R_NONCE_BASE + g."""
+        """The CSP's EncryptCsrMatrix step (Alg. 1): one ciphertext per rating bin at the top
+        level, nonce R_NONCE_BASE + bin."""
         top = self.he.prm.top
-        self.R = [self.he.encrypt(rating_slots(g, self.plan), top, R_NONCE_BASE + t)
-                  for t, g in enumerate(self.plan.groups)]
+        self.R = [self.he.encrypt(bin_slots(t, self.plan), top, R_NONCE_BASE + t)
+                  for t in range(len(self.plan.bin_batch))]
 
     def encrypt_factors(self, U: np.ndarray, V: np.ndarray):
         top = self.he.prm.top
@@ -315,7 +355,7 @@ class EncryptedMF:
         he, p = self.he, self.plan
         g = p.groups[t]
         S = block_sum(he, he.mul_relin_rescale(UD_b, vr), p.kp)
-        E = he.sub(he.drop(self.R[t], S.level), S)
+        E = he.sub(he.drop(self.R[p.bin_of[t]], S.level), S)   # exact on g's blocks; the mask kills the rest
         mask = he.enc.encode(mask_slots(g, p, lr))
         M = he.rescale(he.mul_plain(vr, mask))
         MU = he.rescale(he.mul_plain(UD_b, mask))

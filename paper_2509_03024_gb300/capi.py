@@ -30,7 +30,7 @@ EXPORTS = [
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
     "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
-    "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
+    "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_get_bins", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
     "fhe_serve_poll", "fhe_serve_encrypt_request", "fhe_serve_take",
@@ -66,7 +66,7 @@ class PlanInfo(ctypes.Structure):
                 ("kp", ctypes.c_int32), ("w", ctypes.c_int32), ("B", ctypes.c_int32),
                 ("n_user_batches", ctypes.c_int32), ("n_item_batches", ctypes.c_int32),
                 ("n_ratings", ctypes.c_int64), ("n_groups", ctypes.c_int64),
-                ("n_tree_nodes", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+                ("n_tree_nodes", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
             "fhe_mf_plan_destroy": [vp],
             "fhe_mf_plan_get_info": [vp, ctypes.POINTER(PlanInfo)],
             "fhe_mf_plan_get_groups": [vp, vp, vp, vp, vp],
+            "fhe_mf_plan_get_bins": [vp, vp],
             "fhe_mf_plan_set_chunk": [vp, i32],
             "fhe_mf_encrypt_factors": [vp, vp, i32, vp, i32, vp, vp],
             "fhe_mf_decrypt_factors": [vp, vp, i32, vp, i32, vp, i32, vp],
@@ -364,6 +365,12 @@ class MfPlan:
         self.ctx._check(lib().fhe_mf_plan_get_groups(self.h, b.ctypes.data, c.ctypes.data, d.ctypes.data,
                                                      cnt.ctypes.data))
         return b, c, d, cnt
+
+    def bins(self):
+        """Rating bin of each group (int32 [n_groups])."""
+        out = np.zeros(max(int(self.info.n_groups), 1), dtype=np.int32)
+        self.ctx._check(lib().fhe_mf_plan_get_bins(self.h, out.ctypes.data))
+        return out[: int(self.info.n_groups)]
 
     def set_chunk(self, groups_per_chunk: int):
         self.ctx._check(lib().fhe_mf_plan_set_chunk(self.h, groups_per_chunk))

@@ -64,7 +64,9 @@ struct fhe_mf_plan {
     std::vector<int> node_of;               // [n_vb * B] -> node id or -1
     std::vector<int> group_node;            // node of each group
     std::vector<int> nnz_u, nnz_v;
-    u64* d_R = nullptr;                     // [G] rating ciphertexts, top level
+    std::vector<int> bin_of;                // rating bin of each group
+    std::vector<int> bin_b;                 // user batch of each bin
+    u64* d_R = nullptr;                     // [bins] rating ciphertexts, top level
     // plaintext caches (learning-rate dependent)
     bool have_plain = false;
     double lr_c = 0, lam_c = 0;
@@ -289,7 +291,8 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
         u64* cur = Tb;
         // E = R - S
         std::vector<BinItem> esub;
-        for (int i = 0; i < cnt; i++) esub.push_back({p.d_R + (size_t)(g0 + i) * w, cur + (size_t)i * w, Eb + (size_t)i * w});
+        for (int i = 0; i < cnt; i++)
+            esub.push_back({p.d_R + (size_t)p.bin_of[g0 + i] * w, cur + (size_t)i * w, Eb + (size_t)i * w});
         items_add(c, esub, 2, l1 + 1, true, s);
         // masks: M = rescale(Vr (.) mask), MU = rescale(UD (.) mask)
         materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, cnt, l0 + 1, PTb, lw, s);
@@ -582,31 +585,68 @@ int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* r
                 }
         }
         for (const Group& g : p->groups) p->group_node.push_back(p->node(g.c, g.delta));
-        // EncryptCsrMatrix: each group's ratings in the first k slots of their blocks, top level
+        // Rating bins: within each user batch, groups in plan order go to the first bin (in creation
+        // order) holding none of their users, else to a new bin; bins are numbered batch by batch.
         const int G = (int)p->groups.size();
+        p->bin_of.assign(G, 0);
+        {
+            const int words = (p->B + 63) / 64;
+            std::vector<uint64_t> gbits(words);
+            int g = 0;
+            for (int b = 0; b < p->n_ub; b++) {
+                const int first = (int)p->bin_b.size();
+                std::vector<std::vector<uint64_t>> taken;
+                for (; g < G && p->groups[g].b == b; g++) {
+                    std::fill(gbits.begin(), gbits.end(), 0);
+                    for (int a : p->groups[g].a) gbits[a >> 6] |= 1ull << (a & 63);
+                    int chosen = -1;
+                    for (size_t t = 0; t < taken.size() && chosen < 0; t++) {
+                        bool clash = false;
+                        for (int x = 0; x < words && !clash; x++) clash = (taken[t][x] & gbits[x]) != 0;
+                        if (!clash) chosen = (int)t;
+                    }
+                    if (chosen < 0) {
+                        taken.emplace_back(words, 0);
+                        p->bin_b.push_back(b);
+                        chosen = (int)taken.size() - 1;
+                    }
+                    for (int x = 0; x < words; x++) taken[chosen][x] |= gbits[x];
+                    p->bin_of[g] = first + chosen;
+                }
+            }
+        }
+        // EncryptCsrMatrix: one ciphertext per bin, each group's ratings in the first k slots of
+        // their user blocks, top level, nonce 2^40 + bin
+        const int NB = (int)p->bin_b.size();
+        std::vector<std::vector<std::pair<int, double>>> bin_nz(NB);
+        for (int gi = 0; gi < G; gi++) {
+            const Group& gr = p->groups[gi];
+            for (size_t t = 0; t < gr.a.size(); t++)
+                if (gr.r[t] != 0.0)
+                    for (int x = 0; x < p->k; x++) bin_nz[p->bin_of[gi]].push_back({gr.a[t] * p->w + x, gr.r[t]});
+        }
         const size_t w = c.ct_words();
-        p->d_R = plan_alloc<u64>(*p, (size_t)std::max(G, 1) * w);
+        p->d_R = plan_alloc<u64>(*p, (size_t)std::max(NB, 1) * w);
         const int chunk = 256;
         i64* m_dev = (i64*)c.scratch_bytes("pack_m", sizeof(i64) * chunk * c.n);
-        for (int g0 = 0; g0 < G; g0 += chunk) {
-            int g1 = std::min(G, g0 + chunk);
+        for (int t0 = 0; t0 < NB; t0 += chunk) {
+            int t1 = std::min(NB, t0 + chunk);
             std::vector<int> idx, off{0};
             std::vector<double> val;
             std::vector<u64> nonces;
-            for (int g = g0; g < g1; g++) {
-                const Group& gr = p->groups[g];
-                for (size_t t = 0; t < gr.a.size(); t++)
-                    if (gr.r[t] != 0.0)
-                        for (int x = 0; x < p->k; x++) {
-                            idx.push_back(gr.a[t] * p->w + x);
-                            val.push_back(gr.r[t]);
-                        }
+            for (int t = t0; t < t1; t++) {
+                auto& nz = bin_nz[t];
+                std::sort(nz.begin(), nz.end());  // ascending slots: the encoding's summation order
+                for (auto& e : nz) {
+                    idx.push_back(e.first);
+                    val.push_back(e.second);
+                }
                 off.push_back((int)idx.size());
-                nonces.push_back(kRNonce + (u64)g);
+                nonces.push_back(kRNonce + (u64)t);
             }
             c.arena.reset(0);
             encode_many_device(c, idx, val, off, m_dev, 0);
-            encrypt_coeffs_device(c, m_dev, c.n, g1 - g0, c.L, nonces, p->d_R + (size_t)g0 * w, 0);
+            encrypt_coeffs_device(c, m_dev, c.n, t1 - t0, c.L, nonces, p->d_R + (size_t)t0 * w, 0);
         }
         CK(cudaStreamSynchronize(0));
     });
@@ -652,7 +692,14 @@ int fhe_mf_plan_get_info(const fhe_mf_plan* p, fhe_mf_plan_info* out) {
     out->n_ratings = p->M;
     out->n_groups = (int64_t)p->groups.size();
     out->n_tree_nodes = (int64_t)p->node_c.size();
+    out->n_bins = (int64_t)p->bin_b.size();
     out->device_bytes = p->bytes;
+    return FHE_OK;
+}
+
+int fhe_mf_plan_get_bins(const fhe_mf_plan* p, int32_t* bin_of_group) {
+    if (!p || !bin_of_group) return FHE_ERR_INVALID_ARG;
+    std::copy(p->bin_of.begin(), p->bin_of.end(), bin_of_group);
     return FHE_OK;
 }
 

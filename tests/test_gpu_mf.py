@@ -59,6 +59,7 @@ def test_plan_groups_and_factor_encryption_bit_exact():
     b, c, d, cnt = plan.groups()
     assert list(zip(b, c, d, cnt)) == [(g.b, g.c, g.delta, len(g.a)) for g in oplan.groups]
     assert plan.info.n_tree_nodes == sum(len(x) for x in oplan.closure)
+    assert plan.bins().tolist() == oplan.bin_of and plan.info.n_bins == len(oplan.bin_batch)
     got = to_coeff(ctx, UD, ctx.top, plan.n_ub)
     for t, o in enumerate(oUD):
         assert_ct_equal(got[t], o, f"UD[{t}]")
@@ -154,6 +155,18 @@ def test_tiny_config_epoch_bit_exact():
     U1, V1 = mf.mf_epoch_fp64(U, V, rows, cols, vals, lr, lam)
     assert np.abs(plan.decrypt_factors(0, UD, 0, csr.n) - U1).max() < 1e-3
     assert np.abs(plan.decrypt_factors(1, VD, 0, csr.m) - V1).max() < 1e-3
+
+
+def test_rating_bins_match_oracle_at_paper_scale():
+    """The bin assignment of the paper-scale workload (943 x 1682, 90k ratings, k = 10) is the oracle's;
+    about half as many rating ciphertexts as groups."""
+    train, _, _, _ = W.paper_workload(seed=2)
+    ctx = gpu_ctx("paper", SEED)
+    plan = capi.MfPlan(ctx, train.n, train.m, 10, train.row_ptr, train.col_idx, train.vals)
+    rows, cols, vals = train.triples()
+    oplan = mf.build_plan(train.n, train.m, 10, rows, cols, vals, ctx.slots)
+    assert plan.bins().tolist() == oplan.bin_of
+    assert plan.info.n_bins == len(oplan.bin_batch) < plan.info.n_groups
 
 
 def test_csr_pack_rejects_bad_input():

@@ -134,7 +134,39 @@ def test_encrypted_epoch_group_order_independent():
     U2, V2 = emf.epoch(UD, VD, 0.01, 0.02)
     perm = np.random.default_rng(3).permutation(len(plan.groups))
     plan.groups = [plan.groups[t] for t in perm]
-    emf.R = [emf.R[t] for t in perm]
+    plan.bin_of = [plan.bin_of[t] for t in perm]   # the bins (and R) stay; each group keeps its bin
     U3, V3 = emf.epoch(UD, VD, 0.01, 0.02)
     for a, b in zip(U2 + V2, U3 + V3):
         assert (a.c == b.c).all()
+
+
+def test_rating_bins_first_fit_hand_example():
+    """B = 4 user blocks, one item batch; groups (delta order) with user sets {0,1}, {2}, {1,2}, {3}:
+    first fit puts them in bins 0, 0, 1, 0."""
+    # delta = (d - a) mod B: ratings (a, d) -> delta 0: (0,0),(1,1); 1: (2,3); 2: (1,3),(2,0); 3: (3,2)
+    rows = [0, 1, 2, 1, 2, 3]
+    cols = [0, 1, 3, 3, 0, 2]
+    plan = mf.build_plan(4, 4, 1, rows, cols, [1.0] * 6, slots=8)   # k = 1: w = 2, B = 4
+    assert plan.B == 4
+    assert [(g.delta, g.a.tolist()) for g in plan.groups] == [(0, [0, 1]), (1, [2]), (2, [1, 2]), (3, [3])]
+    assert plan.bin_of == [0, 0, 1, 0] and plan.bin_batch == [0, 0]
+
+
+def test_rating_bins_invariants():
+    """Every group lies in one bin; a bin holds each user block at most once; bins per user batch
+    are at least the most ratings of one user (every rating of a user needs its own bin)."""
+    train, _, _, _ = W.paper_workload(seed=2)
+    rows, cols, vals = train.triples()
+    plan = mf.build_plan(train.n, train.m, 10, rows, cols, vals, 1 << 14)
+    assert len(plan.bin_of) == len(plan.groups)
+    for t in range(len(plan.bin_batch)):
+        users = [a for g, bt in zip(plan.groups, plan.bin_of) if bt == t for a in g.a.tolist()]
+        assert len(users) == len(set(users))
+        assert all(plan.groups[i].b == plan.bin_batch[t] for i, bt in enumerate(plan.bin_of) if bt == t)
+    for b in range(plan.n_ub):
+        nb = sum(1 for x in plan.bin_batch if x == b)
+        lb = int(plan.nnz_u[b * plan.B:(b + 1) * plan.B].max())
+        assert lb <= nb <= 2 * lb
+    # the bin slot vectors carry every rating exactly once
+    total = sum(mf.bin_slots(t, plan).sum() for t in range(len(plan.bin_batch)))
+    assert abs(total - plan.k * vals.sum()) < 1e-6
