@@ -160,6 +160,25 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
     const int log_n2 = PASS == 0 ? log_n - LOGM : LOGM;
     const int S1 = log_n - log_n2;
     const int t0 = blockIdx.y * R;
+    if (PASS == 0 && R > 1) {
+        // column tiles: the first and last radix-8 blocks read and write global memory directly
+        constexpr int NB = (LOGM + 2) / 3;
+        const int qq = tid % R, g = tid / R;
+        const int fb = INV ? NB - 1 : 0, lb = INV ? 0 : NB - 1;
+        u64 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            v[u] = load_elem<LOAD>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(fb, g, u) << log_n2), log_n,
+                                   primes);
+        if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false, true, true>(sm, W, q, S1, t0, v);
+        else nttc::tile_stages<LOGM, R, INV, PASS, true, true, true>(sm, W, q, S1, t0, v);
+        const u64 one_s = primes[r.prime].one_s;
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            store_elem<INV, STORE>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(lb, g, u) << log_n2), v[u], q,
+                                   one_s, ninv, ca, log_n);
+        return;
+    }
     if (PASS == 0) {
 #pragma unroll 4
         for (int e = tid; e < R * M; e += T) {

@@ -66,6 +66,36 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     const int log_n2 = PASS == 0 ? log_n - LOGM : LOGM;  // row length of the N1 x N2 view
     const int S1 = log_n - log_n2;                       // column stages
     const int t0 = blockIdx.y * R;                       // first column (PASS 0) or row (PASS 1)
+    const u64 ni = ninv[2 * rp.prime], nis = ninv[2 * rp.prime + 1];
+
+    if (PASS == 0 && R > 1) {
+        // column tiles: the first and last radix-8 blocks read and write global memory directly
+        // (a warp covers 16 consecutive columns of two rows per access)
+        constexpr int NB = (LOGM + 2) / 3;
+        const int qq = tid % R, g = tid / R;
+        const int fb = INV ? NB - 1 : 0, lb = INV ? 0 : NB - 1;
+        u64 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            v[u] = rp.p[(size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(fb, g, u) << log_n2)];
+        if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false, true, true>(sm, W, q, S1, t0, v);
+        else nttc::tile_stages<LOGM, R, INV, PASS, true, true, true>(sm, W, q, S1, t0, v);
+        const u64 one_s = primes[rp.prime].one_s;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            u64 val = v[u];
+            if (LAST) {
+                if (INV) {
+                    u64 r = shoup_lazy(val, ni, nis, q);
+                    val = r >= q ? r - q : r;
+                } else {
+                    val = nttc::reduce_any(val, q, one_s);
+                }
+            }
+            rp.p[(size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(lb, g, u) << log_n2)] = val;
+        }
+        return;
+    }
 
     // load (coalesced), values enter in [0, q)
     if (PASS == 0) {
@@ -89,7 +119,6 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     const u64 one_s = primes[rp.prime].one_s;
 
     // store (coalesced)
-    const u64 ni = ninv[2 * rp.prime], nis = ninv[2 * rp.prime + 1];
     if (PASS == 0) {
 #pragma unroll 4
         for (int e = tid; e < R * M; e += T) {

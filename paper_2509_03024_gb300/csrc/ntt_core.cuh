@@ -47,13 +47,29 @@ __device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
     return x >= q ? x - q : x;
 }
 
-// Butterfly stages of one tile already in shared memory: R sub-transforms of
-// M = 2^LOGM points, element x of sub-transform q at sm[x * P + q]. PASS 0:
-// column transforms (stages [0, LOGM), twiddles W[2^s + group]); PASS 1: row
-// transforms (stages [S1, S1 + LOGM), transposed twiddles, tile rows t0..t0+R-1).
-// Ends with a __syncthreads(); the caller loads before and stores after.
-template <int LOGM, int R, bool INV, int PASS, bool RED = true>
-__device__ __forceinline__ void tile_stages(u64* sm, const ulonglong2* __restrict__ W, u64 q, int S1, int t0) {
+// Element x (within its sub-transform) that register u of 8-element group g holds in radix-8
+// block blk (block blk covers stages [3 blk, min(3 blk + 3, LOGM))).
+template <int LOGM>
+__device__ __forceinline__ int block_elem(int blk, int g, int u) {
+    constexpr int M = 1 << LOGM;
+    const int s0 = 3 * blk;
+    const int b = (LOGM - s0) < 3 ? (LOGM - s0) : 3;
+    const int d = M >> (s0 + b);
+    return (g / d) * (8 * d) + (g % d) + u * d;
+}
+
+// Butterfly stages of one tile: R sub-transforms of M = 2^LOGM points, element x of
+// sub-transform q at sm[x * P + q] between radix-8 blocks. PASS 0: column transforms
+// (stages [0, LOGM), twiddles W[2^s + group]); PASS 1: row transforms (stages
+// [S1, S1 + LOGM), transposed twiddles, tile rows t0..t0+R-1).
+// IN_REG: the first block takes its 8 values from v (the caller loaded the elements
+// block_elem(first block, g, u) from global memory) instead of from sm; otherwise the caller
+// fills sm and synchronises before. OUT_REG: the last block leaves its values in v (elements
+// block_elem(last block, g, u)) and neither stores nor synchronises; otherwise the result is in
+// sm after a final __syncthreads(). The first block is 0 (forward) or NB - 1 (inverse).
+template <int LOGM, int R, bool INV, int PASS, bool RED = true, bool IN_REG = false, bool OUT_REG = false>
+__device__ __forceinline__ void tile_stages(u64* sm, const ulonglong2* __restrict__ W, u64 q, int S1, int t0,
+                                            u64 (&v)[8]) {
     constexpr int M = 1 << LOGM;
     constexpr int P = R == 1 ? 1 : R + 1;
     const int tid = threadIdx.x;
@@ -61,7 +77,6 @@ __device__ __forceinline__ void tile_stages(u64* sm, const ulonglong2* __restric
     const int qq = tid % R;  // sub-transform of this thread
     const int g = tid / R;   // 8-element group within the sub-transform
     const int row_off = PASS == 1 ? t0 + qq : 0;
-    u64 v[8];
 
     // radix-8 blocks of stages; forward runs stages 0..LOGM-1, inverse LOGM-1..0
     constexpr int NB = (LOGM + 2) / 3;
@@ -74,8 +89,10 @@ __device__ __forceinline__ void tile_stages(u64* sm, const ulonglong2* __restric
         const int b = (LOGM - s0) < 3 ? (LOGM - s0) : 3;
         const int d = M >> (s0 + b);
         const int base = (g / d) * (8 * d) + (g % d);
+        if (!(IN_REG && bi == 0)) {
 #pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = sm[(base + u * d) * P + qq];
+            for (int u = 0; u < 8; u++) v[u] = sm[(base + u * d) * P + qq];
+        }
         // Twiddle of the pair (u, u + dist) at block stage j: its group index at stage s0 + j is
         // tb * 2^j + (u >> (b - j)), with tb = base >> (LOGM - s0) the thread's group at s0.
         const int tb = base >> (LOGM - s0);
@@ -110,11 +127,18 @@ __device__ __forceinline__ void tile_stages(u64* sm, const ulonglong2* __restric
                 }
             }
         }
+        if (!(OUT_REG && bi == NB - 1)) {
 #pragma unroll
-        for (int u = 0; u < 8; u++) sm[(base + u * d) * P + qq] = v[u];
-        __syncthreads();
+            for (int u = 0; u < 8; u++) sm[(base + u * d) * P + qq] = v[u];
+            __syncthreads();
+        }
     }
+}
 
+template <int LOGM, int R, bool INV, int PASS, bool RED = true>
+__device__ __forceinline__ void tile_stages(u64* sm, const ulonglong2* __restrict__ W, u64 q, int S1, int t0) {
+    u64 v[8];
+    tile_stages<LOGM, R, INV, PASS, RED, false, false>(sm, W, q, S1, t0, v);
 }
 
 }  // namespace nttc
