@@ -152,8 +152,12 @@ int fhe_sub(fhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, i
  * message (fhe_encode), applied to `count` ciphertexts. No rescale. */
 int fhe_mul_plain(fhe_ctx* ctx, const uint64_t* ct, const int64_t* pt_coeffs_dev, uint64_t* out,
                   int32_t count, int32_t level, void* stream);
-/* Ciphertext product (Eq. 7): tensor, relinearise with the s^2 key, then
- * rescale by q_level. Output at level-1. Needs level >= 1. */
+/* Ciphertext product (Eq. 7): tensor, then relinearise with the s^2 key and
+ * rescale by q_level in one key switch whose ModDown divides by P q_level
+ * (out_h = (acc_h + P c_h - Conv_{P u {q_l} -> Q_{l-1}}(acc_h + P c_h)) (P q_l)^-1,
+ * fast non-centred conversion; equal to fhe_relinearize then fhe_rescale up to a
+ * conversion error of at most alpha + 1 per coefficient). Output at level-1.
+ * Needs level >= 1. */
 int fhe_mul_relin_rescale(fhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out,
                           int32_t count, int32_t level, void* stream);
 /* Tensor only: out3 device [count][3][L+1][N] (three components, capacity limbs). */

@@ -512,6 +512,42 @@ class Ckks:
         k0, k1 = self.keyswitch(t.c[2], t.level, self.rlk)
         return Ciphertext(np.stack([self._add(t.c[0], k0, pr), self._add(t.c[1], k1, pr)]), t.level)
 
+    def relin_rescale(self, t: Ciphertext) -> Ciphertext:
+        """Relinearise and rescale in one step (level l -> l - 1): the key switch's ModDown divides
+        by P q_l instead of P. With acc_h = sum_j ModUp_j(d2) evk_j[h] over Q_l u P and
+        X_h = acc_h + P c_h (c_h the tensor's component h, which is zero on the P limbs):
+            out_h = (X_h - Conv_{P u {q_l} -> Q_{l-1}}(X_h)) (P q_l)^{-1}  mod q_i, i < l,
+        Conv being the fast (non-centred) base conversion. It equals floor(X_h / (P q_l)) - u with
+        0 <= u <= alpha, where rescale(relinearize(t)) rounds in two steps."""
+        prm = self.prm
+        lv = t.level
+        if lv < 1:
+            raise ValueError("relin_rescale needs level >= 1")
+        qs = prm.q[: lv + 1]
+        basis = qs + prm.p
+        rows = self._key_rows(lv)
+        dn = prm.dnum(lv)
+        ups = self._modup(t.c[2][: lv + 1], lv)
+        src_primes = [qs[lv]] + list(prm.p)
+        dst = qs[:lv]
+        Mp = prm.P * qs[lv]
+        out = []
+        for h, K in enumerate((self.rlk.b, self.rlk.a)):
+            Kx = K[:dn][:, rows]
+            acc = ring.polydot_rows(np.ascontiguousarray(ups.transpose(1, 0, 2)),
+                                    np.ascontiguousarray(Kx.transpose(1, 0, 2)), basis)
+            X = acc.copy()
+            for i, q in enumerate(qs):
+                X[i] = self._add(acc[i][None], ring.scalar_mul(t.c[h][i], prm.P % q, q)[None], [q])[0]
+            src = np.stack([X[lv]] + [X[lv + 1 + k] for k in range(prm.alpha)])
+            conv = ring.fast_base_conv(src, src_primes, dst)
+            diff = self._sub(X[:lv], conv, dst)
+            res = np.empty_like(diff)
+            for i, q in enumerate(dst):
+                res[i] = ring.scalar_mul(diff[i], pow(Mp % q, -1, q), q)
+            out.append(res)
+        return Ciphertext(np.stack(out), lv - 1)
+
     def rotate(self, a: Ciphertext, r: int) -> Ciphertext:
         """Left slot rotation by r: phi_g on both components, then key switch phi_g(c1) (g = 5^r)."""
         prm = self.prm
@@ -576,7 +612,8 @@ class Ckks:
         return Ciphertext(np.stack([c0, c1]), lv)
 
     def mul_relin_rescale(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
-        return self.rescale(self.relinearize(self.tensor(a, b)))
+        """Ciphertext product (Eq. 8) followed by the fused relinearise-rescale."""
+        return self.relin_rescale(self.tensor(a, b))
 
     def zero(self, level: int, parts: int = 2) -> Ciphertext:
         return Ciphertext(np.zeros((parts, level + 1, self.prm.n), dtype=np.uint64), level)

@@ -390,7 +390,7 @@ class EncryptedMF:
         out_lv = lv - 2
         newU = []
         for b in range(p.n_ub):
-            acc = he.zero(out_lv) if TU[b] is None else he.rescale(he.relinearize(TU[b]))
+            acc = he.zero(out_lv) if TU[b] is None else he.relin_rescale(TU[b])
             acc = he.add(acc, he.rotate(acc, -p.kp))
             reg = he.enc.encode(reg_slots(p.nnz_u, p, b, lr, lam))
             base = he.drop(he.rescale(he.mul_plain(UD[b], reg)), out_lv)
@@ -399,7 +399,7 @@ class EncryptedMF:
         for c in range(p.n_vb):
             H: Dict[int, Ciphertext] = {}
             for d in p.closure[c]:
-                H[d] = he.rescale(he.relinearize(TV[(c, d)])) if (c, d) in TV else he.zero(out_lv)
+                H[d] = he.relin_rescale(TV[(c, d)]) if (c, d) in TV else he.zero(out_lv)
             for d in sorted(p.closure[c], key=lambda x: (bin(x).count("1"), x), reverse=True):
                 if d:
                     hb = 1 << highest_bit(d)
@@ -426,5 +426,5 @@ class EncryptedMF:
             X = he.add(X, he.rotate(X, (1 << t) * p.w))
         out = []
         for c in range(p.n_vb):
-            out.append(block_sum(he, he.rescale(he.relinearize(he.tensor(X, VD[c]))), p.kp))
+            out.append(block_sum(he, he.mul_relin_rescale(X, VD[c]), p.kp))
         return out

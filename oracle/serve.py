@@ -102,7 +102,7 @@ def encrypt_request(he: Ckks, u0, items, ratings, k: int, n_vb: int, nonce_base:
 def inner_products(he: Ckks, UR: Ciphertext, V: Sequence[Ciphertext], batches, kp: int) -> List[Ciphertext]:
     out = []
     for c in batches:
-        out.append(block_sum(he, he.rescale(he.relinearize(he.tensor(UR, V[c]))), kp))
+        out.append(block_sum(he, he.mul_relin_rescale(UR, V[c]), kp))
     return out
 
 
@@ -120,7 +120,7 @@ def fold_in_step(he: Ckks, UR: Ciphertext, R: Sequence[Ciphertext], V: Sequence[
         t3 = he.tensor(E, MV)
         T = t3 if T is None else he.add(T, t3)
     out_lv = UR.level - 2
-    G = he.zero(out_lv) if T is None else he.rescale(he.relinearize(T))
+    G = he.zero(out_lv) if T is None else he.relin_rescale(T)
     for t in range(highest_bit(B)):
         G = he.add(G, he.rotate(G, (1 << t) * w))
     G = he.add(G, he.rotate(G, -kp))

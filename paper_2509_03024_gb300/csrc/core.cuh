@@ -257,6 +257,11 @@ struct Ctx {
     u64* d_down_hat = nullptr;        // [alpha][L+1][2] Phat_k mod q_i
     u64* d_pinv = nullptr;            // [L+1][2]     P^-1 mod q_i
     u64* d_pmod = nullptr;            // [L+1]        P mod q_i
+    // fused ModDown + rescale at level l (divide by M' = P q_l; sources p_0..p_{alpha-1}, q_l)
+    u64* d_fd_ninv = nullptr;         // [L+1][alpha+1][2]       N^-1 (M'/m_s)^-1 mod m_s
+    u64* d_fd_hat = nullptr;          // [L+1][alpha+1][L+1][2]  (M'/m_s) mod q_i, i < l
+    u64* d_fd_minv = nullptr;         // [L+1][L+1][2]           M'^-1 mod q_i, i < l
+    u64* d_fd_pq = nullptr;           // [L+1][2]                P mod q_l
     double* d_cos = nullptr;          // [2N] cos(pi e / N)
     double* d_sin = nullptr;          // [2N] sin(pi e / N)
     u32* d_pow5 = nullptr;            // [N/2] 5^t mod 2N
@@ -363,6 +368,11 @@ struct KsItem {
     long long galois;
 };
 void keyswitch_items(Ctx& c, const std::vector<KsItem>& it, int level, cudaStream_t s);
+
+// Relinearise and rescale in one key switch (ModDown divides by P q_level): out_i (level - 1)
+// from the 3-component t3_i (level). out_i may equal t3_i.
+void relin_rescale_items(Ctx& c, const std::vector<u64*>& t3, const std::vector<u64*>& out, int level,
+                         cudaStream_t s);
 
 // In-block rotate-and-sum: out_i = sum_{r < kp} rot(in_i, r). Hoisted (one ModUp, kp - 1 key inner
 // products, one ModDown; in_i may equal out_i) for 2 <= kp <= kHoistMaxKp, else log2(kp)

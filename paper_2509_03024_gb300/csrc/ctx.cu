@@ -64,7 +64,7 @@ Ctx::~Ctx() {
     cudaSetDevice(device);
     cudaDeviceSynchronize();
     void* bufs[] = {d_primes, d_psi, d_psi_s, d_ipsi, d_ipsi_s, d_ninv, d_tw, d_itw, d_tw2, d_itw2, d_up_ninv, d_down_ninv, d_resc, d_up_inv, d_up_hat,
-                    d_down_inv, d_down_hat, d_pinv, d_pmod, d_cos, d_sin, d_pow5, d_sk, d_pk, rlk.d};
+                    d_down_inv, d_down_hat, d_pinv, d_pmod, d_fd_ninv, d_fd_hat, d_fd_minv, d_fd_pq, d_cos, d_sin, d_pow5, d_sk, d_pk, rlk.d};
     for (void* p : bufs)
         if (p) cudaFree(p);
     for (auto& kv : rot)
@@ -372,6 +372,46 @@ static void build_tables(Ctx& c) {
     c.d_down_hat = dupload(dhat);
     c.d_pinv = dupload(pinv);
     c.d_pmod = dupload(pmod);
+
+    // fused ModDown + rescale at level l: divide by M' = P q_l; sources m_s = p_s (s < alpha), q_l (s = alpha)
+    {
+        const int S = A + 1;
+        std::vector<u64> fninv((size_t)2 * (L + 1) * S, 0), fhat((size_t)2 * (L + 1) * S * (L + 1), 0);
+        std::vector<u64> fminv((size_t)2 * (L + 1) * (L + 1), 0), fpq((size_t)2 * (L + 1), 0);
+        for (int l = 1; l <= L; l++) {
+            auto src = [&](int sidx) { return sidx < A ? c.primes[L + 1 + sidx] : c.primes[l]; };
+            for (int sidx = 0; sidx < S; sidx++) {
+                const u64 m = src(sidx);
+                u64 hat_m = 1;  // (M' / m) mod m
+                for (int s2 = 0; s2 < S; s2++)
+                    if (s2 != sidx) hat_m = h_mul(hat_m, src(s2) % m, m);
+                const u64 v = h_mul(h_inv(hat_m, m), h_inv((u64)n % m, m), m);
+                fninv[2 * ((size_t)l * S + sidx)] = v;
+                fninv[2 * ((size_t)l * S + sidx) + 1] = h_shoup(v, m);
+                for (int i = 0; i < l; i++) {
+                    const u64 q = c.primes[i];
+                    u64 h = 1;
+                    for (int s2 = 0; s2 < S; s2++)
+                        if (s2 != sidx) h = h_mul(h, src(s2) % q, q);
+                    const size_t o = 2 * (((size_t)l * S + sidx) * (L + 1) + i);
+                    fhat[o] = h;
+                    fhat[o + 1] = h_shoup(h, q);
+                }
+            }
+            for (int i = 0; i < l; i++) {
+                const u64 q = c.primes[i];
+                const u64 inv = h_inv(h_mul(pmod[i], c.primes[l] % q, q), q);
+                fminv[2 * ((size_t)l * (L + 1) + i)] = inv;
+                fminv[2 * ((size_t)l * (L + 1) + i) + 1] = h_shoup(inv, q);
+            }
+            fpq[2 * l] = pmod[l];
+            fpq[2 * l + 1] = h_shoup(pmod[l], c.primes[l]);
+        }
+        c.d_fd_ninv = dupload(fninv);
+        c.d_fd_hat = dupload(fhat);
+        c.d_fd_minv = dupload(fminv);
+        c.d_fd_pq = dupload(fpq);
+    }
 
     // encoding: cos / sin (pi e / N) for e < 2N, computed by the host libm; 5^t mod 2N
     std::vector<double> cs(2 * (size_t)n), sn(2 * (size_t)n);
@@ -1186,10 +1226,12 @@ int fhe_mul_relin_rescale(fhe_ctx* ctx, const uint64_t* a, const uint64_t* b, ui
         const size_t w = c.ct_words(), lw = w / 2;
         u64* t3 = c.scratch_u64("api_t3", (size_t)count * 3 * lw);
         items_tensor(c, bin_items(c, a, b, t3, count, w, w, 3 * lw), level + 1, S(stream));
-        relin_into(c, t3, t3, count, 3 * lw, level, S(stream));
-        std::vector<UnItem> it;
-        for (int t = 0; t < count; t++) it.push_back({t3 + t * 3 * lw, out + t * w});
-        items_rescale(c, it, 2, level, S(stream));
+        std::vector<u64*> in3, outs;
+        for (int t = 0; t < count; t++) {
+            in3.push_back(t3 + t * 3 * lw);
+            outs.push_back(out + t * w);
+        }
+        relin_rescale_items(c, in3, outs, level, S(stream));
     });
 }
 

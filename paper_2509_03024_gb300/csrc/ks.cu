@@ -39,8 +39,8 @@ namespace {
 using nttc::reduce4;
 using nttc::shoup_lazy;
 
-enum LoadMode { LD_PLAIN = 0, LD_GATHER = 1, LD_CONV = 2 };
-enum StoreMode { ST_LAZY = 0, ST_LAST = 1, ST_SCALE = 2, ST_COMBINE = 3 };
+enum LoadMode { LD_PLAIN = 0, LD_GATHER = 1, LD_CONV = 2, LD_AXPY = 3 };
+enum StoreMode { ST_LAZY = 0, ST_LAST = 1, ST_SCALE = 2, ST_COMBINE = 3, ST_COMBINE_RS = 4 };
 
 struct KsRow {
     u64* dst;        // the row's buffer (N residues)
@@ -50,8 +50,10 @@ struct KsRow {
     int galois;      // LD_GATHER: automorphism applied on load (1 = none)
     int src_cnt;     // LD_CONV: number of source limbs
     int cst_stride;  // LD_CONV: words between consecutive source limbs' constant pairs
-    int item, half, limb;  // ST_COMBINE: output item, component and limb
+    int item, half, limb;  // ST_COMBINE(_RS): output item, component and limb
     int pad;
+    const u64* src2;       // LD_AXPY: second source row (null: none)
+    const u64* cst2;       // LD_AXPY: Shoup pair of its factor
 };
 
 // Evaluation slot k holds a(psi^(2 brev(k) + 1)); X -> X^g moves slot k' to slot k
@@ -80,15 +82,22 @@ struct HoistStep {
 
 struct CombineArgs {
     const KsItem* items;
-    const u64* acc;  // [items][2][next][N]
-    const u64* pinv; // [L+1][2]
+    const u64* acc;    // [items][2][next][N]
+    const u64* pinv;   // [L+1][2] P^-1 mod q_i (ST_COMBINE) or (P q_l)^-1 mod q_i (ST_COMBINE_RS)
     int next;
+    const u64* qlinv;  // ST_COMBINE_RS: [L+1][2] q_l^-1 mod q_i
 };
 
 template <int LOAD>
 __device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, const Prime* __restrict__ pr) {
     if (LOAD == LD_PLAIN) return r.dst[k];
     if (LOAD == LD_GATHER) return r.src[r.galois == 1 ? (int)k : auto_src((int)k, r.galois, log_n)];
+    if (LOAD == LD_AXPY) {  // src + cst2 * src2 (both reduced)
+        const u64 p = pr[r.prime].q;
+        u64 v = r.src[k];
+        if (r.src2) v = add_mod(v, mul_shoup(r.src2[k], r.cst2[0], r.cst2[1], p), p);
+        return v;
+    }
     // LD_CONV: fully reduced sum of the converted source limbs
     const u64 p = pr[r.prime].q;
     u64 acc = 0;
@@ -123,12 +132,20 @@ __device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, u64 
         r.dst[k] = t >= q ? t - q : t;
         return;
     }
-    // ST_COMBINE (forward): out_h = (acc_h - v) * P^-1 + add terms
     const KsItem& it = ca.items[r.item];
     const size_t row_off = (size_t)r.limb << log_n;
     u64 conv = nttc::reduce_any(v, q, one_s);
     u64 a = ca.acc[((((size_t)r.item * 2 + r.half) * ca.next + r.limb) << log_n) + k];
     u64 d = a >= conv ? a - conv : a + q - conv;
+    if (STORE == ST_COMBINE_RS) {
+        // fused ModDown + rescale: out_h = (acc_h - conv) (P q_l)^-1 + c_h q_l^-1
+        const u64* c_h = r.half == 0 ? it.addI0 : it.addI1;
+        u64 t = mul_shoup(d, ca.pinv[2 * r.limb], ca.pinv[2 * r.limb + 1], q);
+        t = add_mod(t, mul_shoup(c_h[row_off + k], ca.qlinv[2 * r.limb], ca.qlinv[2 * r.limb + 1], q), q);
+        (r.half == 0 ? it.out0 : it.out1)[row_off + k] = t;
+        return;
+    }
+    // ST_COMBINE (forward): out_h = (acc_h - v) * P^-1 + add terms
     u64 t = shoup_lazy(d, ca.pinv[2 * r.limb], ca.pinv[2 * r.limb + 1], q);
     t = t >= q ? t - q : t;
     if (r.half == 0) {
@@ -422,12 +439,17 @@ namespace {
 
 // K1-K5 over a batch of items; with hk, K3 is the hoisted inner product (items' galois must be 1,
 // addP0 holds c0, d holds c1) and the outputs are sum_r rot(c, r) over r = 0 and hk's rotations.
-void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* hk, cudaStream_t s) {
+// With fused_rescale (relinearisation items: galois 1, addI0/addI1 = c0/c1, no addP0), K4/K5
+// divide by P q_level instead of P and the outputs are at level - 1:
+//   out_h = (acc_h + P c_h - Conv_{P u {q_l} -> Q_{l-1}}(acc_h + P c_h)) (P q_l)^-1.
+void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* hk, cudaStream_t s,
+            bool fused_rescale = false) {
     if (all.empty()) return;
     const int n = c.n, L = c.L, A = c.alpha, l1 = level + 1, next = l1 + A, dn = c.dnum(level);
+    const int SP = fused_rescale ? A + 1 : A;  // ModDown source limbs
     // bound the work area to ~6 GiB per sub-batch
     const size_t per_item =
-        (size_t)(l1 + dn * next + 2 * next + 2 * A + 2 * l1 + (hk ? l1 : 0)) * n * sizeof(u64);
+        (size_t)(l1 + dn * next + 2 * next + 2 * SP + 2 * l1 + (hk ? l1 : 0)) * n * sizeof(u64);
     const int max_items = (int)std::max<size_t>(1, ((size_t)6 << 30) / per_item);
     for (size_t b0 = 0; b0 < all.size(); b0 += max_items) {
         const int items = (int)std::min<size_t>(max_items, all.size() - b0);
@@ -443,10 +465,10 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
         u64* y = c.scratch_u64("ks_y", (size_t)items * l1 * n);
         u64* ext = c.scratch_u64("ks_ext", (size_t)items * dn * next * n);
         u64* acc = c.scratch_u64("ks_acc", (size_t)items * 2 * next * n);
-        u64* yP = c.scratch_u64("ks_yp", (size_t)items * 2 * A * n);
+        u64* yP = c.scratch_u64("ks_yp", (size_t)items * 2 * SP * n);
         u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
-        CombineArgs ca{d_items, acc, c.d_pinv, next};
-        const CombineArgs none{nullptr, nullptr, nullptr, 0};
+        CombineArgs ca{d_items, acc, c.d_pinv, next, nullptr};
+        const CombineArgs none{nullptr, nullptr, nullptr, 0, nullptr};
 
         // K1: y_i = INTT(perm(d_i)) * qhat_i^-1
         std::vector<KsRow> r1;
@@ -519,6 +541,50 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
             ca.items = c.arena.push_vec(it5, s);
         }
 
+        if (fused_rescale) {
+            // K4: y_s = INTT(source s) * N^-1 (M'/m_s)^-1 for m_s = p_0.., p_{alpha-1}, q_l, where the q_l
+            // source is acc_h + (P mod q_l) c_h
+            std::vector<KsRow> r4;
+            for (int t = 0; t < items; t++)
+                for (int h = 0; h < 2; h++)
+                    for (int sx = 0; sx < SP; sx++) {
+                        KsRow r{};
+                        r.dst = yP + (((size_t)t * 2 + h) * SP + sx) * n;
+                        const bool ql = sx == A;
+                        r.src = acc + (((size_t)t * 2 + h) * next + (ql ? level : l1 + sx)) * n;
+                        r.src2 = ql ? (h == 0 ? it[t].addI0 : it[t].addI1) + (size_t)level * n : nullptr;
+                        r.cst2 = c.d_fd_pq + 2 * (size_t)level;
+                        r.cst = c.d_fd_ninv + 2 * ((size_t)level * SP + sx);
+                        r.prime = ql ? level : L + 1 + sx;
+                        r.galois = 1;
+                        r4.push_back(r);
+                    }
+            const KsRow* d_r4 = c.arena.push_vec(r4, s);
+            ks_transform<true, LD_AXPY, ST_SCALE>(c, d_r4, (int)r4.size(), none, K_NTT_INV, 16.0 * r4.size() * n, s);
+            // K5: out_h = (acc_h - NTT(Conv(y))) (P q_l)^-1 + c_h q_l^-1 for limbs i < level
+            std::vector<KsRow> r5;
+            for (int t = 0; t < items; t++)
+                for (int h = 0; h < 2; h++)
+                    for (int i = 0; i < level; i++) {
+                        KsRow r{};
+                        r.dst = conv + (((size_t)t * 2 + h) * l1 + i) * n;
+                        r.src = yP + ((size_t)t * 2 + h) * SP * n;
+                        r.cst = c.d_fd_hat + 2 * ((size_t)level * SP * (L + 1) + i);
+                        r.cst_stride = 2 * (L + 1);
+                        r.src_cnt = SP;
+                        r.prime = i;
+                        r.galois = 1;
+                        r.item = t;
+                        r.half = h;
+                        r.limb = i;
+                        r5.push_back(r);
+                    }
+            CombineArgs cr{d_items, acc, c.d_fd_minv + 2 * (size_t)level * (L + 1), next,
+                           c.d_resc + 2 * (size_t)level * (L + 1)};
+            const KsRow* d_r5 = c.arena.push_vec(r5, s);
+            ks_transform<false, LD_CONV, ST_COMBINE_RS>(c, d_r5, (int)r5.size(), cr, K_NTT_FWD, 16.0 * r5.size() * n, s);
+            continue;
+        }
         // K4: y_k = INTT(acc_h special limb k) * Phat_k^-1
         std::vector<KsRow> r4;
         for (int t = 0; t < items; t++)
@@ -562,6 +628,18 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
 
 void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
     ks_run(c, all, level, nullptr, s);
+}
+
+void relin_rescale_items(Ctx& c, const std::vector<u64*>& t3, const std::vector<u64*>& out, int level,
+                         cudaStream_t s) {
+    if (t3.size() != out.size()) fail(FHE_ERR_INVALID_ARG, "relin_rescale: input and output counts differ");
+    if (t3.empty()) return;
+    if (level < 1) fail(FHE_ERR_LEVEL_EXHAUSTED, "relinearise-rescale needs level >= 1");
+    const size_t lw = c.ct_words() / 2;
+    std::vector<KsItem> ks;
+    for (size_t i = 0; i < t3.size(); i++)
+        ks.push_back({t3[i] + 2 * lw, c.rlk.d, nullptr, t3[i], t3[i] + lw, out[i], out[i] + lw, 1});
+    ks_run(c, ks, level, nullptr, s, true);
 }
 
 std::vector<int> rotsum_steps(int kp) {

@@ -204,14 +204,6 @@ void rotate_items(Ctx& c, const std::vector<const u64*>& in, const std::vector<u
     keyswitch_items(c, ks, level, s);
 }
 
-// in-place relinearisation of 3-component objects (components 0,1 receive the result)
-void relin_inplace(Ctx& c, const std::vector<u64*>& t3, int level, cudaStream_t s) {
-    const size_t lw = c.ct_words() / 2;
-    std::vector<KsItem> ks;
-    for (u64* x : t3) ks.push_back({x + 2 * lw, c.rlk.d, nullptr, x, x + lw, x, x + lw, 1});
-    keyswitch_items(c, ks, level, s);
-}
-
 void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam, cudaStream_t s) {
     Ctx& c = *p.c;
     if (level < 2) fail(FHE_ERR_LEVEL_EXHAUSTED, "an epoch needs level >= 2");
@@ -267,18 +259,16 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
     for (int g0 = 0; g0 < G; g0 += C) {
         const int cnt = std::min(C, G - g0);
         std::vector<BinItem> tens, pm;
-        std::vector<u64*> t3s;
-        std::vector<UnItem> resc_p;
+        std::vector<u64*> t3s, pout;
         for (int i = 0; i < cnt; i++) {
             const Group& g = p.groups[g0 + i];
             u64* t3 = T3 + (size_t)i * 3 * lw;
             tens.push_back({UD(g.b), Vr(p.group_node[g0 + i]), t3});
             t3s.push_back(t3);
-            resc_p.push_back({t3, Sb + (size_t)i * w});
+            pout.push_back(Sb + (size_t)i * w);
         }
         items_tensor(c, tens, l0 + 1, s);
-        relin_inplace(c, t3s, l0, s);
-        items_rescale(c, resc_p, 2, l0, s);
+        relin_rescale_items(c, t3s, pout, l0, s);
         // rotate-and-sum over kp slots: S (in Tb) from P (in Sb)
         {
             std::vector<u64*> in, out;
@@ -333,21 +323,19 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
     u64* FV = BaseU + (size_t)p.n_ub * w;                  // [n_vb]
     u64* BaseV = FV + (size_t)p.n_vb * w;                  // [n_vb]
     {
-        std::vector<u64*> t3;
-        std::vector<UnItem> rs;
+        std::vector<u64*> t3, outs;
         for (int b = 0; b < p.n_ub; b++) {
             t3.push_back(p.d_TU + (size_t)b * 3 * lw);
-            rs.push_back({p.d_TU + (size_t)b * 3 * lw, AccU + (size_t)b * w});
+            outs.push_back(AccU + (size_t)b * w);
         }
         std::vector<char> used(nodes, 0);
         for (int nd : p.group_node) used[nd] = 1;
         for (int nd = 0; nd < nodes; nd++)
             if (used[nd]) {
                 t3.push_back(p.d_TV + (size_t)nd * 3 * lw);
-                rs.push_back({p.d_TV + (size_t)nd * 3 * lw, p.d_H + (size_t)nd * w});
+                outs.push_back(p.d_H + (size_t)nd * w);
             }
-        relin_inplace(c, t3, l1, s);
-        items_rescale(c, rs, 2, l1, s);
+        relin_rescale_items(c, t3, outs, l1, s);
     }
 
     // 4. back-rotation of the item gradients along the delta trees (deepest first)
@@ -453,17 +441,14 @@ void run_predict(const fhe_mf_plan& p, const u64* U, const u64* V, int level, in
     u64* tmp = c.scratch_u64("pred_tmp", (size_t)p.n_vb * w);
     std::vector<BinItem> tens;
     std::vector<u64*> t3s, prod, res;
-    std::vector<UnItem> rs;
     for (int cb = 0; cb < p.n_vb; cb++) {
         tens.push_back({X, V + (size_t)cb * w, T3 + (size_t)cb * 3 * lw});
         t3s.push_back(T3 + (size_t)cb * 3 * lw);
-        rs.push_back({T3 + (size_t)cb * 3 * lw, tmp + (size_t)cb * w});
         prod.push_back(tmp + (size_t)cb * w);
         res.push_back(out + (size_t)cb * w);
     }
     items_tensor(c, tens, level, s);
-    relin_inplace(c, t3s, level - 1, s);
-    items_rescale(c, rs, 2, level - 1, s);
+    relin_rescale_items(c, t3s, prod, level - 1, s);
     rotsum_items(c, prod, res, p.kp, level - 2, s);
 }
 

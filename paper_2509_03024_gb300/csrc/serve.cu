@@ -96,32 +96,22 @@ void rot_add(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& out, 
     keyswitch_items(c, ks, level, s);
 }
 
-void relin_inplace3(Ctx& c, const std::vector<u64*>& t3, int level, cudaStream_t s) {
-    const size_t lw = c.ct_words() / 2;
-    std::vector<KsItem> ks;
-    for (u64* x : t3) ks.push_back({x + 2 * lw, c.rlk.d, nullptr, x, x + lw, x, x + lw, 1});
-    keyswitch_items(c, ks, level, s);
-}
-
 // Inner products of every (slot, batch) pair listed, at `level`: result in wk.S (level - 1).
 void inner_products(fhe_server& sv, const std::vector<std::pair<Slot*, int>>& pairs, int level, cudaStream_t s) {
     Ctx& c = *sv.c;
     const size_t w = c.ct_words();
     std::vector<BinItem> tens;
     std::vector<u64*> t3;
-    std::vector<UnItem> rs;
     std::vector<u64*> prod, res;
     for (auto& pr : pairs) {
         SlotWork wk = work_of(sv, *pr.first, pr.second);
         tens.push_back({pr.first->UR, sv.V + (size_t)pr.second * w, wk.T3});
         t3.push_back(wk.T3);
-        rs.push_back({wk.T3, wk.tmp});
         prod.push_back(wk.tmp);
         res.push_back(wk.S);
     }
     items_tensor(c, tens, level + 1, s);
-    relin_inplace3(c, t3, level, s);
-    items_rescale(c, rs, 2, level, s);
+    relin_rescale_items(c, t3, prod, level, s);
     rotsum_items(c, prod, res, sv.kp, level - 1, s);
 }
 
@@ -160,15 +150,13 @@ void fold_in_step(fhe_server& sv, const std::vector<Slot*>& group, int level, cu
     }
     items_tensor_acc(c, tg, cb, level, s);
     // G = rescale(relin(T)), block sums, half-fill
-    std::vector<u64*> t3;
-    std::vector<UnItem> rg;
+    std::vector<u64*> t3, gs;
     for (Slot* sl : group) {
         SlotWork wt = work_of(sv, *sl, 0);
         t3.push_back(wt.T);
-        rg.push_back({wt.T, wt.G});
+        gs.push_back(wt.G);
     }
-    relin_inplace3(c, t3, level - 1, s);
-    items_rescale(c, rg, 2, level - 1, s);
+    relin_rescale_items(c, t3, gs, level - 1, s);
     const int l2 = level - 2;
     for (int t = 0; t <= sv.beta; t++) {
         const int step = t < sv.beta ? (1 << t) * sv.w : -sv.kp;

@@ -127,8 +127,8 @@ def test_rescale_relin_mul_bit_exact(preset):
         relin = he.relinearize(he.tensor(he.drop(oa, level), he.drop(ob, level)))
         assert_ct_equal(to_coeff(ctx, out, level)[0], relin, "relinearize")
         ctx.mul_relin_rescale(A, B, out, 1, level)
-        prod = he.rescale(relin)
-        assert_ct_equal(to_coeff(ctx, out, level - 1)[0], prod, "mul_relin_rescale")
+        prod = he.relin_rescale(he.tensor(he.drop(oa, level), he.drop(ob, level)))
+        assert_ct_equal(to_coeff(ctx, out, level - 1)[0], prod, "mul_relin_rescale (fused)")
         dec = ctx.decrypt(out, level - 1)
         assert np.abs(dec - x * y).max() < 1e-4
 

@@ -263,3 +263,45 @@ def test_hoisted_rotate_sum_slots_and_special_cases():
     for t in range(3):
         seq = he.add(seq, he.rotate(seq, 1 << t))
     assert np.abs(he.decrypt(seq) - he.decrypt(S)).max() < 1e-6
+
+
+def test_relin_rescale_without_d2_is_floor_rescale():
+    """With d2 = 0 the fused relinearise-rescale is the floor division of (c0, c1) by q_l, exactly
+    (big-integer CRT over Q_l, then floor(c / q_l) reduced modulo each q_i, i < l)."""
+    prm = ckks.Params(5, (50,) * 4, (60, 60), 50)
+    he = ckks.Ckks(prm)
+    he.keygen(31)
+    rng = np.random.default_rng(9)
+    lv = prm.top
+    c = np.stack([np.stack([rng.integers(0, q, prm.n, dtype=np.uint64) for q in prm.q]) for _ in range(2)])
+    t = ckks.Ciphertext(np.concatenate([c, np.zeros((1, lv + 1, prm.n), dtype=np.uint64)]), lv)
+    got = he.relin_rescale(t)
+    Q = math.prod(prm.q[: lv + 1])
+    for h in range(2):
+        for k in range(prm.n):
+            x = 0
+            for i, q in enumerate(prm.q[: lv + 1]):
+                qi_hat = Q // q
+                x += int(c[h][i][k]) * qi_hat * pow(qi_hat, -1, q)
+            x %= Q
+            f = x // prm.q[lv]
+            assert [int(got.c[h][i][k]) for i in range(lv)] == [f % q for q in prm.q[:lv]]
+
+
+def test_relin_rescale_matches_two_step_up_to_conversion_error():
+    """decrypt(relin_rescale(a (x) b)) differs from decrypt(rescale(relinearize(a (x) b))) by
+    e0 + e1 s with |e0|, |e1| <= alpha + 1 per coefficient; slots hold the product."""
+    for prm in (ckks.Params(6, (50,) * 4, (60, 60), 50), ckks.Params(6, (60, 40, 40), (60,), 40)):
+        he = ckks.Ckks(prm)
+        he.keygen(37)
+        rng = np.random.default_rng(10)
+        x, y = rng.normal(size=prm.slots), rng.normal(size=prm.slots)
+        cx, cy = he.encrypt(x, prm.top, 1), he.encrypt(y, prm.top, 2)
+        for lv in sorted({prm.top, 1}):
+            t = he.tensor(he.drop(cx, lv), he.drop(cy, lv))
+            fused = he.relin_rescale(t)
+            two = he.rescale(he.relinearize(t))
+            assert fused.level == two.level == lv - 1
+            d = [a - b for a, b in zip(he.decrypt_coeffs(fused), he.decrypt_coeffs(two))]
+            assert max(abs(v) for v in d) <= (prm.alpha + 1) * (prm.n + 1)
+            assert np.abs(he.decrypt(fused) - x * y).max() < 1e-5
