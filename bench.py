@@ -249,7 +249,13 @@ def run_served(args, dev):
         return len(reqs), batched, one
 
     n, batched, one = at_rate(args.served_rate)
-    out = {"workload": SERVED, "requests": n, "arrival_rate_req_s": args.served_rate,
+    from paper_2509_03024_gb300 import comm
+    B = plan.B
+    reqs = W.served_requests(args.served_requests, args.served_rate, m, k, SEED + 6)
+    per_req = [comm.served_request(ctx.n, ctx.top, n_vb, len(set((r.items // B).tolist())), steps) for r in reqs]
+    out_comm = {"mean_up_bytes": sum(x["up_bytes"] for x in per_req) / len(per_req),
+                "down_bytes": per_req[0]["down_bytes"], "down_level": per_req[0]["out_level"]}
+    out = {"workload": SERVED, "requests": n, "arrival_rate_req_s": args.served_rate, "communication": out_comm,
            "value": batched["ratings_per_s"], "unit": UNIT, "p50_ms": batched["p50_ms"],
            "p99_ms": batched["p99_ms"], "continuous_batching": batched, "one_by_one": one,
            "speedup_vs_one_by_one": batched["ratings_per_s"] / one["ratings_per_s"]}
@@ -434,6 +440,12 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
            "accuracy": {"max_abs_vs_fp64": err, "rmse_gap_test": rmse_gap},
            "kernels": {k: {"launches": v[0], "device_ms": round(v[1], 3), "alg_gb": round(v[2] / 1e9, 3)}
                        for k, v in stats.items() if v[0]}}
+    from paper_2509_03024_gb300 import comm
+    out["communication"] = {
+        "training_10_epochs": comm.mf_training(ctx.n, ctx.top, ctx.alpha, len(ctx.mf_rotation_steps(K_RANK)),
+                                               int(plan.info.n_bins), plan.n_ub, plan.n_vb, epochs=10),
+        "note": "bytes between the parties (key holder, data owners, recommender) for the paper-scale workload; "
+                "the epochs themselves move nothing off the GPU"}
     if not args.no_served:
         out["served"] = run_served(args, torch_device_of(ctx))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

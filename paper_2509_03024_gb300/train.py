@@ -1,6 +1,7 @@
 """End-to-end encrypted MF training on one GPU (Alg. 1 / Alg. 2 of the paper).
 
   python -m paper_2509_03024_gb300.train --workload paper --epochs 10 [--lr 0.005] [--damped]
+                                         [--checkpoint ck.npz] [--resume ck.npz]
 
 Encrypts the initial factors, runs `epochs` encrypted SGD epochs (each uses two
 levels; when fewer than two are left the key holder refreshes U and V back to
@@ -18,21 +19,46 @@ import numpy as np
 REFRESH_NONCE_BASE = 1 << 42
 
 
+def save_checkpoint(path: str, ctx, UD, VD, level: int, epoch: int, refreshes: int) -> None:
+    """Write the encrypted factors (raw residues of every limb slot), their level, the number of
+    epochs done and of refreshes so far, and the modulus chain they belong to."""
+    np.savez(path, UD=UD.cpu().numpy(), VD=VD.cpu().numpy(), level=level, epoch=epoch, refreshes=refreshes,
+             log_n=ctx.log_n, primes=np.asarray(ctx.primes, dtype=np.uint64))
+
+
+def load_checkpoint(path: str, ctx) -> dict:
+    """Read a checkpoint written by save_checkpoint back onto the context's device; the ring and
+    the primes must be the context's."""
+    import torch
+    z = np.load(path)
+    if int(z["log_n"]) != ctx.log_n or list(z["primes"]) != list(np.asarray(ctx.primes, dtype=np.uint64)):
+        raise ValueError("checkpoint belongs to another parameter set")
+    dev = f"cuda:{ctx.device}"
+    return {"UD": torch.from_numpy(z["UD"]).to(dev), "VD": torch.from_numpy(z["VD"]).to(dev),
+            "level": int(z["level"]), "epoch": int(z["epoch"]), "refreshes": int(z["refreshes"])}
+
+
 def run(ctx, plan, U0, V0, epochs: int, lr: float, lam: float, damped: bool = False, stream=None,
-        on_epoch=None):
+        on_epoch=None, state=None):
     """Encrypted training loop; returns (UD, VD, level, per-epoch seconds, refresh count).
 
     Refresh r (r = 1, 2, ...) uses nonces REFRESH_NONCE_BASE + r * (n_ub + n_vb) + batch index
     (user batches first, then item batches). A refresh raises capi.FheError when a plaintext
-    coefficient has left the int64 range, i.e. when the factors have diverged."""
+    coefficient has left the int64 range, i.e. when the factors have diverged. With `state` (a
+    load_checkpoint result) training resumes from it (U0, V0 unused) and runs epochs
+    state["epoch"] .. epochs - 1, giving the same ciphertexts as an uninterrupted run."""
     import torch
-    UD, VD = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
-    plan.encrypt_factors(0, U0, UD)
-    plan.encrypt_factors(1, V0, VD)
-    level = ctx.top
-    times, refreshes = [], 0
+    if state is None:
+        UD, VD = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
+        plan.encrypt_factors(0, U0, UD)
+        plan.encrypt_factors(1, V0, VD)
+        level, first, refreshes = ctx.top, 0, 0
+    else:
+        UD, VD = state["UD"], state["VD"]
+        level, first, refreshes = state["level"], state["epoch"], state["refreshes"]
+    times = []
     per = plan.n_ub + plan.n_vb
-    for t in range(epochs):
+    for t in range(first, epochs):
         if level < 2:
             refreshes += 1
             base = REFRESH_NONCE_BASE + refreshes * per
@@ -47,7 +73,7 @@ def run(ctx, plan, U0, V0, epochs: int, lr: float, lam: float, damped: bool = Fa
         times.append(time.perf_counter() - t0)
         level -= 2
         if on_epoch:
-            on_epoch(t, UD, VD, level)
+            on_epoch(t, UD, VD, level, refreshes)
     return UD, VD, level, times, refreshes
 
 
@@ -82,6 +108,8 @@ def cli():
     ap.add_argument("--lam", type=float, default=0.02)
     ap.add_argument("--damped", action="store_true")
     ap.add_argument("--seed", type=int, default=20250903)
+    ap.add_argument("--checkpoint", default=None, help="write the encrypted state here after every epoch")
+    ap.add_argument("--resume", default=None, help="continue from a checkpoint written by --checkpoint")
     args = ap.parse_args()
     build.build()
     if args.workload == "tiny":
@@ -99,8 +127,14 @@ def cli():
     trow, tcol, tval = test.triples()
     curve = []
     state = {"U": U.copy(), "V": V.copy()}
+    resume = load_checkpoint(args.resume, ctx) if args.resume else None
+    for t in range(resume["epoch"] if resume else 0):   # the float64 reference up to the resume point
+        a = lr / (1.0 + 0.1 * t) if args.damped else lr
+        state["U"], state["V"] = _fp64_epochs(state["U"], state["V"], rows, cols, vals, 1, a, args.lam, False)
 
-    def on_epoch(t, UD, VD, level):
+    def on_epoch(t, UD, VD, level, refreshes):
+        if args.checkpoint:
+            save_checkpoint(args.checkpoint, ctx, UD, VD, level, t + 1, refreshes)
         a = lr / (1.0 + 0.1 * t) if args.damped else lr
         state["U"], state["V"] = _fp64_epochs(state["U"], state["V"], rows, cols, vals, 1, a, args.lam, False)
         Ud = plan.decrypt_factors(0, UD, level, train.n)
@@ -119,7 +153,7 @@ def cli():
     times, refreshes = [], 0
     try:
         UD, VD, level, times, refreshes = run(ctx, plan, U, V, args.epochs, lr, args.lam, args.damped,
-                                              on_epoch=on_epoch)
+                                              on_epoch=on_epoch, state=resume)
     except capi.FheError as e:
         diverged = {"after_epoch": len(curve), "error": str(e)}
     epoch_s = [c for c in times] if times else None

@@ -209,3 +209,25 @@ def test_refresh_then_epoch_bit_exact():
     for _ in range(3):
         Ur, Vr = mf.mf_epoch_fp64(Ur, Vr, rows, cols, vals, lr, lam)
     assert np.abs(plan.decrypt_factors(0, UD, level, csr.n) - Ur).max() < 1e-3
+
+
+def test_checkpoint_resume_bit_identical(tmp_path):
+    """Three epochs straight (one refresh on the way) equal two epochs, a checkpoint written and read
+    back, and the third epoch."""
+    from paper_2509_03024_gb300 import train as T
+    csr, U, V = _small_case(seed=12, n=45, m=35, density=0.07, k=3)
+    ctx, plan, he, oplan, emf, UD0, VD0, oUD, oVD = _setup("t11a2", csr, 3, U, V)
+    lr, lam = 0.02, 0.01
+    UDa, VDa, la, _, ra = T.run(ctx, plan, U, V, 3, lr, lam)
+    path = str(tmp_path / "ck.npz")
+
+    def save(t, UD, VD, level, refreshes):
+        if t == 1:
+            T.save_checkpoint(path, ctx, UD, VD, level, t + 1, refreshes)
+
+    T.run(ctx, plan, U, V, 2, lr, lam, on_epoch=save)
+    st = T.load_checkpoint(path, ctx)
+    assert st["epoch"] == 2
+    UDb, VDb, lb, _, rb = T.run(ctx, plan, U, V, 3, lr, lam, state=st)
+    assert (la, ra) == (lb, rb) == (ctx.top - 2, 1)
+    assert torch.equal(UDa, UDb) and torch.equal(VDa, VDb)
