@@ -108,6 +108,7 @@ def cli():
     ap.add_argument("--lam", type=float, default=0.02)
     ap.add_argument("--damped", action="store_true")
     ap.add_argument("--seed", type=int, default=20250903)
+    ap.add_argument("--preset", default=None, help="CKKS parameter preset (default: the workload's)")
     ap.add_argument("--checkpoint", default=None, help="write the encrypted state here after every epoch")
     ap.add_argument("--resume", default=None, help="continue from a checkpoint written by --checkpoint")
     args = ap.parse_args()
@@ -120,6 +121,8 @@ def cli():
         train, test, U, V = W.paper_workload(seed=2)
         preset, k, lr = W.PRESETS["paper"], 10, 0.005
     lr = args.lr if args.lr is not None else lr
+    if args.preset:
+        preset = W.PRESETS[args.preset]
     ctx = capi.Context.from_preset(preset)
     ctx.keygen(args.seed, ctx.mf_rotation_steps(k))
     plan = capi.MfPlan(ctx, train.n, train.m, k, train.row_ptr, train.col_idx, train.vals)
@@ -157,7 +160,8 @@ def cli():
     except capi.FheError as e:
         diverged = {"after_epoch": len(curve), "error": str(e)}
     epoch_s = [c for c in times] if times else None
-    out = {"workload": args.workload, "epochs": args.epochs, "lr": lr, "lambda": args.lam, "damped": args.damped,
+    out = {"workload": args.workload, "preset": preset.name, "log_scale": preset.log_scale, "epochs": args.epochs,
+           "lr": lr, "lambda": args.lam, "damped": args.damped,
            "refreshes": refreshes, "epoch_s": epoch_s, "diverged": diverged, "curve": curve}
     if times:
         out["ratings_per_s"] = float(rows.size * len(times) / sum(times))

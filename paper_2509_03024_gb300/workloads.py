@@ -44,6 +44,10 @@ PRESETS = {
     "batched": CkksPreset("batched", 16, (50,) * 12, (60, 60, 60), 50),
     "served": CkksPreset("served", 16, (50,) * 13, (60, 60, 60), 50),
     "large": CkksPreset("large", 16, (50,) * 20, (60, 60, 60), 50),
+    # the paper's ring (N = 8192) at its two fractional precisions (22 and 32 bits): one epoch
+    # (two levels) per refresh, 128-bit secure chains (log QP = 144 and 164)
+    "sweep22": CkksPreset("sweep22", 13, (40, 22, 22), (60,), 22),
+    "sweep32": CkksPreset("sweep32", 13, (40, 32, 32), (60,), 32),
     # test-only small rings
     "t10": CkksPreset("t10", 10, (60, 40, 40), (60,), 40),
     "t11a2": CkksPreset("t11a2", 11, (50,) * 5, (60, 60), 50),
