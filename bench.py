@@ -146,7 +146,7 @@ def oracle_sample(train, U, V, groups_sampled: int = 1):
     emf.R = [None] * len(plan.bin_batch)
     for t in pick:
         bt = plan.bin_of[t]
-        emf.R[bt] = he.encrypt(mf.bin_slots(bt, plan), top, mf.R_NONCE_BASE + bt)
+        emf.R[bt] = he.encrypt_seeded(he.enc.encode(mf.bin_slots(bt, plan)), top - 1, mf.R_NONCE_BASE + bt)
     UD = {g.b: None for g in (plan.groups[t] for t in pick)}
     for b in UD:
         UD[b] = he.encrypt(mf.pack_factors(U, plan, b), top, mf.U_NONCE_BASE + b)

@@ -255,8 +255,12 @@ int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t ca
  * stored in bins (the paper packs many ratings per ciphertext, Sec. III-C):
  * within each user batch, each group goes to the first bin (in creation order)
  * that holds none of its users, else to a new bin; bins are numbered batch by
- * batch. Each bin is encrypted at the top level (nonce 2^40 + bin) and kept on
- * the device by the plan. Duplicate (i, j) pairs are rejected. */
+ * batch. The key holder encrypts each bin at level L - 1 (the highest level an
+ * epoch reads it at) with a regenerable c1: c1 = a, the uniform polynomial drawn
+ * coefficient by coefficient from the seed's stream (purpose 9, object
+ * 2^40 + bin, one stream per limb), c0 = -a s + m + e (e: purpose 10, same
+ * object). The plan keeps c0 only and regenerates c1 when an epoch reads the
+ * bin. Duplicate (i, j) pairs are rejected. */
 int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* row_ptr,
                  const int32_t* col_idx, const double* vals, fhe_mf_plan** out);
 void fhe_mf_plan_destroy(fhe_mf_plan* plan);
@@ -271,6 +275,12 @@ int fhe_mf_plan_get_bins(const fhe_mf_plan* plan, int32_t* bin_of_group);
 /* Tuning: process at most `groups_per_chunk` groups per launch set of the
  * epoch (default: as many as fit a 6 GiB work area). Results do not depend on it. */
 int fhe_mf_plan_set_chunk(fhe_mf_plan* plan, int32_t groups_per_chunk);
+/* Memory: the epoch runs the item batches in consecutive waves whose delta-tree
+ * workspace (per node one rotated item ciphertext, one gradient ciphertext and one
+ * three-component accumulator at the top level) fits `bytes` (default 72 GiB; a wave
+ * holds at least one item batch). The user-side accumulators span all waves. Results
+ * do not depend on it. */
+int fhe_mf_plan_set_wave_budget(fhe_mf_plan* plan, uint64_t bytes);
 
 /* Encrypt factor rows (host double [count][k], users if which = 0, items if 1)
  * into the plan's batch layout: n_user_batches (or n_item_batches)

@@ -44,6 +44,8 @@ MIX2 = 0x94D049BB133111EB
 
 # sampling purposes (the first field of every stream key)
 P_SECRET, P_PK_A, P_PK_E, P_EVK_A, P_EVK_E, P_ENC_V, P_ENC_E0, P_ENC_E1 = 1, 2, 3, 4, 5, 6, 7, 8
+P_SEEDED_A, P_SEEDED_E = 9, 10   # key-holder encryption with a regenerable c1 (object = the ciphertext's id)
+SEEDED_TRIES = 16
 RELIN_OBJECT = 0
 
 
@@ -174,6 +176,21 @@ def sample_uniform(h: int, n: int, q: int) -> np.ndarray:
     """n residues uniform mod q: accept x < floor(2^64/q)*q, value x mod q."""
     bound = ((1 << 64) // q) * q
     return _rejection(h, n, bound) % np.uint64(q)
+
+
+def sample_uniform_indexed(h: int, n: int, q: int, tries: int = SEEDED_TRIES) -> np.ndarray:
+    """n residues uniform mod q, coefficient k drawn on its own: the first of the stream outputs
+    x_{jn + k}, j = 0..tries-1, below floor(2^64/q)*q, reduced mod q (x_{(tries-1)n + k} mod q if
+    none is). Any coefficient can thus be regenerated without the others."""
+    bound = np.uint64(((1 << 64) // q) * q)
+    out = np.zeros(n, dtype=np.uint64)
+    done = np.zeros(n, dtype=bool)
+    for j in range(tries):
+        x = draws(h, j * n, n)
+        take = ~done & ((x < bound) | (j == tries - 1))
+        out[take] = x[take] % np.uint64(q)
+        done |= take
+    return out
 
 
 def sample_ternary(h: int, n: int) -> np.ndarray:
@@ -380,6 +397,21 @@ class Ckks:
         c0 = self._add(self._add(self._mul(v, self.pk[0][: level + 1], primes), e0, primes), mm, primes)
         c1 = self._add(self._mul(v, self.pk[1][: level + 1], primes), e1, primes)
         return Ciphertext(np.stack([c0, c1]), level)
+
+    def encrypt_seeded(self, m: np.ndarray, level: int, obj: int) -> Ciphertext:
+        """Key-holder (symmetric) encryption whose c1 is regenerable from (seed, obj):
+        c1 = a with a_i = sample_uniform_indexed(stream_key(seed, P_SEEDED_A, obj, 0, i), N, q_i)
+        (coefficient form), e from stream_key(seed, P_SEEDED_E, obj), c0 = -a s + m + e mod Q_level.
+        A holder of the seed stores c0 only."""
+        prm = self.prm
+        n = prm.n
+        primes = prm.q[: level + 1]
+        a = np.stack([sample_uniform_indexed(stream_key(self.seed, P_SEEDED_A, obj, 0, i), n, q)
+                      for i, q in enumerate(primes)])
+        e = to_rns(sample_gaussian(stream_key(self.seed, P_SEEDED_E, obj), n, prm.sigma), primes)
+        s_q = to_rns(self.s, primes)
+        c0 = self._add(self._add(self._neg(self._mul(a, s_q, primes), primes), e, primes), to_rns(m, primes), primes)
+        return Ciphertext(np.stack([c0, a]), level)
 
     def encrypt(self, z, level: int, nonce: int) -> Ciphertext:
         return self.encrypt_coeffs(self.enc.encode(z), level, nonce)

@@ -328,10 +328,12 @@ class EncryptedMF:
         self.R: List[Ciphertext] = []
 
     def encrypt_ratings(self) -> None:
-        """The CSP's EncryptCsrMatrix step (Alg. 1): one ciphertext per rating bin at the top
-        level, nonce R_NONCE_BASE + bin."""
-        top = self.he.prm.top
-        self.R = [self.he.encrypt(bin_slots(t, self.plan), top, R_NONCE_BASE + t)
+        """The CSP's EncryptCsrMatrix step (Alg. 1): one ciphertext per rating bin, encrypted by the
+        key holder with a regenerable c1 (object R_NONCE_BASE + bin) at level top - 1, the highest
+        level at which an epoch reads it."""
+        he = self.he
+        lv = he.prm.top - 1
+        self.R = [he.encrypt_seeded(he.enc.encode(bin_slots(t, self.plan)), lv, R_NONCE_BASE + t)
                   for t in range(len(self.plan.bin_batch))]
 
     def encrypt_factors(self, U: np.ndarray, V: np.ndarray):

@@ -30,7 +30,7 @@ EXPORTS = [
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
     "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
-    "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_get_bins", "fhe_mf_plan_set_chunk", "fhe_mf_encrypt_factors",
+    "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_get_bins", "fhe_mf_plan_set_chunk", "fhe_mf_plan_set_wave_budget", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
     "fhe_serve_poll", "fhe_serve_encrypt_request", "fhe_serve_take",
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
             "fhe_mf_plan_get_info": [vp, ctypes.POINTER(PlanInfo)],
             "fhe_mf_plan_get_groups": [vp, vp, vp, vp, vp],
             "fhe_mf_plan_get_bins": [vp, vp],
+            "fhe_mf_plan_set_wave_budget": [vp, ctypes.c_uint64],
             "fhe_mf_plan_set_chunk": [vp, i32],
             "fhe_mf_encrypt_factors": [vp, vp, i32, vp, i32, vp, vp],
             "fhe_mf_decrypt_factors": [vp, vp, i32, vp, i32, vp, i32, vp],
@@ -371,6 +372,10 @@ class MfPlan:
         out = np.zeros(max(int(self.info.n_groups), 1), dtype=np.int32)
         self.ctx._check(lib().fhe_mf_plan_get_bins(self.h, out.ctypes.data))
         return out[: int(self.info.n_groups)]
+
+    def set_wave_budget(self, nbytes: int):
+        """Node-workspace budget per wave of item batches (results do not depend on it)."""
+        self.ctx._check(lib().fhe_mf_plan_set_wave_budget(self.h, nbytes))
 
     def set_chunk(self, groups_per_chunk: int):
         self.ctx._check(lib().fhe_mf_plan_set_chunk(self.h, groups_per_chunk))

@@ -394,6 +394,23 @@ void encode_many_device(Ctx& c, const std::vector<int>& idx, const std::vector<d
                         const std::vector<int>& offsets, i64* out_dev, cudaStream_t s);
 void encrypt_coeffs_device(Ctx& c, const i64* m_dev, size_t m_stride, int count, int level,
                            const std::vector<u64>& nonces, u64* ct, cudaStream_t s);
+
+// Key-holder encryption with a regenerable c1 (stream purposes 9 and 10): c1 = a, the uniform
+// polynomial drawn coefficient by coefficient from stream_key(seed, 9, obj, 0, limb) (up to
+// kSeededTries draws each), c0 = -a s + m + e with e from stream_key(seed, 10, obj, 0, 0).
+constexpr int kSeededTries = 16;
+struct SeedRow {
+    u64 h;       // stream key of the row
+    u64* dst;    // N residues (coefficient form)
+    int prime;   // prime index of the row
+    int pad;
+};
+u64 seeded_key(const Ctx& c, u64 obj, int limb);
+// Fill each row with its uniform coefficients (coefficient form).
+void seeded_uniform_device(Ctx& c, const std::vector<SeedRow>& rows, cudaStream_t s);
+// c0 only, evaluation domain, compact [count][level+1][N] at c0_out.
+void encrypt_seeded_device(Ctx& c, const i64* m_dev, size_t m_stride, int count, int level,
+                           const std::vector<u64>& objs, u64* c0_out, cudaStream_t s);
 // plaintext materialisation: int64 coefficients -> evaluation domain limbs [0, limbs)
 void materialize_plain(Ctx& c, const i64* m_dev, size_t m_stride, int count, int limbs, u64* out,
                        size_t out_stride, cudaStream_t s);

@@ -151,7 +151,10 @@ static Prime make_prime(u64 q) {
 // ============================================================================ sampling (SplitMix64 streams)
 
 static constexpr u64 kGamma = 0x9E3779B97F4A7C15ULL;
-enum Purpose : u64 { kSecret = 1, kPkA = 2, kPkE = 3, kEvkA = 4, kEvkE = 5, kEncV = 6, kEncE0 = 7, kEncE1 = 8 };
+enum Purpose : u64 {
+    kSecret = 1, kPkA = 2, kPkE = 3, kEvkA = 4, kEvkE = 5, kEncV = 6, kEncE0 = 7, kEncE1 = 8,
+    kSeededA = 9, kSeededE = 10  // key-holder encryption with a regenerable c1 (object = ciphertext id)
+};
 
 static inline u64 mix64(u64 z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -496,6 +499,44 @@ __global__ void enc_combine_kernel(u64* ct, size_t ct_stride, size_t part_stride
     }
 }
 
+__device__ __forceinline__ u64 mix64_dev(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Row r: dst[k] = the first of the stream outputs x_{jN + k} = mix64(h + (jN + k + 1) gamma),
+// j < kSeededTries, below floor(2^64/q) q, reduced mod q (the last one if none is).
+__global__ void seeded_uniform_kernel(const SeedRow* __restrict__ rows, int n_rows, int log_n,
+                                      const Prime* __restrict__ pr) {
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = (size_t)n_rows << log_n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const SeedRow r = rows[e >> log_n];
+        const size_t k = e & (n - 1);
+        const Prime P = pr[r.prime];
+        const u64 bound = (u64)0 - ((u64)0 - P.q * P.one_s);  // 2^64 - (2^64 mod q)
+        u64 x = 0;
+        for (int j = 0; j < kSeededTries; j++) {
+            x = mix64_dev(r.h + ((u64)j * n + k + 1) * 0x9E3779B97F4A7C15ULL);
+            if (x < bound) break;
+        }
+        const u64 t = x - __umul64hi(x, P.one_s) * P.q;  // in [0, 2q)
+        r.dst[k] = t >= P.q ? t - P.q : t;
+    }
+}
+
+// c0[t][i] = me[t][i] - a[t][i] * s[i] (evaluation domain), compact [count][l1][N] buffers.
+__global__ void seeded_c0_kernel(u64* out, const u64* __restrict__ me, const u64* __restrict__ a,
+                                 const u64* __restrict__ sk, size_t total, int l1, int log_n, const Prime* __restrict__ pr) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = e >> log_n, k = e & (((size_t)1 << log_n) - 1);
+        const int i = (int)(row % l1);
+        const Prime P = pr[i];
+        out[e] = sub_mod(me[e], mul_mod(a[e], sk[((size_t)i << log_n) + k], P), P.q);
+    }
+}
+
 __global__ void add_compact_kernel(u64* out, const u64* __restrict__ a, size_t total, int l1, int log_n,
                                    const Prime* __restrict__ pr) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
@@ -676,6 +717,59 @@ void materialize_plain(Ctx& c, const i64* m_dev, size_t m_stride, int count, int
                        size_t out_stride, cudaStream_t s) {
     k_int_to_rns(c, out, out_stride, m_dev, m_stride, count, limbs, s);
     ntt_forward(c, poly_batch(out, out_stride, 0, count, 1, 0, limbs), s);
+}
+
+u64 seeded_key(const Ctx& c, u64 obj, int limb) { return stream_key(c.seed, kSeededA, obj, 0, (u64)limb); }
+
+void seeded_uniform_device(Ctx& c, const std::vector<SeedRow>& rows, cudaStream_t s) {
+    if (rows.empty()) return;
+    const SeedRow* d = c.arena.push_vec(rows, s);
+    LaunchScope _ls(c.prof, K_ELEMENTWISE, 8.0 * rows.size() * c.n, s);
+    seeded_uniform_kernel<<<blocks_for(rows.size() * (size_t)c.n), kT, 0, s>>>(d, (int)rows.size(), c.log_n,
+                                                                                c.d_primes);
+    CK(cudaGetLastError());
+}
+
+void encrypt_seeded_device(Ctx& c, const i64* m_dev, size_t m_stride, int count, int level,
+                           const std::vector<u64>& objs, u64* c0_out, cudaStream_t s) {
+    if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
+    if (level < 0 || level > c.L) fail(FHE_ERR_INVALID_ARG, "level out of range");
+    const int n = c.n, l1 = level + 1;
+    const GaussTable T = gauss_table(c.sigma);
+    const int chunk = 32;
+    std::vector<int8_t> host((size_t)chunk * n);
+    for (int t0 = 0; t0 < count; t0 += chunk) {
+        const int cnt = std::min(chunk, count - t0);
+        for (int t = 0; t < cnt; t++)
+            sample_gaussian(stream_key(c.seed, kSeededE, objs[t0 + t], 0, 0), T, host.data() + (size_t)t * n, n);
+        int8_t* d_e = (int8_t*)c.scratch_bytes("senc_e", (size_t)chunk * n);
+        u64* me = c.scratch_u64("senc_me", (size_t)chunk * l1 * n);
+        u64* ee = c.scratch_u64("senc_ee", (size_t)chunk * l1 * n);
+        u64* a = c.scratch_u64("senc_a", (size_t)chunk * l1 * n);
+        CK(cudaMemcpyAsync(d_e, host.data(), (size_t)cnt * n, cudaMemcpyHostToDevice, s));
+        const size_t st = (size_t)l1 * n;
+        k_int_to_rns(c, me, st, m_dev + (size_t)t0 * m_stride, m_stride, cnt, l1, s);
+        k_int8_to_rns(c, ee, st, d_e, (size_t)n, cnt, l1, 1 << 30, 0, s);
+        {
+            LaunchScope _ls(c.prof, K_ELEMENTWISE, 24.0 * cnt * st, s);
+            add_compact_kernel<<<blocks_for((size_t)cnt * st), kT, 0, s>>>(me, ee, (size_t)cnt * st, l1, c.log_n,
+                                                                           c.d_primes);
+            CK(cudaGetLastError());
+        }
+        std::vector<SeedRow> rows;
+        for (int t = 0; t < cnt; t++)
+            for (int i = 0; i < l1; i++) rows.push_back({seeded_key(c, objs[t0 + t], i), a + ((size_t)t * l1 + i) * n, i, 0});
+        seeded_uniform_device(c, rows, s);
+        ntt_forward(c, poly_batch(me, st, 0, cnt, 1, 0, l1), s);
+        ntt_forward(c, poly_batch(a, st, 0, cnt, 1, 0, l1), s);
+        {
+            LaunchScope _ls(c.prof, K_ELEMENTWISE, 32.0 * cnt * st, s);
+            seeded_c0_kernel<<<blocks_for((size_t)cnt * st), kT, 0, s>>>(c0_out + (size_t)t0 * st, me, a, c.d_sk,
+                                                                         (size_t)cnt * st, l1, c.log_n, c.d_primes);
+            CK(cudaGetLastError());
+        }
+        CK(cudaStreamSynchronize(s));  // `host` is refilled by the next chunk
+    }
 }
 
 void encrypt_coeffs_device(Ctx& c, const i64* m_dev, size_t m_stride, int count, int level,

@@ -66,17 +66,23 @@ struct fhe_mf_plan {
     std::vector<int> nnz_u, nnz_v;
     std::vector<int> bin_of;                // rating bin of each group
     std::vector<int> bin_b;                 // user batch of each bin
-    u64* d_R = nullptr;                     // [bins] rating ciphertexts, top level
+    std::vector<int> order;                 // groups in (c, b, delta) order: the execution order
+    std::vector<int> c_first_pos;           // [n_vb + 1] first position in `order` of each item batch
+    std::vector<int> c_first_node;          // [n_vb + 1] first node of each item batch (nodes are by c)
+    std::vector<int> wave_c;                // item-batch boundaries of the node-workspace waves
+    int wave_nodes = 0;                     // nodes of the largest wave
+    size_t wave_budget = (size_t)72 << 30;  // node workspace budget per wave (bytes)
+    u64* d_R = nullptr;                     // [bins][L][N] c0 of the rating bins at level L - 1 (c1 is regenerated)
     // plaintext caches (learning-rate dependent)
     bool have_plain = false;
     double lr_c = 0, lam_c = 0;
-    i64* d_mask = nullptr;                  // [G][N]
+    i64* d_mask = nullptr;                  // [G][N], in execution order
     i64* d_reg = nullptr;                   // [n_ub + n_vb][N]
     // epoch workspace
-    u64* d_Vr = nullptr;                    // [nodes] ciphertexts
-    u64* d_TV = nullptr;                    // [nodes] 3-component
+    u64* d_Vr = nullptr;                    // [wave nodes] ciphertexts
+    u64* d_TV = nullptr;                    // [wave nodes] 3-component
     u64* d_TU = nullptr;                    // [n_ub] 3-component
-    u64* d_H = nullptr;                     // [nodes]
+    u64* d_H = nullptr;                     // [wave nodes]
     u64* d_chunk = nullptr;                 // chunk buffers
     u64* d_fin = nullptr;                   // [n_ub + n_vb] x 3 ciphertexts for the final step
     int chunk = 0;        // groups per launch set
@@ -115,9 +121,9 @@ void ensure_plaintexts(fhe_mf_plan& p, double lr, double lam, cudaStream_t s) {
         idx.clear();
         val.clear();
         off.assign(1, 0);
-        for (int g = g0; g < g1; g++) {
+        for (int pos = g0; pos < g1; pos++) {
             if (lr != 0.0)
-                for (int a : p.groups[g].a)
+                for (int a : p.groups[p.order[pos]].a)
                     for (int x = 0; x < p.k; x++) {
                         idx.push_back(a * p.w + x);
                         val.push_back(lr);
@@ -152,10 +158,29 @@ void ensure_plaintexts(fhe_mf_plan& p, double lr, double lam, cudaStream_t s) {
     p.lam_c = lam;
 }
 
+// Item batches in consecutive waves whose delta-tree node workspace (Vr, H, TV) fits wave_budget
+// (a wave holds at least one item batch).
+void plan_waves(fhe_mf_plan& p) {
+    const size_t node_bytes = (size_t)7 * (p.c->ct_words() / 2) * sizeof(u64);  // Vr, H (2 lw each), TV (3 lw)
+    p.wave_c.assign(1, 0);
+    p.wave_nodes = 0;
+    int nodes_in = 0;
+    for (int cb = 0; cb < p.n_vb; cb++) {
+        const int nc = p.c_first_node[cb + 1] - p.c_first_node[cb];
+        if (nodes_in > 0 && (size_t)(nodes_in + nc) * node_bytes > p.wave_budget) {
+            p.wave_c.push_back(cb);
+            nodes_in = 0;
+        }
+        nodes_in += nc;
+        p.wave_nodes = std::max(p.wave_nodes, nodes_in);
+    }
+    p.wave_c.push_back(p.n_vb);
+}
+
 void ensure_workspace(fhe_mf_plan& p) {
     Ctx& c = *p.c;
     const size_t w = c.ct_words(), lw = w / 2;
-    const size_t nodes = p.node_c.size();
+    const size_t nodes = (size_t)p.wave_nodes;
     if (!p.d_Vr) {
         p.d_Vr = plan_alloc<u64>(p, nodes * w);
         p.d_TV = plan_alloc<u64>(p, nodes * 3 * lw);
@@ -215,198 +240,231 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
     c.arena.reset(s);
     const size_t w = c.ct_words(), lw = w / 2;
     const int l0 = level, l1 = level - 1, l2 = level - 2;
-    const int nodes = (int)p.node_c.size();
-    CK(cudaMemsetAsync(p.d_TV, 0, sizeof(u64) * nodes * 3 * lw, s));
     CK(cudaMemsetAsync(p.d_TU, 0, sizeof(u64) * p.n_ub * 3 * lw, s));
-    CK(cudaMemsetAsync(p.d_H, 0, sizeof(u64) * nodes * w, s));
-    auto Vr = [&](int nd) { return p.d_Vr + (size_t)nd * w; };
     auto UD = [&](int b) { return U + (size_t)b * w; };
     auto VD = [&](int cb) { return V + (size_t)cb * w; };
-
-    // 1. delta trees of the item batches, one launch set per popcount level
-    {
-        std::vector<UnItem> roots;
-        for (int cb = 0; cb < p.n_vb; cb++) roots.push_back({VD(cb), Vr(p.node(cb, 0))});
-        items_copy(c, roots, 2, l0 + 1, s);
-        int maxpop = 0;
-        for (int d : p.node_delta) maxpop = std::max(maxpop, popc(d));
-        for (int pc = 1; pc <= maxpop; pc++) {
-            std::vector<const u64*> in;
-            std::vector<u64*> out;
-            std::vector<int> steps;
-            for (int nd = 0; nd < nodes; nd++) {
-                int d = p.node_delta[nd];
-                if (popc(d) != pc) continue;
-                int hb = 1 << hbit(d);
-                in.push_back(Vr(p.node(p.node_c[nd], d - hb)));
-                out.push_back(Vr(nd));
-                steps.push_back(hb * p.w);
-            }
-            rotate_items(c, in, out, steps, l0, false, s);
-        }
-    }
-
-    // 2. groups, in chunks
-    const int G = (int)p.groups.size();
-    const int C = p.chunk;
-    u64* T3 = p.d_chunk;
-    u64* Sb = T3 + (size_t)C * 3 * lw;
-    u64* Tb = Sb + (size_t)C * w;
-    u64* Eb = Tb + (size_t)C * w;
-    u64* Mb = Eb + (size_t)C * w;
-    u64* MUb = Mb + (size_t)C * w;
-    u64* PTb = MUb + (size_t)C * w;
-    for (int g0 = 0; g0 < G; g0 += C) {
-        const int cnt = std::min(C, G - g0);
-        std::vector<BinItem> tens, pm;
-        std::vector<u64*> t3s, pout;
-        for (int i = 0; i < cnt; i++) {
-            const Group& g = p.groups[g0 + i];
-            u64* t3 = T3 + (size_t)i * 3 * lw;
-            tens.push_back({UD(g.b), Vr(p.group_node[g0 + i]), t3});
-            t3s.push_back(t3);
-            pout.push_back(Sb + (size_t)i * w);
-        }
-        items_tensor(c, tens, l0 + 1, s);
-        relin_rescale_items(c, t3s, pout, l0, s);
-        // rotate-and-sum over kp slots: S (in Tb) from P (in Sb)
-        {
-            std::vector<u64*> in, out;
-            for (int i = 0; i < cnt; i++) {
-                in.push_back(Sb + (size_t)i * w);
-                out.push_back(Tb + (size_t)i * w);
-            }
-            rotsum_items(c, in, out, p.kp, l1, s);
-        }
-        u64* cur = Tb;
-        // E = R - S
-        std::vector<BinItem> esub;
-        for (int i = 0; i < cnt; i++)
-            esub.push_back({p.d_R + (size_t)p.bin_of[g0 + i] * w, cur + (size_t)i * w, Eb + (size_t)i * w});
-        items_add(c, esub, 2, l1 + 1, true, s);
-        // masks: M = rescale(Vr (.) mask), MU = rescale(UD (.) mask)
-        materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, cnt, l0 + 1, PTb, lw, s);
-        std::vector<UnItem> resc_m;
-        for (int i = 0; i < cnt; i++) {
-            const Group& g = p.groups[g0 + i];
-            const u64* pt = PTb + (size_t)i * lw;
-            pm.push_back({Vr(p.group_node[g0 + i]), pt, Mb + (size_t)i * w});
-            pm.push_back({UD(g.b), pt, MUb + (size_t)i * w});
-            resc_m.push_back({Mb + (size_t)i * w, Mb + (size_t)i * w});
-            resc_m.push_back({MUb + (size_t)i * w, MUb + (size_t)i * w});
-        }
-        items_mul_plain(c, pm, 2, l0 + 1, s);
-        items_rescale(c, resc_m, 2, l0, s);
-        // accumulate the tensors: TU_b += E (x) M, TV[node] += E (x) MU
-        std::map<int, std::vector<int>> by_b, by_node;
-        for (int i = 0; i < cnt; i++) {
-            by_b[p.groups[g0 + i].b].push_back(i);
-            by_node[p.group_node[g0 + i]].push_back(i);
-        }
-        std::vector<AccTarget> tg;
-        std::vector<BinItem> cb;
-        for (auto& kv : by_b) {
-            tg.push_back({p.d_TU + (size_t)kv.first * 3 * lw, (int)cb.size(), (int)kv.second.size()});
-            for (int i : kv.second) cb.push_back({Eb + (size_t)i * w, Mb + (size_t)i * w, nullptr});
-        }
-        for (auto& kv : by_node) {
-            tg.push_back({p.d_TV + (size_t)kv.first * 3 * lw, (int)cb.size(), (int)kv.second.size()});
-            for (int i : kv.second) cb.push_back({Eb + (size_t)i * w, MUb + (size_t)i * w, nullptr});
-        }
-        items_tensor_acc(c, tg, cb, l1 + 1, s);
-    }
-
-    // 3. relinearise and rescale the accumulators
     u64* AccU = p.d_fin;                                   // [n_ub] ciphertexts
     u64* FU = AccU + (size_t)p.n_ub * w;                   // [n_ub]
     u64* BaseU = FU + (size_t)p.n_ub * w;                  // [n_ub]
     u64* FV = BaseU + (size_t)p.n_ub * w;                  // [n_vb]
     u64* BaseV = FV + (size_t)p.n_vb * w;                  // [n_vb]
+
+    // The item batches run in waves whose delta-tree nodes fit the node workspace; user-side
+    // accumulators collect over all waves, each wave finishes its own item batches.
+    for (size_t wv = 0; wv + 1 < p.wave_c.size(); wv++) {
+        const int cb0 = p.wave_c[wv], cb1 = p.wave_c[wv + 1];
+        const int nd0 = p.c_first_node[cb0], nd1 = p.c_first_node[cb1], nodes = nd1 - nd0;
+        auto Vr = [&](int nd) { return p.d_Vr + (size_t)(nd - nd0) * w; };
+        auto H = [&](int nd) { return p.d_H + (size_t)(nd - nd0) * w; };
+        auto TV = [&](int nd) { return p.d_TV + (size_t)(nd - nd0) * 3 * lw; };
+        CK(cudaMemsetAsync(p.d_TV, 0, sizeof(u64) * nodes * 3 * lw, s));
+        CK(cudaMemsetAsync(p.d_H, 0, sizeof(u64) * nodes * w, s));
+        int maxpop = 0;
+        for (int nd = nd0; nd < nd1; nd++) maxpop = std::max(maxpop, popc(p.node_delta[nd]));
+
+        // 1. delta trees of the wave's item batches, one launch set per popcount level
+        {
+            std::vector<UnItem> roots;
+            for (int cb = cb0; cb < cb1; cb++) roots.push_back({VD(cb), Vr(p.node(cb, 0))});
+            items_copy(c, roots, 2, l0 + 1, s);
+            for (int pc = 1; pc <= maxpop; pc++) {
+                std::vector<const u64*> in;
+                std::vector<u64*> out;
+                std::vector<int> steps;
+                for (int nd = nd0; nd < nd1; nd++) {
+                    int d = p.node_delta[nd];
+                    if (popc(d) != pc) continue;
+                    int hb = 1 << hbit(d);
+                    in.push_back(Vr(p.node(p.node_c[nd], d - hb)));
+                    out.push_back(Vr(nd));
+                    steps.push_back(hb * p.w);
+                }
+                rotate_items(c, in, out, steps, l0, false, s);
+            }
+        }
+
+        // 2. the wave's groups, in chunks (positions of the execution order)
+        const int C = p.chunk;
+        u64* T3 = p.d_chunk;
+        u64* Sb = T3 + (size_t)C * 3 * lw;
+        u64* Tb = Sb + (size_t)C * w;
+        u64* Eb = Tb + (size_t)C * w;
+        u64* Mb = Eb + (size_t)C * w;
+        u64* MUb = Mb + (size_t)C * w;
+        u64* PTb = MUb + (size_t)C * w;
+        const int pos_end = p.c_first_pos[cb1];
+        for (int g0 = p.c_first_pos[cb0]; g0 < pos_end; g0 += C) {
+            const int cnt = std::min(C, pos_end - g0);
+            auto gid = [&](int i) { return p.order[g0 + i]; };
+            std::vector<BinItem> tens, pm;
+            std::vector<u64*> t3s, pout;
+            for (int i = 0; i < cnt; i++) {
+                const Group& g = p.groups[gid(i)];
+                u64* t3 = T3 + (size_t)i * 3 * lw;
+                tens.push_back({UD(g.b), Vr(p.group_node[gid(i)]), t3});
+                t3s.push_back(t3);
+                pout.push_back(Sb + (size_t)i * w);
+            }
+            items_tensor(c, tens, l0 + 1, s);
+            relin_rescale_items(c, t3s, pout, l0, s);
+            // rotate-and-sum over kp slots: S (in Tb) from P (in Sb)
+            {
+                std::vector<u64*> in, out;
+                for (int i = 0; i < cnt; i++) {
+                    in.push_back(Sb + (size_t)i * w);
+                    out.push_back(Tb + (size_t)i * w);
+                }
+                rotsum_items(c, in, out, p.kp, l1, s);
+            }
+            // E = R - S: R's c1 regenerated from its seed into E's c1 rows, then transformed
+            {
+                std::vector<SeedRow> rows;
+                for (int i = 0; i < cnt; i++)
+                    for (int x = 0; x <= l1; x++)
+                        rows.push_back({seeded_key(c, kRNonce + (u64)p.bin_of[gid(i)], x),
+                                        Eb + (size_t)i * w + lw + (size_t)x * c.n, x, 0});
+                seeded_uniform_device(c, rows, s);
+                ntt_forward(c, poly_batch(Eb + lw, w, 0, cnt, 1, 0, l1 + 1), s);
+                std::vector<BinItem> e0, e1;
+                for (int i = 0; i < cnt; i++) {
+                    e0.push_back({p.d_R + (size_t)p.bin_of[gid(i)] * c.L * c.n, Tb + (size_t)i * w, Eb + (size_t)i * w});
+                    e1.push_back({Eb + (size_t)i * w + lw, Tb + (size_t)i * w + lw, Eb + (size_t)i * w + lw});
+                }
+                items_add(c, e0, 1, l1 + 1, true, s);
+                items_add(c, e1, 1, l1 + 1, true, s);
+            }
+            // masks: M = rescale(Vr (.) mask), MU = rescale(UD (.) mask)
+            materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, cnt, l0 + 1, PTb, lw, s);
+            std::vector<UnItem> resc_m;
+            for (int i = 0; i < cnt; i++) {
+                const Group& g = p.groups[gid(i)];
+                const u64* pt = PTb + (size_t)i * lw;
+                pm.push_back({Vr(p.group_node[gid(i)]), pt, Mb + (size_t)i * w});
+                pm.push_back({UD(g.b), pt, MUb + (size_t)i * w});
+                resc_m.push_back({Mb + (size_t)i * w, Mb + (size_t)i * w});
+                resc_m.push_back({MUb + (size_t)i * w, MUb + (size_t)i * w});
+            }
+            items_mul_plain(c, pm, 2, l0 + 1, s);
+            items_rescale(c, resc_m, 2, l0, s);
+            // accumulate the tensors: TU_b += E (x) M, TV[node] += E (x) MU
+            std::map<int, std::vector<int>> by_b, by_node;
+            for (int i = 0; i < cnt; i++) {
+                by_b[p.groups[gid(i)].b].push_back(i);
+                by_node[p.group_node[gid(i)]].push_back(i);
+            }
+            std::vector<AccTarget> tg;
+            std::vector<BinItem> cbi;
+            for (auto& kv : by_b) {
+                tg.push_back({p.d_TU + (size_t)kv.first * 3 * lw, (int)cbi.size(), (int)kv.second.size()});
+                for (int i : kv.second) cbi.push_back({Eb + (size_t)i * w, Mb + (size_t)i * w, nullptr});
+            }
+            for (auto& kv : by_node) {
+                tg.push_back({TV(kv.first), (int)cbi.size(), (int)kv.second.size()});
+                for (int i : kv.second) cbi.push_back({Eb + (size_t)i * w, MUb + (size_t)i * w, nullptr});
+            }
+            items_tensor_acc(c, tg, cbi, l1 + 1, s);
+        }
+
+        // 3. relinearise and rescale the wave's item-side accumulators
+        {
+            std::vector<char> used(nodes, 0);
+            for (int pos = p.c_first_pos[cb0]; pos < pos_end; pos++) used[p.group_node[p.order[pos]] - nd0] = 1;
+            std::vector<u64*> t3, outs;
+            for (int nd = nd0; nd < nd1; nd++)
+                if (used[nd - nd0]) {
+                    t3.push_back(TV(nd));
+                    outs.push_back(H(nd));
+                }
+            relin_rescale_items(c, t3, outs, l1, s);
+        }
+
+        // 4. back-rotation of the item gradients along the delta trees (deepest first)
+        {
+            u64* rot_buf = p.d_chunk;  // reuse the chunk area
+            const int cap = (int)((size_t)p.chunk_alloc * 14 * lw / w);
+            for (int pc = maxpop; pc >= 1; pc--) {
+                std::vector<int> lvl;
+                for (int nd = nd0; nd < nd1; nd++)
+                    if (popc(p.node_delta[nd]) == pc) lvl.push_back(nd);
+                for (size_t o = 0; o < lvl.size(); o += cap) {
+                    size_t cnt = std::min(lvl.size() - o, (size_t)cap);
+                    std::vector<const u64*> in;
+                    std::vector<u64*> out;
+                    std::vector<int> steps;
+                    std::map<int, std::vector<int>> by_parent;
+                    for (size_t i = 0; i < cnt; i++) {
+                        int nd = lvl[o + i];
+                        int d = p.node_delta[nd];
+                        int hb = 1 << hbit(d);
+                        in.push_back(H(nd));
+                        out.push_back(rot_buf + i * w);
+                        steps.push_back(-hb * p.w);
+                        by_parent[p.node(p.node_c[nd], d - hb)].push_back((int)i);
+                    }
+                    rotate_items(c, in, out, steps, l2, false, s);
+                    std::vector<AccTarget> tg;
+                    std::vector<BinItem> cbi;
+                    for (auto& kv : by_parent) {
+                        tg.push_back({H(kv.first), (int)cbi.size(), (int)kv.second.size()});
+                        for (int i : kv.second) cbi.push_back({rot_buf + (size_t)i * w, nullptr, nullptr});
+                    }
+                    items_sum_acc(c, tg, cbi, 2, l2 + 1, s);
+                }
+            }
+        }
+
+        // 5. the wave's item batches: half-fill and apply (V_c is read only by its own wave)
+        {
+            std::vector<const u64*> in;
+            std::vector<u64*> out;
+            for (int cb = cb0; cb < cb1; cb++) {
+                in.push_back(H(p.node(cb, 0)));
+                out.push_back(FV + (size_t)cb * w);
+            }
+            std::vector<int> steps(in.size(), -p.kp);
+            rotate_items(c, in, out, steps, l2, true, s);
+            u64* PT = p.d_chunk;
+            materialize_plain(c, p.d_reg + (size_t)(p.n_ub + cb0) * c.n, c.n, cb1 - cb0, l0 + 1, PT, lw, s);
+            std::vector<BinItem> pm, fin;
+            std::vector<UnItem> rs;
+            for (int cb = cb0; cb < cb1; cb++) {
+                pm.push_back({VD(cb), PT + (size_t)(cb - cb0) * lw, BaseV + (size_t)cb * w});
+                rs.push_back({BaseV + (size_t)cb * w, BaseV + (size_t)cb * w});
+                fin.push_back({BaseV + (size_t)cb * w, FV + (size_t)cb * w, VD(cb)});
+            }
+            items_mul_plain(c, pm, 2, l0 + 1, s);
+            items_rescale(c, rs, 2, l0, s);
+            items_add(c, fin, 2, l2 + 1, false, s);
+        }
+    }
+
+    // 6. the user side: relinearise-rescale the accumulators, half-fill and apply
     {
         std::vector<u64*> t3, outs;
         for (int b = 0; b < p.n_ub; b++) {
             t3.push_back(p.d_TU + (size_t)b * 3 * lw);
             outs.push_back(AccU + (size_t)b * w);
         }
-        std::vector<char> used(nodes, 0);
-        for (int nd : p.group_node) used[nd] = 1;
-        for (int nd = 0; nd < nodes; nd++)
-            if (used[nd]) {
-                t3.push_back(p.d_TV + (size_t)nd * 3 * lw);
-                outs.push_back(p.d_H + (size_t)nd * w);
-            }
         relin_rescale_items(c, t3, outs, l1, s);
-    }
-
-    // 4. back-rotation of the item gradients along the delta trees (deepest first)
-    {
-        int maxpop = 0;
-        for (int d : p.node_delta) maxpop = std::max(maxpop, popc(d));
-        u64* rot_buf = p.d_chunk;  // reuse the chunk area
-        const int cap = (int)((size_t)p.chunk_alloc * 14 * lw / w);
-        for (int pc = maxpop; pc >= 1; pc--) {
-            std::vector<int> lvl;
-            for (int nd = 0; nd < nodes; nd++)
-                if (popc(p.node_delta[nd]) == pc) lvl.push_back(nd);
-            for (size_t o = 0; o < lvl.size(); o += cap) {
-                size_t cnt = std::min(lvl.size() - o, (size_t)cap);
-                std::vector<const u64*> in;
-                std::vector<u64*> out;
-                std::vector<int> steps;
-                std::map<int, std::vector<int>> by_parent;
-                for (size_t i = 0; i < cnt; i++) {
-                    int nd = lvl[o + i];
-                    int d = p.node_delta[nd];
-                    int hb = 1 << hbit(d);
-                    in.push_back(p.d_H + (size_t)nd * w);
-                    out.push_back(rot_buf + i * w);
-                    steps.push_back(-hb * p.w);
-                    by_parent[p.node(p.node_c[nd], d - hb)].push_back((int)i);
-                }
-                rotate_items(c, in, out, steps, l2, false, s);
-                std::vector<AccTarget> tg;
-                std::vector<BinItem> cb;
-                for (auto& kv : by_parent) {
-                    tg.push_back({p.d_H + (size_t)kv.first * w, (int)cb.size(), (int)kv.second.size()});
-                    for (int i : kv.second) cb.push_back({rot_buf + (size_t)i * w, nullptr, nullptr});
-                }
-                items_sum_acc(c, tg, cb, 2, l2 + 1, s);
-            }
-        }
-    }
-
-    // 5. half-fill (copy the first kp slots of each block into the second half) and apply
-    {
         std::vector<const u64*> in;
         std::vector<u64*> out;
         for (int b = 0; b < p.n_ub; b++) {
             in.push_back(AccU + (size_t)b * w);
             out.push_back(FU + (size_t)b * w);
         }
-        for (int cb = 0; cb < p.n_vb; cb++) {
-            in.push_back(p.d_H + (size_t)p.node(cb, 0) * w);
-            out.push_back(FV + (size_t)cb * w);
-        }
         std::vector<int> steps(in.size(), -p.kp);
         rotate_items(c, in, out, steps, l2, true, s);
-        // base = rescale(X (.) reg), then X <- base + F (limbs 0..l2)
         u64* PT = p.d_chunk;
-        materialize_plain(c, p.d_reg, c.n, p.n_ub + p.n_vb, l0 + 1, PT, lw, s);
-        std::vector<BinItem> pm;
+        materialize_plain(c, p.d_reg, c.n, p.n_ub, l0 + 1, PT, lw, s);
+        std::vector<BinItem> pm, fin;
         std::vector<UnItem> rs;
         for (int b = 0; b < p.n_ub; b++) {
             pm.push_back({UD(b), PT + (size_t)b * lw, BaseU + (size_t)b * w});
             rs.push_back({BaseU + (size_t)b * w, BaseU + (size_t)b * w});
-        }
-        for (int cb = 0; cb < p.n_vb; cb++) {
-            pm.push_back({VD(cb), PT + (size_t)(p.n_ub + cb) * lw, BaseV + (size_t)cb * w});
-            rs.push_back({BaseV + (size_t)cb * w, BaseV + (size_t)cb * w});
+            fin.push_back({BaseU + (size_t)b * w, FU + (size_t)b * w, UD(b)});
         }
         items_mul_plain(c, pm, 2, l0 + 1, s);
         items_rescale(c, rs, 2, l0, s);
-        std::vector<BinItem> fin;
-        for (int b = 0; b < p.n_ub; b++) fin.push_back({BaseU + (size_t)b * w, FU + (size_t)b * w, UD(b)});
-        for (int cb = 0; cb < p.n_vb; cb++) fin.push_back({BaseV + (size_t)cb * w, FV + (size_t)cb * w, VD(cb)});
         items_add(c, fin, 2, l2 + 1, false, s);
     }
 }
@@ -570,6 +628,21 @@ int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* r
                 }
         }
         for (const Group& g : p->groups) p->group_node.push_back(p->node(g.c, g.delta));
+        // execution order (c, b, delta) and the item-batch waves of the node workspace
+        {
+            const int G0 = (int)p->groups.size();
+            p->order.resize(G0);
+            for (int gi = 0; gi < G0; gi++) p->order[gi] = gi;
+            std::stable_sort(p->order.begin(), p->order.end(),
+                             [&](int x, int y) { return p->groups[x].c < p->groups[y].c; });
+            p->c_first_pos.assign(p->n_vb + 1, G0);
+            for (int pos = G0 - 1; pos >= 0; pos--) p->c_first_pos[p->groups[p->order[pos]].c] = pos;
+            for (int cb = p->n_vb - 1; cb >= 0; cb--)
+                p->c_first_pos[cb] = std::min(p->c_first_pos[cb], p->c_first_pos[cb + 1]);
+            p->c_first_node.assign(p->n_vb + 1, (int)p->node_c.size());
+            for (int nd = (int)p->node_c.size() - 1; nd >= 0; nd--) p->c_first_node[p->node_c[nd]] = nd;
+            plan_waves(*p);
+        }
         // Rating bins: within each user batch, groups in plan order go to the first bin (in creation
         // order) holding none of their users, else to a new bin; bins are numbered batch by batch.
         const int G = (int)p->groups.size();
@@ -600,8 +673,9 @@ int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* r
                 }
             }
         }
-        // EncryptCsrMatrix: one ciphertext per bin, each group's ratings in the first k slots of
-        // their user blocks, top level, nonce 2^40 + bin
+        // EncryptCsrMatrix: one ciphertext per bin, each group's ratings in the first k slots of their
+        // user blocks, encrypted by the key holder with a regenerable c1 (object 2^40 + bin) at level
+        // L - 1, the highest level an epoch reads it at; only c0 is stored
         const int NB = (int)p->bin_b.size();
         std::vector<std::vector<std::pair<int, double>>> bin_nz(NB);
         for (int gi = 0; gi < G; gi++) {
@@ -610,8 +684,9 @@ int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* r
                 if (gr.r[t] != 0.0)
                     for (int x = 0; x < p->k; x++) bin_nz[p->bin_of[gi]].push_back({gr.a[t] * p->w + x, gr.r[t]});
         }
-        const size_t w = c.ct_words();
-        p->d_R = plan_alloc<u64>(*p, (size_t)std::max(NB, 1) * w);
+        if (c.L < 1) fail(FHE_ERR_INVALID_ARG, "the modulus chain needs at least two data primes");
+        const size_t rw = (size_t)c.L * c.n;  // c0 at level L - 1
+        p->d_R = plan_alloc<u64>(*p, (size_t)std::max(NB, 1) * rw);
         const int chunk = 256;
         i64* m_dev = (i64*)c.scratch_bytes("pack_m", sizeof(i64) * chunk * c.n);
         for (int t0 = 0; t0 < NB; t0 += chunk) {
@@ -631,7 +706,7 @@ int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* r
             }
             c.arena.reset(0);
             encode_many_device(c, idx, val, off, m_dev, 0);
-            encrypt_coeffs_device(c, m_dev, c.n, t1 - t0, c.L, nonces, p->d_R + (size_t)t0 * w, 0);
+            encrypt_seeded_device(c, m_dev, c.n, t1 - t0, c.L - 1, nonces, p->d_R + (size_t)t0 * rw, 0);
         }
         CK(cudaStreamSynchronize(0));
     });
@@ -661,6 +736,24 @@ int fhe_mf_plan_set_chunk(fhe_mf_plan* p, int32_t groups) {
         p->d_chunk = nullptr;
     }
     p->chunk = groups;
+    return FHE_OK;
+}
+
+int fhe_mf_plan_set_wave_budget(fhe_mf_plan* p, uint64_t bytes) {
+    if (!p || bytes == 0) return FHE_ERR_INVALID_ARG;
+    if (p->d_Vr) {  // the node workspace is re-sized at the next epoch
+        cudaSetDevice(p->c->device);
+        cudaDeviceSynchronize();
+        const size_t w = p->c->ct_words();
+        for (u64** b : {&p->d_Vr, &p->d_TV, &p->d_TU, &p->d_H, &p->d_fin}) {
+            cudaFree(*b);
+            *b = nullptr;
+        }
+        p->bytes -= ((size_t)p->wave_nodes * (2 * w + 3 * (w / 2)) + (size_t)p->n_ub * 3 * (w / 2) +
+                     (size_t)(p->n_ub + p->n_vb) * 3 * w) * sizeof(u64);
+    }
+    p->wave_budget = bytes;
+    plan_waves(*p);
     return FHE_OK;
 }
 

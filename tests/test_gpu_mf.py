@@ -99,6 +99,21 @@ def test_epoch_bit_exact_and_fp64(preset, n, m, density, k, chunk):
     assert abs(e_gpu - e_ref) < 1e-4
 
 
+def test_epoch_in_item_batch_waves_bit_exact():
+    """One item batch per wave of the node workspace (the large-workload memory mode): the same bits."""
+    csr, U, V = _small_case(seed=260, n=60, m=200, density=0.04, k=3)
+    ctx, plan, he, oplan, emf, UD, VD, oUD, oVD = _setup("t10", csr, 3, U, V, 5)
+    assert plan.n_vb > 1
+    plan.set_wave_budget(1)
+    lr, lam = 0.01, 0.02
+    plan.sgd_epoch(UD, VD, ctx.top, lr, lam)
+    oU2, oV2 = emf.epoch(oUD, oVD, lr, lam)
+    lv = ctx.top - 2
+    for got, want, name in ((to_coeff(ctx, UD, lv, plan.n_ub), oU2, "U"), (to_coeff(ctx, VD, lv, plan.n_vb), oV2, "V")):
+        for t, o in enumerate(want):
+            assert_ct_equal(got[t], o, f"{name}'[{t}]")
+
+
 def test_two_epochs_and_level_exhaustion():
     csr, U, V = _small_case(seed=8, n=50, m=40, density=0.06, k=2)
     ctx, plan, he, oplan, emf, UD, VD, oUD, oVD = _setup("t11a2", csr, 2, U, V)

@@ -305,3 +305,39 @@ def test_relin_rescale_matches_two_step_up_to_conversion_error():
             d = [a - b for a, b in zip(he.decrypt_coeffs(fused), he.decrypt_coeffs(two))]
             assert max(abs(v) for v in d) <= (prm.alpha + 1) * (prm.n + 1)
             assert np.abs(he.decrypt(fused) - x * y).max() < 1e-5
+
+
+def test_uniform_indexed_sampler():
+    """Uniform residues, each coefficient from its own draws: the first-try value is the SplitMix64
+    output x_k mod q whenever x_k is below floor(2^64/q) q."""
+    q = ckks.gen_primes(10, [50])[0]
+    h = ckks.stream_key(5, ckks.P_SEEDED_A, 3, 0, 1)
+    u = ckks.sample_uniform_indexed(h, 4096, q)
+    assert (u < np.uint64(q)).all()
+    assert abs(float(np.mean(u.astype(np.float64))) / q - 0.5) < 0.02
+    x = ckks.draws(h, 0, 4096)
+    ok = x < np.uint64(((1 << 64) // q) * q)
+    assert (u[ok] == x[ok] % np.uint64(q)).all()
+    # just above 2^63 the bound is q itself, so about half the first draws are rejected; the
+    # retries keep the values uniform
+    q3 = 9223372036854775837   # the first prime above 2^63
+    v = ckks.sample_uniform_indexed(h, 20000, q3)
+    x = ckks.draws(h, 0, 20000)
+    assert 0.45 < float(np.mean(x >= np.uint64(q3))) < 0.55
+    assert (v < np.uint64(q3)).all() and abs(float(np.mean(v.astype(np.float64))) / q3 - 0.5) < 0.02
+
+
+def test_encrypt_seeded_exact_error_and_regenerable_c1():
+    """decrypt(encrypt_seeded(m)) = m + e exactly, with e the seeded Gaussian stream; c1 is the
+    uniform stream of (seed, object) and nothing else."""
+    prm = _params(log_n=5)
+    he = ckks.Ckks(prm)
+    he.keygen(41)
+    rng = np.random.default_rng(4)
+    m = rng.integers(-(1 << 40), 1 << 40, size=prm.n)
+    ct = he.encrypt_seeded(m, prm.top - 1, 77)
+    e = ckks.sample_gaussian(ckks.stream_key(41, ckks.P_SEEDED_E, 77), prm.n, 3.2)
+    assert he.decrypt_coeffs(ct) == [int(a) + int(b) for a, b in zip(m, e)]
+    for i, q in enumerate(prm.q[: prm.top]):
+        a = ckks.sample_uniform_indexed(ckks.stream_key(41, ckks.P_SEEDED_A, 77, 0, i), prm.n, q)
+        assert (ct.c[1][i] == a).all()
