@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--served-rate", type=float, default=100.0)
     ap.add_argument("--served-slots", type=int, default=48)
     ap.add_argument("--served-sweep", default="", help="comma-separated arrival rates (req/s) to sweep")
+    ap.add_argument("--workload", choices=["paper", "large"], default="paper",
+                    help="paper: the headline paper-scale epoch; large: the 6040 x 3706 workload at N=2^16")
     return ap.parse_args()
 
 
@@ -110,8 +112,24 @@ def stop_clocks(proc, path):
 
 # ----------------------------------------------------------------------------- workload
 
-def workload():
+LARGE = ("large encrypted MF epoch: 6040 users x 3706 items, 1,000,209 synthetic MovieLens-1M-shaped ratings "
+         "(Zipf 1.1, 90 % train), k=16; RNS-CKKS N=2^16, 20x50-bit data + 3x60-bit special primes, scale 2^50; "
+         "one SGD epoch (lr 0.0002, lambda 0.02) per step")
+
+
+def workload_spec(name):
+    """(preset, rank, learning rate, description) of a bench workload."""
+    if name == "large":   # lr 0.0002: the largest stable rate of the accumulated update at this shape
+        return "large", 16, 0.0002, LARGE
+    return "paper", K_RANK, LR, WORKLOAD
+
+
+def workload(name="paper"):
     from paper_2509_03024_gb300 import workloads as W
+    if name == "large":
+        full = W.movielens_like(6040, 3706, 1_000_209, 1.1, 5)
+        train, test = W.split_holdout(full, 0.1, 12)
+        return train, test, W.init_factors(6040, 16, 105), W.init_factors(3706, 16, 205)
     train, test, U, V = W.paper_workload(seed=2)
     return train, test, U, V
 
@@ -125,14 +143,8 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
 
-def oracle_sample(train, U, V, groups_sampled: int = 1):
-    """Time the oracle (as it stands) on a bounded sample of the epoch and extrapolate.
-
-    Sample: the per-group work (product, relinearise, rescale, rotate-and-sum,
-    masks, tensors) of `groups_sampled` groups plus one delta-tree rotation; the
-    epoch estimate is per-group time x groups + per-rotation time x 2 x tree
-    nodes + per-relinearisation time x tree nodes. Returns (ratings/s, seconds
-    measured, description)."""
+def oracle_setup(train, U, V, groups_sampled: int = 1):
+    """Keys, plan and the sampled groups' ciphertexts on the oracle (not timed)."""
     from oracle import ckks, mf
     from paper_2509_03024_gb300.workloads import PRESETS
     rows, cols, vals = train.triples()
@@ -155,20 +167,34 @@ def oracle_sample(train, U, V, groups_sampled: int = 1):
         c = plan.groups[t].c
         if c not in VDc:
             VDc[c] = he.encrypt(mf.pack_factors(V, plan, c), top, mf.V_NONCE_BASE + c)
+    return {"he": he, "plan": plan, "emf": emf, "pick": pick, "UD": UD, "VDc": VDc, "ratings": rows.size}
+
+
+def oracle_time(st):
+    """Time the oracle (as it stands) on the sampled groups' per-group work (product,
+    relinearise-rescale, rotate-and-sum, masks, tensors) plus one delta-tree rotation, and
+    extrapolate to an epoch: per-group time x groups + per-rotation time x 3 x tree nodes (the
+    rotation, relinearisation and back-rotation of every node). Returns (ratings/s, seconds
+    measured, description)."""
+    he, plan, emf, pick = st["he"], st["plan"], st["emf"], st["pick"]
     t0 = time.perf_counter()
     for t in pick:
         g = plan.groups[t]
-        emf.group_terms(t, UD[g.b], VDc[g.c], LR)   # Vr of delta 0 stands in for the rotated copy
+        emf.group_terms(t, st["UD"][g.b], st["VDc"][g.c], LR)   # Vr of delta 0 stands in for the rotated copy
     t_groups = (time.perf_counter() - t0) / len(pick)
     t1 = time.perf_counter()
-    he.rotate(next(iter(VDc.values())), plan.w)
+    he.rotate(next(iter(st["VDc"].values())), plan.w)
     t_rot = time.perf_counter() - t1
     nodes = sum(len(c) for c in plan.closure)
-    est = t_groups * len(plan.groups) + t_rot * 2 * nodes + t_rot * nodes
+    est = t_groups * len(plan.groups) + t_rot * 3 * nodes
     desc = (f"oracle on {len(pick)} of {len(plan.groups)} groups + 1 rotation at N=2^15, single thread; "
             f"epoch extrapolated as groups x {t_groups:.2f} s + {3 * nodes} rotation-sized key switches x "
             f"{t_rot:.2f} s = {est:.0f} s")
-    return rows.size / est, time.perf_counter() - t0, desc
+    return st["ratings"] / est, time.perf_counter() - t0, desc
+
+
+def oracle_sample(train, U, V, groups_sampled: int = 1):
+    return oracle_time(oracle_setup(train, U, V, groups_sampled))
 
 
 # ----------------------------------------------------------------------------- served workload
@@ -291,10 +317,11 @@ def run_gpu(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    train, test, U, V = workload()
-    ctx = capi.Context.from_preset(PRESETS["paper"], device=dev)
-    ctx.keygen(SEED + rank, ctx.mf_rotation_steps(K_RANK))
-    plan = capi.MfPlan(ctx, train.n, train.m, K_RANK, train.row_ptr, train.col_idx, train.vals)
+    preset, k_rank, lr, _ = workload_spec(args.workload)
+    train, test, U, V = workload(args.workload)
+    ctx = capi.Context.from_preset(PRESETS[preset], device=dev)
+    ctx.keygen(SEED + rank, ctx.mf_rotation_steps(k_rank))
+    plan = capi.MfPlan(ctx, train.n, train.m, k_rank, train.row_ptr, train.col_idx, train.vals)
     U0, V0 = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
     plan.encrypt_factors(0, U, U0)
     plan.encrypt_factors(1, V, V0)
@@ -307,7 +334,7 @@ def run_gpu(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             UD.copy_(U0)
             VD.copy_(V0)
-        plan.sgd_epoch(UD, VD, top, LR, LAM, stream)
+        plan.sgd_epoch(UD, VD, top, lr, LAM, stream)
 
     for _ in range(args.warmup):
         step()
@@ -335,7 +362,7 @@ def run_gpu(args, rank, world, local_rank):
     # decrypted accuracy of the last step against the FP64 epoch (sanity, not timed)
     from oracle import mf as omf
     rows, cols, vals = train.triples()
-    U1, V1 = omf.mf_epoch_fp64(U, V, rows, cols, vals, LR, LAM)
+    U1, V1 = omf.mf_epoch_fp64(U, V, rows, cols, vals, lr, LAM)
     Ud = plan.decrypt_factors(0, UD, top - 2, train.n)
     Vd = plan.decrypt_factors(1, VD, top - 2, train.m)
     err = max(float(np.abs(Ud - U1).max()), float(np.abs(Vd - V1).max()))
@@ -345,12 +372,12 @@ def run_gpu(args, rank, world, local_rank):
     # end to end through the C ABI with host buffers: H2D of the encrypted factors, epoch, D2H
     e2e = None
     if args.e2e_steps > 0:
-        e2e = run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier)
+        e2e = run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier, lr)
     return finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
                   train, U, V, dist)
 
 
-def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier):
+def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier, lr):
     hU = torch.empty(U0.numel(), dtype=torch.int64, pin_memory=True)
     hV = torch.empty(V0.numel(), dtype=torch.int64, pin_memory=True)
     hU.copy_(U0.cpu())
@@ -365,7 +392,7 @@ def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world
         with torch.cuda.stream(stream):
             UD.copy_(hU, non_blocking=True)
             VD.copy_(hV, non_blocking=True)
-        plan.sgd_epoch(UD, VD, top, LR, LAM, stream)
+        plan.sgd_epoch(UD, VD, top, lr, LAM, stream)
         with torch.cuda.stream(stream):
             oU.copy_(UD, non_blocking=True)
             oV.copy_(VD, non_blocking=True)
@@ -400,11 +427,12 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
     if name.startswith("ntt"):
         # one NTT pass sweeps every row once (16 bytes per residue) and runs log2(N)/2 butterfly stages,
         # i.e. log2(N)/4 butterflies per residue
-        log_n = 15
+        log_n = ctx.log_n
         bfly = (alg_bytes / launches) / 16.0 * (log_n / 4.0)
         achieved = bfly / avg_s / 1e9
         rows_per_launch = (alg_bytes / launches) / (16.0 * 2 ** log_n)
-        traffic = NCU_FWD_DRAM_BYTES_PER_ROW * rows_per_launch if name == "ntt_forward" else None
+        traffic = (NCU_FWD_DRAM_BYTES_PER_ROW * rows_per_launch
+                   if name == "ntt_forward" and args.workload == "paper" else None)
         # peak: the same butterfly arithmetic on register-resident values, measured now on this GPU
         peak = ctx.probe_butterfly_rate(2000)
         roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Gbfly/s",
@@ -431,8 +459,9 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "ratings_per_step": ratings, "parallelism": "replicas",
-                      "l2": "inputs larger than L2 (the rating ciphertexts alone are ~8 GiB)",
+           "config": {"workload": workload_spec(args.workload)[3], "ratings_per_step": ratings, "parallelism": "replicas",
+                      "l2": "inputs larger than L2 (the rating ciphertexts alone are %.1f GiB)" % (
+                          plan.info.n_bins * ctx.top * ctx.n * 8 / 2 ** 30),
                       "rating_bins": int(plan.info.n_bins),
                       "groups": int(plan.info.n_groups), "tree_nodes": int(plan.info.n_tree_nodes),
                       "plan_device_gib": plan.info.device_bytes / 2 ** 30},
@@ -442,13 +471,14 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
                        for k, v in stats.items() if v[0]}}
     from paper_2509_03024_gb300 import comm
     out["communication"] = {
-        "training_10_epochs": comm.mf_training(ctx.n, ctx.top, ctx.alpha, len(ctx.mf_rotation_steps(K_RANK)),
+        "training_10_epochs": comm.mf_training(ctx.n, ctx.top, ctx.alpha,
+                                               len(ctx.mf_rotation_steps(workload_spec(args.workload)[1])),
                                                int(plan.info.n_bins), plan.n_ub, plan.n_vb, epochs=10),
         "note": "bytes between the parties (key holder, data owners, recommender) for the paper-scale workload; "
                 "the epochs themselves move nothing off the GPU"}
     if not args.no_served:
         out["served"] = run_served(args, torch_device_of(ctx))
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "paper":
         rps, secs, desc = oracle_sample(train, U, V)
         out["cpu_baseline"] = {"value": rps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                "measured_s": round(secs, 1)}
@@ -462,9 +492,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     train, test, U, V = workload()
+    st = oracle_setup(train, U, V, groups_sampled=1)
     vals = []
     for i in range(args.warmup + args.steps):
-        rps, secs, desc = oracle_sample(train, U, V, groups_sampled=1)
+        rps, secs, desc = oracle_time(st)
         if i >= args.warmup:
             vals.append(rps)
     v = statistics.median(vals)
