@@ -376,7 +376,8 @@ class EncryptedMF:
             for d in sorted(p.closure[c], key=lambda x: (bin(x).count("1"), x)):
                 if d:
                     hb = 1 << highest_bit(d)
-                    t[d] = he.rotate(t[d - hb], hb * p.w)
+                    # hoisted: the children of a node share the ModUp of its c1
+                    t[d] = he.rotate_sum_hoisted(t[d - hb], [hb * p.w])
             Vr.append(t)
         TU: List[Optional[Ciphertext]] = [None] * p.n_ub
         TV: Dict[Tuple[int, int], Ciphertext] = {}

@@ -369,6 +369,12 @@ struct KsItem {
 };
 void keyswitch_items(Ctx& c, const std::vector<KsItem>& it, int level, cudaStream_t s);
 
+// Rotations that share inputs: out_i = rot(in_i, step_i) with one ModUp per distinct input (the
+// automorphism applied to the raised digits, as in a hoisted rotate-and-sum of one step). out_i
+// must not alias any input.
+void rotate_fanout_items(Ctx& c, const std::vector<const u64*>& in, const std::vector<u64*>& out,
+                         const std::vector<int>& steps, int level, cudaStream_t s);
+
 // Relinearise and rescale in one key switch (ModDown divides by P q_level): out_i (level - 1)
 // from the 3-component t3_i (level). out_i may equal t3_i.
 void relin_rescale_items(Ctx& c, const std::vector<u64*>& t3, const std::vector<u64*>& out, int level,

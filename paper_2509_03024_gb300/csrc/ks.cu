@@ -326,10 +326,13 @@ __device__ __forceinline__ void load_pair_auto(const u64* __restrict__ row, int 
 // outside digit j and the item's input d (through its automorphism) for x in digit j. The
 // products are summed in 128 bits and reduced once; the limb index is the slowest, so one limb's
 // rows of a shared key stay in L2 while every item reads them.
+// FANOUT: item t's raised digits are those of source src_of[t] (its c1 raised once for all the
+// items that rotate it) and every digit is read through item t's automorphism.
+template <bool FANOUT>
 __global__ void __launch_bounds__(256, 4) ks_inner_kernel(u64* acc, const u64* __restrict__ ext,
-                                                          const KsItem* __restrict__ tab, int items, int dn, int alpha,
-                                                          int next, int level, int L, int n_ext, int log_n,
-                                                          const Prime* __restrict__ pr) {
+                                                          const KsItem* __restrict__ tab, const int* __restrict__ src_of,
+                                                          int items, int dn, int alpha, int next, int level, int L,
+                                                          int n_ext, int log_n, const Prime* __restrict__ pr) {
     const size_t half = (size_t)1 << (log_n - 1);
     const size_t total = (size_t)items * next * half;
     const int l1 = level + 1;
@@ -342,9 +345,13 @@ __global__ void __launch_bounds__(256, 4) ks_inner_kernel(u64* acc, const u64* _
         const KsItem it = tab[t];
         const int own = x < l1 ? x / alpha : -1;
         u64 a0x = 0, h0x = 0, a0y = 0, h0y = 0, a1x = 0, h1x = 0, a1y = 0, h1y = 0;
+        const int st = FANOUT ? src_of[t] : t;
         for (int j = 0; j < dn; j++) {
             u64 vx, vy;
-            if (j == own && it.galois != 1) {
+            if (FANOUT) {
+                const u64* src = j == own ? it.d + ((size_t)x << log_n) : ext + ((size_t)((st * dn + j) * next + x) << log_n);
+                load_pair_auto(src, k2, (int)it.galois, log_n, vx, vy);
+            } else if (j == own && it.galois != 1) {
                 load_pair_auto(it.d + ((size_t)x << log_n), k2, (int)it.galois, log_n, vx, vy);
             } else {
                 const u64* src = j == own ? it.d + ((size_t)x << log_n) : ext + ((size_t)((t * dn + j) * next + x) << log_n);
@@ -443,18 +450,38 @@ namespace {
 // divide by P q_level instead of P and the outputs are at level - 1:
 //   out_h = (acc_h + P c_h - Conv_{P u {q_l} -> Q_{l-1}}(acc_h + P c_h)) (P q_l)^-1.
 void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* hk, cudaStream_t s,
-            bool fused_rescale = false) {
+            bool fused_rescale = false, const std::vector<int>* fanout_src = nullptr) {
     if (all.empty()) return;
     const int n = c.n, L = c.L, A = c.alpha, l1 = level + 1, next = l1 + A, dn = c.dnum(level);
     const int SP = fused_rescale ? A + 1 : A;  // ModDown source limbs
-    // bound the work area to ~6 GiB per sub-batch
-    const size_t per_item =
-        (size_t)(l1 + dn * next + 2 * next + 2 * SP + 2 * l1 + (hk ? l1 : 0)) * n * sizeof(u64);
-    const int max_items = (int)std::max<size_t>(1, ((size_t)6 << 30) / per_item);
-    for (size_t b0 = 0; b0 < all.size(); b0 += max_items) {
-        const int items = (int)std::min<size_t>(max_items, all.size() - b0);
+    const bool fan = fanout_src != nullptr;
+    // bound the work area to ~6 GiB per sub-batch (per source: y and the raised digits; per item the rest)
+    const size_t per_src = (size_t)(l1 + dn * next) * n * sizeof(u64);
+    const size_t per_item = (size_t)(2 * next + 2 * SP + 2 * l1 + (hk ? l1 : 0)) * n * sizeof(u64);
+    const size_t budget = (size_t)6 << 30;
+    for (size_t b0 = 0; b0 < all.size();) {
+        // items [b0, b0 + items): a fan-out sub-batch ends where a new source would exceed the budget
+        int items = 0, n_src = 0;
+        size_t used = 0;
+        while (b0 + items < all.size()) {
+            const bool new_src = !fan || items == 0 || (*fanout_src)[b0 + items] != (*fanout_src)[b0 + items - 1];
+            const size_t need = per_item + (new_src ? per_src : 0);
+            if (items > 0 && used + need > budget) break;
+            used += need;
+            n_src += new_src ? 1 : 0;
+            items++;
+        }
         std::vector<KsItem> it(all.begin() + b0, all.begin() + b0 + items);
+        std::vector<int> src_of(items), src_first;
+        for (int t = 0; t < items; t++) {
+            const bool new_src = !fan || t == 0 || (*fanout_src)[b0 + t] != (*fanout_src)[b0 + t - 1];
+            if (new_src) src_first.push_back(t);
+            src_of[t] = (int)src_first.size() - 1;
+        }
+        b0 += items;
+        const int n_sources = (int)src_first.size();
         const KsItem* d_items = c.arena.push_vec(it, s);
+        const int* d_src_of = fan ? c.arena.push_vec(src_of, s) : nullptr;
         size_t nkeys = 0;
         {
             std::vector<const u64*> ks;
@@ -462,25 +489,26 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
             std::sort(ks.begin(), ks.end());
             nkeys = std::unique(ks.begin(), ks.end()) - ks.begin();
         }
-        u64* y = c.scratch_u64("ks_y", (size_t)items * l1 * n);
-        u64* ext = c.scratch_u64("ks_ext", (size_t)items * dn * next * n);
+        u64* y = c.scratch_u64("ks_y", (size_t)n_sources * l1 * n);
+        u64* ext = c.scratch_u64("ks_ext", (size_t)n_sources * dn * next * n);
         u64* acc = c.scratch_u64("ks_acc", (size_t)items * 2 * next * n);
         u64* yP = c.scratch_u64("ks_yp", (size_t)items * 2 * SP * n);
         u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
         CombineArgs ca{d_items, acc, c.d_pinv, next, nullptr};
         const CombineArgs none{nullptr, nullptr, nullptr, 0, nullptr};
 
-        // K1: y_i = INTT(perm(d_i)) * qhat_i^-1
+        // K1: y_i = INTT(perm(d_i)) * qhat_i^-1 (fan-out: once per source, no permutation)
         std::vector<KsRow> r1;
-        r1.reserve((size_t)items * l1);
-        for (int t = 0; t < items; t++)
+        r1.reserve((size_t)n_sources * l1);
+        for (int sx = 0; sx < n_sources; sx++)
             for (int i = 0; i < l1; i++) {
+                const KsItem& x0 = it[src_first[sx]];
                 KsRow r{};
-                r.dst = y + ((size_t)t * l1 + i) * n;
-                r.src = it[t].d + (size_t)i * n;
+                r.dst = y + ((size_t)sx * l1 + i) * n;
+                r.src = x0.d + (size_t)i * n;
                 r.cst = c.d_up_ninv + 2 * ((size_t)level * (L + 1) + i);
                 r.prime = i;
-                r.galois = (int)it[t].galois;
+                r.galois = fan ? 1 : (int)x0.galois;
                 r1.push_back(r);
             }
         const KsRow* d_r1 = c.arena.push_vec(r1, s);
@@ -488,8 +516,8 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
 
         // K2: ModUp_j(d)_x for x outside D_j
         std::vector<KsRow> r2;
-        r2.reserve((size_t)items * dn * next);
-        for (int t = 0; t < items; t++)
+        r2.reserve((size_t)n_sources * dn * next);
+        for (int t = 0; t < n_sources; t++)
             for (int j = 0; j < dn; j++) {
                 const int lo = j * A, cnt = std::min(A, l1 - lo);
                 for (int x = 0; x < next; x++) {
@@ -514,9 +542,12 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
             LaunchScope _ls(c.prof, K_KS_INNER,
                             8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next),
                             s);
-            ks_inner_kernel<<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(acc, ext, d_items, items, dn, A,
-                                                                                     next, level, L, c.n_ext, c.log_n,
-                                                                                     c.d_primes);
+            if (fan)
+                ks_inner_kernel<true><<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(
+                    acc, ext, d_items, d_src_of, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
+            else
+                ks_inner_kernel<false><<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(
+                    acc, ext, d_items, nullptr, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
             CK(cudaGetLastError());
         } else {
             // reads: the raised digits and c0 once per item, every key once; writes acc and c0sum
@@ -628,6 +659,27 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
 
 void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
     ks_run(c, all, level, nullptr, s);
+}
+
+void rotate_fanout_items(Ctx& c, const std::vector<const u64*>& in, const std::vector<u64*>& out,
+                         const std::vector<int>& steps, int level, cudaStream_t s) {
+    if (in.size() != out.size() || in.size() != steps.size()) fail(FHE_ERR_INVALID_ARG, "fan-out: list sizes differ");
+    if (in.empty()) return;
+    const size_t lw = c.ct_words() / 2;
+    std::vector<size_t> ord(in.size());
+    for (size_t i = 0; i < ord.size(); i++) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return in[a] < in[b]; });
+    std::vector<KsItem> ks;
+    std::vector<int> src;
+    for (size_t k = 0; k < ord.size(); k++) {
+        const size_t i = ord[k];
+        const int g = (int)c.galois(steps[i]);
+        if (g == 1) fail(FHE_ERR_INVALID_ARG, "fan-out rotation by a multiple of the slot count");
+        const EvalKey& key = rotation_key(c, steps[i]);
+        ks.push_back({in[i] + lw, key.d, in[i], nullptr, nullptr, out[i], out[i] + lw, g});
+        src.push_back(k == 0 || in[i] != in[ord[k - 1]] ? (int)k : src.back());
+    }
+    ks_run(c, ks, level, nullptr, s, false, &src);
 }
 
 void relin_rescale_items(Ctx& c, const std::vector<u64*>& t3, const std::vector<u64*>& out, int level,

@@ -77,6 +77,8 @@ struct fhe_mf_plan {
     bool have_plain = false;
     double lr_c = 0, lam_c = 0;
     i64* d_mask = nullptr;                  // [G][N], in execution order
+    u64* d_mask_eval = nullptr;             // [G][L+1][N] the masks in evaluation form, when they fit
+    size_t mask_cache_budget = (size_t)16 << 30;
     i64* d_reg = nullptr;                   // [n_ub + n_vb][N]
     // epoch workspace
     u64* d_Vr = nullptr;                    // [wave nodes] ciphertexts
@@ -91,7 +93,7 @@ struct fhe_mf_plan {
 
     int node(int cb, int delta) const { return node_of[(size_t)cb * B + delta]; }
     ~fhe_mf_plan() {
-        void* bufs[] = {d_R, d_mask, d_reg, d_Vr, d_TV, d_TU, d_H, d_chunk, d_fin};
+        void* bufs[] = {d_R, d_mask, d_mask_eval, d_reg, d_Vr, d_TV, d_TU, d_H, d_chunk, d_fin};
         for (void* p : bufs)
             if (p) cudaFree(p);
     }
@@ -153,6 +155,14 @@ void ensure_plaintexts(fhe_mf_plan& p, double lr, double lam, cudaStream_t s) {
         }
     }
     encode_many_device(c, idx, val, off, p.d_reg, s);
+    // masks in evaluation form at every limb, reused by every epoch (each reads its first l+1 limbs)
+    const size_t lw = (size_t)(c.L + 1) * c.n;
+    if ((size_t)G * lw * sizeof(u64) <= p.mask_cache_budget) {
+        if (!p.d_mask_eval) p.d_mask_eval = plan_alloc<u64>(p, (size_t)std::max(G, 1) * lw);
+        for (int g0 = 0; g0 < G; g0 += 256)
+            materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, std::min(256, G - g0), c.L + 1,
+                              p.d_mask_eval + (size_t)g0 * lw, lw, s);
+    }
     p.have_plain = true;
     p.lr_c = lr;
     p.lam_c = lam;
@@ -279,7 +289,7 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
                     out.push_back(Vr(nd));
                     steps.push_back(hb * p.w);
                 }
-                rotate_items(c, in, out, steps, l0, false, s);
+                rotate_fanout_items(c, in, out, steps, l0, s);  // siblings share their parent's ModUp
             }
         }
 
@@ -334,11 +344,15 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
                 items_add(c, e1, 1, l1 + 1, true, s);
             }
             // masks: M = rescale(Vr (.) mask), MU = rescale(UD (.) mask)
-            materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, cnt, l0 + 1, PTb, lw, s);
+            const u64* masks = PTb;
+            if (p.d_mask_eval)
+                masks = p.d_mask_eval + (size_t)g0 * lw;
+            else
+                materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, cnt, l0 + 1, PTb, lw, s);
             std::vector<UnItem> resc_m;
             for (int i = 0; i < cnt; i++) {
                 const Group& g = p.groups[gid(i)];
-                const u64* pt = PTb + (size_t)i * lw;
+                const u64* pt = masks + (size_t)i * lw;
                 pm.push_back({Vr(p.group_node[gid(i)]), pt, Mb + (size_t)i * w});
                 pm.push_back({UD(g.b), pt, MUb + (size_t)i * w});
                 resc_m.push_back({Mb + (size_t)i * w, Mb + (size_t)i * w});
