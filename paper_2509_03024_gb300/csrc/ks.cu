@@ -20,6 +20,10 @@
 // tables (one descriptor per limb row), so the conversions happen while the
 // tiles are loaded and the combinations while they are stored.
 //
+// The exact rescale uses the same machinery: an inverse transform of the last limb, then forward
+// transforms whose load forms the centred last limb modulo each q_i and whose store writes
+// (x_i - that) q_l^-1.
+//
 // Hoisted rotate-and-sum (Halevi-Shoup 2018): S = sum_{r < kp} rot(c, r) runs
 // K1 and K2 once on c1, replaces K3 by a kernel that applies each rotation's
 // automorphism to the raised digits while it reads them and sums the inner
@@ -39,8 +43,8 @@ namespace {
 using nttc::reduce4;
 using nttc::shoup_lazy;
 
-enum LoadMode { LD_PLAIN = 0, LD_GATHER = 1, LD_CONV = 2, LD_AXPY = 3 };
-enum StoreMode { ST_LAZY = 0, ST_LAST = 1, ST_SCALE = 2, ST_COMBINE = 3, ST_COMBINE_RS = 4 };
+enum LoadMode { LD_PLAIN = 0, LD_GATHER = 1, LD_CONV = 2, LD_AXPY = 3, LD_CENTRED = 4 };
+enum StoreMode { ST_LAZY = 0, ST_LAST = 1, ST_SCALE = 2, ST_COMBINE = 3, ST_COMBINE_RS = 4, ST_RESCALE = 5 };
 
 struct KsRow {
     u64* dst;        // the row's buffer (N residues)
@@ -52,8 +56,9 @@ struct KsRow {
     int cst_stride;  // LD_CONV: words between consecutive source limbs' constant pairs
     int item, half, limb;  // ST_COMBINE(_RS): output item, component and limb
     int pad;
-    const u64* src2;       // LD_AXPY: second source row (null: none)
-    const u64* cst2;       // LD_AXPY: Shoup pair of its factor
+    const u64* src2;       // LD_AXPY: second source row (null: none); ST_RESCALE: the input limb
+    const u64* cst2;       // LD_AXPY: Shoup pair of its factor; ST_RESCALE: q_l^-1 mod the row's prime
+    u64* out2;             // ST_RESCALE: output row
 };
 
 // Evaluation slot k holds a(psi^(2 brev(k) + 1)); X -> X^g moves slot k' to slot k
@@ -92,14 +97,31 @@ template <int LOAD>
 __device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, const Prime* __restrict__ pr) {
     if (LOAD == LD_PLAIN) return r.dst[k];
     if (LOAD == LD_GATHER) return r.src[r.galois == 1 ? (int)k : auto_src((int)k, r.galois, log_n)];
+    if (LOAD == LD_CENTRED) {  // the centred representative of src[k] (mod q_limb) reduced mod the row's prime
+        const Prime P = pr[r.prime];
+        const u64 ql = pr[r.limb].q, v = r.src[k];
+        const bool neg = v > (ql >> 1);
+        const u64 m = nttc::reduce_any(neg ? ql - v : v, P.q, P.one_s);
+        return neg ? (m ? P.q - m : 0) : m;
+    }
     if (LOAD == LD_AXPY) {  // src + cst2 * src2 (both reduced)
         const u64 p = pr[r.prime].q;
         u64 v = r.src[k];
         if (r.src2) v = add_mod(v, mul_shoup(r.src2[k], r.cst2[0], r.cst2[1], p), p);
         return v;
     }
-    // LD_CONV: fully reduced sum of the converted source limbs
+    // LD_CONV: sum of the converted source limbs. For primes below 2^58 the forward transform that
+    // follows runs without intermediate reduction, so the sum stays lazy (each term below 2p, at most
+    // 8 terms, so below 16p; 16 stages add less than 32p: below 48p < 2^64); otherwise fully reduced.
     const u64 p = pr[r.prime].q;
+    if (p < ((u64)1 << 58) && r.src_cnt <= 8) {
+        u64 lazy = 0;
+        for (int i = 0; i < r.src_cnt; i++) {
+            const u64* c = r.cst + (size_t)i * r.cst_stride;
+            lazy += shoup_lazy(r.src[((size_t)i << log_n) + k], c[0], c[1], p);
+        }
+        return lazy;
+    }
     u64 acc = 0;
     for (int i = 0; i < r.src_cnt; i++) {
         const u64* c = r.cst + (size_t)i * r.cst_stride;
@@ -125,6 +147,11 @@ __device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, u64 
         } else {
             r.dst[k] = nttc::reduce_any(v, q, one_s);
         }
+        return;
+    }
+    if (STORE == ST_RESCALE) {  // forward: out = (x - [x_l]) q_l^-1 with the transformed [x_l] in v
+        const u64 t = nttc::reduce_any(v, q, one_s);
+        r.out2[k] = mul_shoup(sub_mod(r.src2[k], t, q), r.cst2[0], r.cst2[1], q);
         return;
     }
     if (STORE == ST_SCALE) {  // inverse transforms only: times the row's constant instead of N^-1
@@ -659,6 +686,53 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
 
 void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStream_t s) {
     ks_run(c, all, level, nullptr, s);
+}
+
+// Exact centred rescale of `parts` components per item (level -> level - 1), in two transforms:
+// the inverse NTT of the last limb (scaled by N^-1), then for every limb i < level a forward NTT
+// whose load forms [x_level]_centred mod q_i and whose store writes (x_i - that) q_level^-1.
+// out may equal in.
+void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s) {
+    if (level < 1) fail(FHE_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 1");
+    if (it.empty()) return;
+    const int n = c.n, L = c.L;
+    const size_t pw = (size_t)(L + 1) * n;
+    const int max_items = (int)std::max<size_t>(1, ((size_t)2 << 30) / ((size_t)parts * (1 + level) * n * sizeof(u64)));
+    const CombineArgs none{nullptr, nullptr, nullptr, 0, nullptr};
+    for (size_t b0 = 0; b0 < it.size(); b0 += max_items) {
+        const int items = (int)std::min<size_t>(max_items, it.size() - b0);
+        const int rows = items * parts;
+        u64* last = c.scratch_u64("resc_last", (size_t)rows * n);
+        u64* work = c.scratch_u64("resc_work", (size_t)rows * level * n);
+        std::vector<KsRow> ra, rb;
+        for (int t = 0; t < items; t++)
+            for (int p = 0; p < parts; p++) {
+                const UnItem& x = it[b0 + t];
+                KsRow r{};
+                r.dst = last + ((size_t)t * parts + p) * n;
+                r.src = x.in + (size_t)p * pw + (size_t)level * n;
+                r.cst = c.d_ninv + 2 * (size_t)level;
+                r.prime = level;
+                r.galois = 1;
+                ra.push_back(r);
+                for (int i = 0; i < level; i++) {
+                    KsRow q{};
+                    q.dst = work + (((size_t)t * parts + p) * level + i) * n;
+                    q.src = r.dst;
+                    q.prime = i;
+                    q.limb = level;
+                    q.galois = 1;
+                    q.src2 = x.in + (size_t)p * pw + (size_t)i * n;
+                    q.cst2 = c.d_resc + 2 * ((size_t)level * (L + 1) + i);
+                    q.out2 = x.out + (size_t)p * pw + (size_t)i * n;
+                    rb.push_back(q);
+                }
+            }
+        const KsRow* d_ra = c.arena.push_vec(ra, s);
+        ks_transform<true, LD_GATHER, ST_SCALE>(c, d_ra, (int)ra.size(), none, K_NTT_INV, 16.0 * ra.size() * n, s);
+        const KsRow* d_rb = c.arena.push_vec(rb, s);
+        ks_transform<false, LD_CENTRED, ST_RESCALE>(c, d_rb, (int)rb.size(), none, K_NTT_FWD, 16.0 * rb.size() * n, s);
+    }
 }
 
 void rotate_fanout_items(Ctx& c, const std::vector<const u64*>& in, const std::vector<u64*>& out,

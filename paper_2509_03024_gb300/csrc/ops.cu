@@ -1,7 +1,7 @@
 // ops.cu — batched RNS kernels over descriptor tables: element-wise add / sub /
-// plaintext product / tensor product, segmented accumulation, exact rescale,
-// the evaluation-domain automorphism and hybrid key switching (ModUp, key
-// inner product, ModDown; Han-Ki 2020 with fast base conversion).
+// plaintext product / tensor product, segmented accumulation, integer-to-RNS
+// conversion and the evaluation-domain automorphism. (Key switching and the
+// rescale run as fused NTT passes in ks.cu.)
 //
 // Launch shape of the element-wise kernels: blockIdx.y selects the item (a
 // table entry), the x dimension walks (component, limb, coefficient pair) with
@@ -338,59 +338,6 @@ __global__ void automorphism_kernel(u64* out, const u64* __restrict__ in, int li
     }
 }
 
-// ---------------------------------------------------------------- rescale
-
-__global__ void gather_last_kernel(u64* last, const UnItem* __restrict__ tab, int items, int parts, int level,
-                                   int log_n, size_t pw) {
-    const size_t per = (size_t)parts << log_n;
-    ITEM_LOOP(items) {
-        int k = (int)(e & ((1u << log_n) - 1));
-        int p = (int)(e >> log_n);
-        last[((size_t)it * parts + p << log_n) + k] = tab[it].in[(size_t)p * pw + ((size_t)level << log_n) + k];
-    }
-}
-
-// spread[row][i][k] = centred(last[row][k]) mod q_i, i < l
-__global__ void rescale_spread_kernel(u64* out, const u64* __restrict__ last, int rows, int l, int log_n,
-                                      const Prime* __restrict__ pr) {
-    const size_t total = (size_t)rows << log_n;
-    const u64 ql = pr[l].q;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int k = (int)(e & ((1u << log_n) - 1));
-        size_t row = e >> log_n;
-        u64 r = last[e];
-        bool neg = r > (ql >> 1);
-        u64 mag = neg ? ql - r : r;
-        for (int i = 0; i < l; i++) {
-            u64 qi = pr[i].q;
-            u64 m = mag % qi;
-            out[((row * l + i) << log_n) + k] = neg ? (m ? qi - m : 0) : m;
-        }
-    }
-}
-
-// out[i] = (in[i] - spread[i]) * q_l^-1 mod q_i
-__global__ void rescale_combine_kernel(const UnItem* __restrict__ tab, const u64* __restrict__ spread, int items,
-                                       int parts, int l, int log_n, size_t pw, const Prime* __restrict__ pr,
-                                       const u64* __restrict__ resc_row) {
-    const size_t per = (size_t)parts * l << (log_n - 1);
-    ITEM_LOOP(items) {
-        const UnItem t = tab[it];
-        PIdx x = pidx(e, log_n - 1, l);
-        size_t o = off2(x.part, x.limb, log_n, pw);
-        const u64 q = pr[x.limb].q;
-        const u64 w = resc_row[2 * x.limb], ws = resc_row[2 * x.limb + 1];
-        ulonglong2 a = reinterpret_cast<const ulonglong2*>(t.in + o)[x.k2];
-        size_t row = (size_t)it * parts + x.part;
-        ulonglong2 v = reinterpret_cast<const ulonglong2*>(spread + ((row * l + x.limb) << log_n))[x.k2];
-        ulonglong2 r;
-        r.x = mul_shoup(sub_mod(a.x, v.x, q), w, ws, q);
-        r.y = mul_shoup(sub_mod(a.y, v.y, q), w, ws, q);
-        reinterpret_cast<ulonglong2*>(t.out + o)[x.k2] = r;
-    }
-}
-
 }  // namespace
 
 // ============================================================================ launchers
@@ -480,35 +427,6 @@ void items_sum_acc(Ctx& c, const std::vector<AccTarget>& tg, const std::vector<B
         LaunchScope _ls(c.prof, K_ELEMENTWISE, 8.0 * per * 2 * (contrib.size() + 2.0 * tg.size()), s);
         sum_acc_kernel<<<grid2(per, (int)tg.size()), kThreads, 0, s>>>(dt, dc, (int)tg.size(), parts, limbs, c.log_n,
                                                                    (size_t)(c.L + 1) * c.n, c.d_primes);
-    CK(cudaGetLastError());
-    }
-}
-
-void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s) {
-    if (level < 1) fail(FHE_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 1");
-    if (it.empty()) return;
-    const int n = c.n, items = (int)it.size(), rows = items * parts;
-    const size_t pw = (size_t)(c.L + 1) * n;
-    const UnItem* d = upload(c, it, s);
-    u64* last = c.scratch_u64("resc_last", (size_t)rows * n);
-    u64* spread = c.scratch_u64("resc_spread", (size_t)rows * level * n);
-    {
-        LaunchScope _ls(c.prof, K_RESCALE, 16.0 * rows * n, s);
-        gather_last_kernel<<<grid2((size_t)parts * n, items), kThreads, 0, s>>>(last, d, items, parts, level, c.log_n, pw);
-    CK(cudaGetLastError());
-    }
-    ntt_inverse(c, poly_batch(last, n, 0, rows, 1, level, 1, level), s);
-    {
-        LaunchScope _ls(c.prof, K_RESCALE, 8.0 * rows * n * (1 + level), s);
-        rescale_spread_kernel<<<grid1((size_t)rows * n), kThreads, 0, s>>>(spread, last, rows, level, c.log_n,
-                                                                       c.d_primes);
-    CK(cudaGetLastError());
-    }
-    ntt_forward(c, poly_batch(spread, (size_t)level * n, 0, rows, 1, 0, level), s);
-    {
-        LaunchScope _ls(c.prof, K_RESCALE, 24.0 * rows * level * n, s);
-        rescale_combine_kernel<<<grid2((size_t)parts * level * n / 2, items), kThreads, 0, s>>>(
-        d, spread, items, parts, level, c.log_n, pw, c.d_primes, c.d_resc + (size_t)2 * level * (c.L + 1));
     CK(cudaGetLastError());
     }
 }
