@@ -344,6 +344,9 @@ struct ConstItem {
 void items_mul_const(Ctx& c, const std::vector<ConstItem>& it, int parts, int limbs, cudaStream_t s);
 // rescale components [0, parts) from level l to l-1 (out may alias in)
 void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s);
+// rescale(a (.) b) for each item: a a ciphertext at `level`, b a plaintext (limb stride N); the
+// product is formed inside the rescale's transforms. out may equal a.
+void mul_plain_rescale_items(Ctx& c, const std::vector<BinItem>& it, int level, cudaStream_t s);
 
 // signed int64 coefficients -> residues for limbs [0, limbs): out [items][L+1][N] (limb stride N)
 void k_int_to_rns(const Ctx& c, u64* out, size_t out_item_stride, const i64* in, size_t in_stride,

@@ -43,7 +43,7 @@ namespace {
 using nttc::reduce4;
 using nttc::shoup_lazy;
 
-enum LoadMode { LD_PLAIN = 0, LD_GATHER = 1, LD_CONV = 2, LD_AXPY = 3, LD_CENTRED = 4 };
+enum LoadMode { LD_PLAIN = 0, LD_GATHER = 1, LD_CONV = 2, LD_AXPY = 3, LD_CENTRED = 4, LD_MUL = 5 };
 enum StoreMode { ST_LAZY = 0, ST_LAST = 1, ST_SCALE = 2, ST_COMBINE = 3, ST_COMBINE_RS = 4, ST_RESCALE = 5 };
 
 struct KsRow {
@@ -56,9 +56,10 @@ struct KsRow {
     int cst_stride;  // LD_CONV: words between consecutive source limbs' constant pairs
     int item, half, limb;  // ST_COMBINE(_RS): output item, component and limb
     int pad;
-    const u64* src2;       // LD_AXPY: second source row (null: none); ST_RESCALE: the input limb
+    const u64* src2;       // LD_AXPY / LD_MUL: second source row (LD_AXPY: null = none); ST_RESCALE: the input limb
     const u64* cst2;       // LD_AXPY: Shoup pair of its factor; ST_RESCALE: q_l^-1 mod the row's prime
     u64* out2;             // ST_RESCALE: output row
+    const u64* src3;       // ST_RESCALE: when set, the input limb is src2 (.) src3 (a plaintext product)
 };
 
 // Evaluation slot k holds a(psi^(2 brev(k) + 1)); X -> X^g moves slot k' to slot k
@@ -104,6 +105,7 @@ __device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, co
         const u64 m = nttc::reduce_any(neg ? ql - v : v, P.q, P.one_s);
         return neg ? (m ? P.q - m : 0) : m;
     }
+    if (LOAD == LD_MUL) return mul_mod(r.src[k], r.src2[k], pr[r.prime]);
     if (LOAD == LD_AXPY) {  // src + cst2 * src2 (both reduced)
         const u64 p = pr[r.prime].q;
         u64 v = r.src[k];
@@ -134,7 +136,7 @@ __device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, co
 }
 
 template <bool INV, int STORE>
-__device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, u64 q, u64 one_s,
+__device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, const Prime* __restrict__ prow, u64 q, u64 one_s,
                                            const u64* __restrict__ ninv, const CombineArgs& ca, int log_n) {
     if (STORE == ST_LAZY) {
         r.dst[k] = v;
@@ -151,7 +153,8 @@ __device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, u64 
     }
     if (STORE == ST_RESCALE) {  // forward: out = (x - [x_l]) q_l^-1 with the transformed [x_l] in v
         const u64 t = nttc::reduce_any(v, q, one_s);
-        r.out2[k] = mul_shoup(sub_mod(r.src2[k], t, q), r.cst2[0], r.cst2[1], q);
+        const u64 x = r.src3 ? mul_mod(r.src2[k], r.src3[k], *prow) : r.src2[k];
+        r.out2[k] = mul_shoup(sub_mod(x, t, q), r.cst2[0], r.cst2[1], q);
         return;
     }
     if (STORE == ST_SCALE) {  // inverse transforms only: times the row's constant instead of N^-1
@@ -219,8 +222,8 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
         const u64 one_s = primes[r.prime].one_s;
 #pragma unroll
         for (int u = 0; u < 8; u++)
-            store_elem<INV, STORE>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(lb, g, u) << log_n2), v[u], q,
-                                   one_s, ninv, ca, log_n);
+            store_elem<INV, STORE>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(lb, g, u) << log_n2), v[u], primes + r.prime,
+                                   q, one_s, ninv, ca, log_n);
         return;
     }
     if (PASS == 0) {
@@ -244,13 +247,15 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
 #pragma unroll 4
         for (int e = tid; e < R * M; e += T) {
             int x = e / R, c = e % R;
-            store_elem<INV, STORE>(r, (size_t)(t0 + c) + ((size_t)x << log_n2), sm[x * P + c], q, one_s, ninv, ca, log_n);
+            store_elem<INV, STORE>(r, (size_t)(t0 + c) + ((size_t)x << log_n2), sm[x * P + c], primes + r.prime, q,
+                                   one_s, ninv, ca, log_n);
         }
     } else {
 #pragma unroll 4
         for (int e = tid; e < R * M; e += T) {
             int x = e & (M - 1), c = e >> LOGM;
-            store_elem<INV, STORE>(r, ((size_t)(t0 + c) << LOGM) + x, sm[x * P + c], q, one_s, ninv, ca, log_n);
+            store_elem<INV, STORE>(r, ((size_t)(t0 + c) << LOGM) + x, sm[x * P + c], primes + r.prime, q, one_s,
+                                   ninv, ca, log_n);
         }
     }
 }
@@ -688,29 +693,34 @@ void keyswitch_items(Ctx& c, const std::vector<KsItem>& all, int level, cudaStre
     ks_run(c, all, level, nullptr, s);
 }
 
+namespace {
+
 // Exact centred rescale of `parts` components per item (level -> level - 1), in two transforms:
 // the inverse NTT of the last limb (scaled by N^-1), then for every limb i < level a forward NTT
 // whose load forms [x_level]_centred mod q_i and whose store writes (x_i - that) q_level^-1.
 // out may equal in.
-void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s) {
-    if (level < 1) fail(FHE_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 1");
-    if (it.empty()) return;
+// in_t (component p, limb i) is in[t] + p pw + i N; with pt[t] set, the rescaled value is that of
+// in (.) pt (pt: one polynomial, limb stride N, shared by both components).
+void rescale_run(Ctx& c, const std::vector<const u64*>& in, const std::vector<const u64*>& pt,
+                 const std::vector<u64*>& out, int parts, int level, cudaStream_t s) {
     const int n = c.n, L = c.L;
     const size_t pw = (size_t)(L + 1) * n;
     const int max_items = (int)std::max<size_t>(1, ((size_t)2 << 30) / ((size_t)parts * (1 + level) * n * sizeof(u64)));
     const CombineArgs none{nullptr, nullptr, nullptr, 0, nullptr};
-    for (size_t b0 = 0; b0 < it.size(); b0 += max_items) {
-        const int items = (int)std::min<size_t>(max_items, it.size() - b0);
+    const bool prod = !pt.empty();
+    for (size_t b0 = 0; b0 < in.size(); b0 += max_items) {
+        const int items = (int)std::min<size_t>(max_items, in.size() - b0);
         const int rows = items * parts;
         u64* last = c.scratch_u64("resc_last", (size_t)rows * n);
         u64* work = c.scratch_u64("resc_work", (size_t)rows * level * n);
         std::vector<KsRow> ra, rb;
         for (int t = 0; t < items; t++)
             for (int p = 0; p < parts; p++) {
-                const UnItem& x = it[b0 + t];
+                const u64* x = in[b0 + t] + (size_t)p * pw;
                 KsRow r{};
                 r.dst = last + ((size_t)t * parts + p) * n;
-                r.src = x.in + (size_t)p * pw + (size_t)level * n;
+                r.src = x + (size_t)level * n;
+                r.src2 = prod ? pt[b0 + t] + (size_t)level * n : nullptr;
                 r.cst = c.d_ninv + 2 * (size_t)level;
                 r.prime = level;
                 r.galois = 1;
@@ -722,18 +732,50 @@ void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, 
                     q.prime = i;
                     q.limb = level;
                     q.galois = 1;
-                    q.src2 = x.in + (size_t)p * pw + (size_t)i * n;
+                    q.src2 = x + (size_t)i * n;
+                    q.src3 = prod ? pt[b0 + t] + (size_t)i * n : nullptr;
                     q.cst2 = c.d_resc + 2 * ((size_t)level * (L + 1) + i);
-                    q.out2 = x.out + (size_t)p * pw + (size_t)i * n;
+                    q.out2 = out[b0 + t] + (size_t)p * pw + (size_t)i * n;
                     rb.push_back(q);
                 }
             }
         const KsRow* d_ra = c.arena.push_vec(ra, s);
-        ks_transform<true, LD_GATHER, ST_SCALE>(c, d_ra, (int)ra.size(), none, K_NTT_INV, 16.0 * ra.size() * n, s);
+        if (prod)
+            ks_transform<true, LD_MUL, ST_SCALE>(c, d_ra, (int)ra.size(), none, K_NTT_INV, 16.0 * ra.size() * n, s);
+        else
+            ks_transform<true, LD_GATHER, ST_SCALE>(c, d_ra, (int)ra.size(), none, K_NTT_INV, 16.0 * ra.size() * n, s);
         const KsRow* d_rb = c.arena.push_vec(rb, s);
         ks_transform<false, LD_CENTRED, ST_RESCALE>(c, d_rb, (int)rb.size(), none, K_NTT_FWD, 16.0 * rb.size() * n, s);
     }
 }
+
+}  // namespace
+
+void mul_plain_rescale_items(Ctx& c, const std::vector<BinItem>& it, int level, cudaStream_t s) {
+    if (level < 1) fail(FHE_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 1");
+    if (it.empty()) return;
+    std::vector<const u64*> in, pt;
+    std::vector<u64*> out;
+    for (const BinItem& x : it) {
+        in.push_back(x.a);
+        pt.push_back(x.b);
+        out.push_back(x.out);
+    }
+    rescale_run(c, in, pt, out, 2, level, s);
+}
+
+void items_rescale(Ctx& c, const std::vector<UnItem>& it, int parts, int level, cudaStream_t s) {
+    if (level < 1) fail(FHE_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 1");
+    if (it.empty()) return;
+    std::vector<const u64*> in;
+    std::vector<u64*> out;
+    for (const UnItem& x : it) {
+        in.push_back(x.in);
+        out.push_back(x.out);
+    }
+    rescale_run(c, in, {}, out, parts, level, s);
+}
+
 
 void rotate_fanout_items(Ctx& c, const std::vector<const u64*>& in, const std::vector<u64*>& out,
                          const std::vector<int>& steps, int level, cudaStream_t s) {

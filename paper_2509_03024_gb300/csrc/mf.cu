@@ -349,17 +349,13 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
                 masks = p.d_mask_eval + (size_t)g0 * lw;
             else
                 materialize_plain(c, p.d_mask + (size_t)g0 * c.n, c.n, cnt, l0 + 1, PTb, lw, s);
-            std::vector<UnItem> resc_m;
             for (int i = 0; i < cnt; i++) {
                 const Group& g = p.groups[gid(i)];
                 const u64* pt = masks + (size_t)i * lw;
                 pm.push_back({Vr(p.group_node[gid(i)]), pt, Mb + (size_t)i * w});
                 pm.push_back({UD(g.b), pt, MUb + (size_t)i * w});
-                resc_m.push_back({Mb + (size_t)i * w, Mb + (size_t)i * w});
-                resc_m.push_back({MUb + (size_t)i * w, MUb + (size_t)i * w});
             }
-            items_mul_plain(c, pm, 2, l0 + 1, s);
-            items_rescale(c, resc_m, 2, l0, s);
+            mul_plain_rescale_items(c, pm, l0, s);
             // accumulate the tensors: TU_b += E (x) M, TV[node] += E (x) MU
             std::map<int, std::vector<int>> by_b, by_node;
             for (int i = 0; i < cnt; i++) {
@@ -440,14 +436,11 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
             u64* PT = p.d_chunk;
             materialize_plain(c, p.d_reg + (size_t)(p.n_ub + cb0) * c.n, c.n, cb1 - cb0, l0 + 1, PT, lw, s);
             std::vector<BinItem> pm, fin;
-            std::vector<UnItem> rs;
             for (int cb = cb0; cb < cb1; cb++) {
                 pm.push_back({VD(cb), PT + (size_t)(cb - cb0) * lw, BaseV + (size_t)cb * w});
-                rs.push_back({BaseV + (size_t)cb * w, BaseV + (size_t)cb * w});
                 fin.push_back({BaseV + (size_t)cb * w, FV + (size_t)cb * w, VD(cb)});
             }
-            items_mul_plain(c, pm, 2, l0 + 1, s);
-            items_rescale(c, rs, 2, l0, s);
+            mul_plain_rescale_items(c, pm, l0, s);
             items_add(c, fin, 2, l2 + 1, false, s);
         }
     }
@@ -471,14 +464,11 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
         u64* PT = p.d_chunk;
         materialize_plain(c, p.d_reg, c.n, p.n_ub, l0 + 1, PT, lw, s);
         std::vector<BinItem> pm, fin;
-        std::vector<UnItem> rs;
         for (int b = 0; b < p.n_ub; b++) {
             pm.push_back({UD(b), PT + (size_t)b * lw, BaseU + (size_t)b * w});
-            rs.push_back({BaseU + (size_t)b * w, BaseU + (size_t)b * w});
             fin.push_back({BaseU + (size_t)b * w, FU + (size_t)b * w, UD(b)});
         }
-        items_mul_plain(c, pm, 2, l0 + 1, s);
-        items_rescale(c, rs, 2, l0, s);
+        mul_plain_rescale_items(c, pm, l0, s);
         items_add(c, fin, 2, l2 + 1, false, s);
     }
 }
@@ -503,8 +493,7 @@ void run_predict(const fhe_mf_plan& p, const u64* U, const u64* V, int level, in
     materialize_plain(c, mcoef, c.n, 1, level + 1, pt, lw, s);
     u64* X = c.scratch_u64("pred_x", 2 * w);
     u64* Y = X + w;
-    items_mul_plain(c, {BinItem{U + (size_t)b * w, pt, X}}, 2, level + 1, s);
-    items_rescale(c, {UnItem{X, X}}, 2, level, s);
+    mul_plain_rescale_items(c, {BinItem{U + (size_t)b * w, pt, X}}, level, s);
     for (int t = 0; t < p.beta; t++) {
         rotate_items(c, {X}, {Y}, {(1 << t) * p.w}, level - 1, true, s);
         std::swap(X, Y);

@@ -124,18 +124,15 @@ void fold_in_step(fhe_server& sv, const std::vector<Slot*>& group, int level, cu
     inner_products(sv, pairs, level, s);
     // E = R - S, MV = rescale(V (.) mask)
     std::vector<BinItem> esub, pm;
-    std::vector<UnItem> rs;
     for (Slot* sl : group)  // all of a slot's mask encodings at once (PT of batch c at stride kPerBatch lw)
         materialize_plain(c, sl->mask, c.n, sv.n_vb, level + 1, work_of(sv, *sl, 0).PT, kPerBatch * lw, s);
     for (auto& pr : pairs) {
         SlotWork wk = work_of(sv, *pr.first, pr.second);
         esub.push_back({pr.first->R + (size_t)pr.second * w, wk.S, wk.E});
         pm.push_back({sv.V + (size_t)pr.second * w, wk.PT, wk.MV});
-        rs.push_back({wk.MV, wk.MV});
     }
     items_add(c, esub, 2, level, true, s);
-    items_mul_plain(c, pm, 2, level + 1, s);
-    items_rescale(c, rs, 2, level, s);
+    mul_plain_rescale_items(c, pm, level, s);
     // T = sum_c E (x) MV
     std::vector<AccTarget> tg;
     std::vector<BinItem> cb;
