@@ -192,13 +192,18 @@ __device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, cons
 }
 
 // One NTT pass over a row table (PASS 0: column tiles / single pass; PASS 1: row tiles).
-template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE>
-__global__ void __launch_bounds__(R * (1 << LOGM) / 8, (1024 / (R * (1 << LOGM) / 8)) > 0 ? 1024 / (R * (1 << LOGM) / 8) : 1)
+constexpr int ks_min_blocks(int rb, int threads) {
+    return (rb == 3 ? 1024 : 768) / threads > 0 ? (rb == 3 ? 1024 : 768) / threads : 1;
+}
+
+template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB>
+__global__ void __launch_bounds__(R * (1 << LOGM) / (1 << RB), ks_min_blocks(RB, R * (1 << LOGM) / (1 << RB)))
 ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, const ulonglong2* __restrict__ tw,
               const u64* __restrict__ ninv, CombineArgs ca, int log_n) {
     constexpr int M = 1 << LOGM;
     constexpr int P = R == 1 ? 1 : R + 1;
-    constexpr int T = R * M / 8;
+    constexpr int V = 1 << RB;
+    constexpr int T = R * M / V;
     extern __shared__ u64 sm[];
     const int tid = threadIdx.x;
     const KsRow r = rows[blockIdx.x];
@@ -208,21 +213,23 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
     const int S1 = log_n - log_n2;
     const int t0 = blockIdx.y * R;
     if (PASS == 0 && R > 1) {
-        // column tiles: the first and last radix-8 blocks read and write global memory directly
-        constexpr int NB = (LOGM + 2) / 3;
+        // column tiles: the first and last register blocks read and write global memory directly
+        constexpr int NB = (LOGM + RB - 1) / RB;
         const int qq = tid % R, g = tid / R;
         const int fb = INV ? NB - 1 : 0, lb = INV ? 0 : NB - 1;
-        u64 v[8];
+        u64 v[V];
 #pragma unroll
-        for (int u = 0; u < 8; u++)
-            v[u] = load_elem<LOAD>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(fb, g, u) << log_n2), log_n,
-                                   primes);
-        if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false, true, true>(sm, W, q, S1, t0, v);
-        else nttc::tile_stages<LOGM, R, INV, PASS, true, true, true>(sm, W, q, S1, t0, v);
+        for (int u = 0; u < V; u++)
+            v[u] = load_elem<LOAD>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM, RB>(fb, g, u) << log_n2),
+                                   log_n, primes);
+        if (!INV && q < ((u64)1 << 58))
+            nttc::tile_stages<LOGM, R, INV, PASS, false, true, true, RB>(sm, W, q, S1, t0, v);
+        else
+            nttc::tile_stages<LOGM, R, INV, PASS, true, true, true, RB>(sm, W, q, S1, t0, v);
         const u64 one_s = primes[r.prime].one_s;
 #pragma unroll
-        for (int u = 0; u < 8; u++)
-            store_elem<INV, STORE>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(lb, g, u) << log_n2), v[u], primes + r.prime,
+        for (int u = 0; u < V; u++)
+            store_elem<INV, STORE>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM, RB>(lb, g, u) << log_n2), v[u], primes + r.prime,
                                    q, one_s, ninv, ca, log_n);
         return;
     }
@@ -240,8 +247,8 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
         }
     }
     __syncthreads();
-    if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false>(sm, W, q, S1, t0);
-    else nttc::tile_stages<LOGM, R, INV, PASS, true>(sm, W, q, S1, t0);
+    if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false, RB>(sm, W, q, S1, t0);
+    else nttc::tile_stages<LOGM, R, INV, PASS, true, RB>(sm, W, q, S1, t0);
     const u64 one_s = primes[r.prime].one_s;
     if (PASS == 0) {
 #pragma unroll 4
@@ -260,18 +267,20 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
     }
 }
 
-template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE>
+// The fused passes keep radix-8 register blocks: with 16 residues per thread their load and
+// store stages run out of registers (measured slower, unlike the plain transform).
+template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB = 3>
 void launch_pass(const Ctx& c, const KsRow* rows, int n_rows, int tiles, const CombineArgs& ca, int cls, double bytes,
                  cudaStream_t s) {
     if (n_rows == 0) return;
-    constexpr int T = R * (1 << LOGM) / 8;
+    constexpr int T = R * (1 << LOGM) / (1 << RB);
     constexpr size_t smem = sizeof(u64) * (1 << LOGM) * (R == 1 ? 1 : R + 1);
     const ulonglong2* tw = PASS == 1 ? (INV ? c.d_itw2 : c.d_tw2) : (INV ? c.d_itw : c.d_tw);
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE>,
+        CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE, RB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchScope _ls(c.prof, cls, bytes, s);
-    ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE><<<dim3(n_rows, tiles), T, smem, s>>>(rows, c.d_primes, tw, c.d_ninv,
+    ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE, RB><<<dim3(n_rows, tiles), T, smem, s>>>(rows, c.d_primes, tw, c.d_ninv,
                                                                                         ca, c.log_n);
     CK(cudaGetLastError());
 }
@@ -285,7 +294,7 @@ void ks_transform(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs
     switch (c.log_n) {
 #define SINGLE(LG)                                                                        \
     case LG:                                                                              \
-        launch_pass<LG, 1, INV, 0, LOAD, STORE>(c, rows, n_rows, 1, ca, cls, bytes, s);   \
+        launch_pass<LG, 1, INV, 0, LOAD, STORE, 3>(c, rows, n_rows, 1, ca, cls, bytes, s); \
         return;
         SINGLE(9)
         SINGLE(10)

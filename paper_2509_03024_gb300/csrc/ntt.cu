@@ -51,13 +51,20 @@ __device__ __forceinline__ RowPtr row_ptr(const PolyBatch& pb, int row, int log_
 //         with LOGM = log N and R = 1 this is the whole single-pass transform.
 // PASS 1: row transforms (stages [S1, log N)), tile = R consecutive rows of M = N2 points.
 // LAST: this kernel performs the final stages (reduce to [0, q); inverse: times N^-1).
-template <int LOGM, int R, bool INV, int PASS, bool LAST>
-__global__ void __launch_bounds__(R * (1 << LOGM) / 8, (1024 / (R * (1 << LOGM) / 8)) > 0 ? 1024 / (R * (1 << LOGM) / 8) : 1)
+// Each thread owns 2^RB residues (RB = 3: radix-8 register blocks, RB = 4: radix-16).
+template <int LOGM, int RB>
+constexpr int tile_min_blocks(int threads) {
+    return (RB == 3 ? 1024 : 768) / threads > 0 ? (RB == 3 ? 1024 : 768) / threads : 1;
+}
+
+template <int LOGM, int R, bool INV, int PASS, bool LAST, int RB = 3>
+__global__ void __launch_bounds__(R * (1 << LOGM) / (1 << RB), tile_min_blocks<LOGM, RB>(R * (1 << LOGM) / (1 << RB)))
 ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2* __restrict__ tw,
                 const u64* __restrict__ ninv, int log_n) {
     constexpr int M = 1 << LOGM;
     constexpr int P = R == 1 ? 1 : R + 1;
-    constexpr int T = R * M / 8;
+    constexpr int V = 1 << RB;
+    constexpr int T = R * M / V;
     extern __shared__ u64 sm[];
     const int tid = threadIdx.x;
     const RowPtr rp = row_ptr(pb, blockIdx.x, log_n);
@@ -69,20 +76,22 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     const u64 ni = ninv[2 * rp.prime], nis = ninv[2 * rp.prime + 1];
 
     if (PASS == 0 && R > 1) {
-        // column tiles: the first and last radix-8 blocks read and write global memory directly
+        // column tiles: the first and last register blocks read and write global memory directly
         // (a warp covers 16 consecutive columns of two rows per access)
-        constexpr int NB = (LOGM + 2) / 3;
+        constexpr int NB = (LOGM + RB - 1) / RB;
         const int qq = tid % R, g = tid / R;
         const int fb = INV ? NB - 1 : 0, lb = INV ? 0 : NB - 1;
-        u64 v[8];
+        u64 v[V];
 #pragma unroll
-        for (int u = 0; u < 8; u++)
-            v[u] = rp.p[(size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(fb, g, u) << log_n2)];
-        if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false, true, true>(sm, W, q, S1, t0, v);
-        else nttc::tile_stages<LOGM, R, INV, PASS, true, true, true>(sm, W, q, S1, t0, v);
+        for (int u = 0; u < V; u++)
+            v[u] = rp.p[(size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM, RB>(fb, g, u) << log_n2)];
+        if (!INV && q < ((u64)1 << 58))
+            nttc::tile_stages<LOGM, R, INV, PASS, false, true, true, RB>(sm, W, q, S1, t0, v);
+        else
+            nttc::tile_stages<LOGM, R, INV, PASS, true, true, true, RB>(sm, W, q, S1, t0, v);
         const u64 one_s = primes[rp.prime].one_s;
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
+        for (int u = 0; u < V; u++) {
             u64 val = v[u];
             if (LAST) {
                 if (INV) {
@@ -92,7 +101,7 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
                     val = nttc::reduce_any(val, q, one_s);
                 }
             }
-            rp.p[(size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM>(lb, g, u) << log_n2)] = val;
+            rp.p[(size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM, RB>(lb, g, u) << log_n2)] = val;
         }
         return;
     }
@@ -114,8 +123,8 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     __syncthreads();
 
     // forward transforms of primes below 2^58 skip the per-butterfly reduction (values < 33 q)
-    if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false>(sm, W, q, S1, t0);
-    else nttc::tile_stages<LOGM, R, INV, PASS, true>(sm, W, q, S1, t0);
+    if (!INV && q < ((u64)1 << 58)) nttc::tile_stages<LOGM, R, INV, PASS, false, RB>(sm, W, q, S1, t0);
+    else nttc::tile_stages<LOGM, R, INV, PASS, true, RB>(sm, W, q, S1, t0);
     const u64 one_s = primes[rp.prime].one_s;
 
     // store (coalesced)
@@ -152,17 +161,17 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     }
 }
 
-template <int LOGM, int R, bool INV, int PASS, bool LAST>
+template <int LOGM, int R, bool INV, int PASS, bool LAST, int RB = nttc::kTileRB>
 void launch_tile(const Ctx& c, const PolyBatch& pb, int tiles, cudaStream_t s, double bytes) {
-    constexpr int T = R * (1 << LOGM) / 8;
+    constexpr int T = R * (1 << LOGM) / (1 << RB);
     constexpr size_t smem = sizeof(u64) * (1 << LOGM) * (R == 1 ? 1 : R + 1);
     // row passes read the transposed [stage][group][row] tables
     const ulonglong2* tw = PASS == 1 ? (INV ? c.d_itw2 : c.d_tw2) : (INV ? c.d_itw : c.d_tw);
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(ntt_tile_kernel<LOGM, R, INV, PASS, LAST>,
+        CK(cudaFuncSetAttribute(ntt_tile_kernel<LOGM, R, INV, PASS, LAST, RB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchScope _ls(c.prof, INV ? K_NTT_INV : K_NTT_FWD, bytes, s);
-    ntt_tile_kernel<LOGM, R, INV, PASS, LAST><<<dim3(pb.rows(), tiles), T, smem, s>>>(pb, c.d_primes, tw,
+    ntt_tile_kernel<LOGM, R, INV, PASS, LAST, RB><<<dim3(pb.rows(), tiles), T, smem, s>>>(pb, c.d_primes, tw,
                                                                                       c.d_ninv, c.log_n);
     CK(cudaGetLastError());
 }
@@ -173,11 +182,11 @@ void run_ntt(const Ctx& c, const PolyBatch& pb, cudaStream_t s) {
     if (rows == 0) return;
     const double bytes = 16.0 * rows * ((size_t)1 << c.log_n);
     switch (c.log_n) {
-        case 9: launch_tile<9, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
-        case 10: launch_tile<10, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
-        case 11: launch_tile<11, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
-        case 12: launch_tile<12, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
-        case 13: launch_tile<13, 1, INV, 0, true>(c, pb, 1, s, bytes); return;
+        case 9: launch_tile<9, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 10: launch_tile<10, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 11: launch_tile<11, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 12: launch_tile<12, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 13: launch_tile<13, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
         case 14:  // 128 x 128
             if (!INV) {
                 launch_tile<7, 16, false, 0, false>(c, pb, 128 / 16, s, bytes);
