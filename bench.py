@@ -298,6 +298,17 @@ def run_served(args, dev):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def job_throughput(elapsed_ms, ratings, steps, world, dist, device):
+    """Whole-job rate: every rank processed `ratings` x `steps` (weak scaling, independent
+    replicas); the job time is the slowest rank's (max over ranks). Returns (max ms, ratings/s)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, world * ratings * steps / (elapsed_ms / 1e3)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2509_03024_gb300 import build as B
@@ -352,12 +363,7 @@ def run_gpu(args, rank, world, local_rank):
     stats = ctx.profile_end()
     clocks = stop_clocks(clk, clk_path)
     barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * ratings * args.steps / (elapsed_ms / 1e3)
+    elapsed_ms, value = job_throughput(ev0.elapsed_time(ev1), ratings, args.steps, world, dist, f"cuda:{dev}")
 
     # decrypted accuracy of the last step against the FP64 epoch (sanity, not timed)
     from oracle import mf as omf
@@ -398,13 +404,9 @@ def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world
             oV.copy_(VD, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms, e2e_value = job_throughput(e0.elapsed_time(e1), ratings, args.e2e_steps, world, dist, f"cuda:{dev}")
     bytes_h2d = (hU.numel() + hV.numel()) * 8
-    return {"value": world * ratings * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+    return {"value": e2e_value, "unit": UNIT,
             "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d}
 
 
