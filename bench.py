@@ -10,9 +10,14 @@ scale 2^50. One step = one encrypted SGD epoch (lr 0.005, lambda 0.02) over the
 resident copy at the start of each step; the chain holds three epochs).
 
 Metric: training ratings processed per second (whole job over all ranks).
-Multi-GPU runs are independent replicas (one per rank, weak scaling).
+Multi-GPU runs are independent replicas (one per rank, weak scaling). The same
+line carries the served section (continuous batching of fold-in + predict
+requests against one-at-a-time execution, p50/p99 latency), the roofline of
+the dominant kernel class, the end-to-end rate with host copies, the
+communication report and the oracle's CPU rate.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--workload paper|large] [--served-rate R] [--served-sweep R1,R2,...]
 """
 from __future__ import annotations
 
@@ -31,9 +36,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 METRIC = "encrypted MF ratings/sec, served vs one-by-one on 1 GB300; p50/p99 latency"
-# integer-ALU ceiling of the NTT butterfly: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz issue slots,
-# at 20 32-bit instructions per lazy 64-bit Shoup butterfly (product high half 5, two low halves 6,
-# subtraction 2, range reduction 4, sum and difference 3)
+# nominal integer-issue ceiling of the NTT butterfly, reported beside the measured one: 152 SMs x 4
+# schedulers x 32 lanes x 2.07 GHz issue slots at 20 32-bit instructions per lazy 64-bit Shoup
+# butterfly (product high half 5, two low halves 6, subtraction 2, range reduction 4, sum and
+# difference 3), assuming full issue
 ALU_PEAK_GBFLY = 152 * 128 * 2.07 / 20.0
 # DRAM bytes per limb row of a forward NTT pass at N = 2^15, from one ncu capture of the fused
 # ModUp passes (64 rotations at level 7, 2048 rows per pass): (614 MB + 1020 MB) / 2 passes / 2048
