@@ -75,6 +75,8 @@ def test_plan_groups_and_factor_encryption_bit_exact():
     ("t10", 150, 70, 0.05, 2, 7),         # several user batches (B = 128), ragged chunks of 7 groups
     ("t10", 60, 200, 0.04, 3, None),      # k < kp, several item batches
     ("t11a2", 90, 50, 0.06, 10, 5),       # k = 10 (kp = 16), alpha = 2, dnum > 1
+    ("t10", 30, 20, 0.1, 1, None),        # k = 1: no rotate-and-sum at all
+    ("t10", 12, 10, 0.2, 17, None),       # k = 17 (kp = 32): rotate-and-adds instead of hoisting, B = 8
 ])
 def test_epoch_bit_exact_and_fp64(preset, n, m, density, k, chunk):
     csr, U, V = _small_case(seed=n + m, n=n, m=m, density=density, k=k)
@@ -246,3 +248,30 @@ def test_checkpoint_resume_bit_identical(tmp_path):
     UDb, VDb, lb, _, rb = T.run(ctx, plan, U, V, 3, lr, lam, state=st)
     assert (la, ra) == (lb, rb) == (ctx.top - 2, 1)
     assert torch.equal(UDa, UDb) and torch.equal(VDa, VDb)
+
+
+def test_paper_scale_epoch_properties():
+    """The paper-scale epoch as the bench runs it (943 x 1682, 89,893 training ratings, k = 10,
+    N = 2^15): every output residue is reduced below its prime, and the decrypted factors are
+    within 1e-3 of the FP64 epoch with a held-out RMSE gap below 1e-4."""
+    train, test, U, V = W.paper_workload(seed=2)
+    ctx = gpu_ctx("paper", SEED)
+    ctx.add_rotation_keys(ctx.mf_rotation_steps(10))
+    plan = capi.MfPlan(ctx, train.n, train.m, 10, train.row_ptr, train.col_idx, train.vals)
+    UD, VD = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
+    plan.encrypt_factors(0, U, UD)
+    plan.encrypt_factors(1, V, VD)
+    lr, lam = 0.005, 0.02
+    plan.sgd_epoch(UD, VD, ctx.top, lr, lam)
+    lv = ctx.top - 2
+    primes = torch.tensor([int(q) for q in ctx.primes[: lv + 1]], dtype=torch.int64, device=UD.device)
+    for buf, cnt in ((UD, plan.n_ub), (VD, plan.n_vb)):
+        x = buf.view(cnt, 2, ctx.top + 1, ctx.n)[:, :, : lv + 1, :]
+        assert bool((x >= 0).all()) and bool((x < primes.view(1, 1, -1, 1)).all())
+    rows, cols, vals = train.triples()
+    U1, V1 = mf.mf_epoch_fp64(U, V, rows, cols, vals, lr, lam)
+    Ud = plan.decrypt_factors(0, UD, lv, train.n)
+    Vd = plan.decrypt_factors(1, VD, lv, train.m)
+    assert max(np.abs(Ud - U1).max(), np.abs(Vd - V1).max()) < 1e-3
+    trow, tcol, tval = test.triples()
+    assert abs(mf.rmse(Ud, Vd, trow, tcol, tval) - mf.rmse(U1, V1, trow, tcol, tval)) < 1e-4
