@@ -275,3 +275,23 @@ def test_paper_scale_epoch_properties():
     assert max(np.abs(Ud - U1).max(), np.abs(Vd - V1).max()) < 1e-3
     trow, tcol, tval = test.triples()
     assert abs(mf.rmse(Ud, Vd, trow, tcol, tval) - mf.rmse(U1, V1, trow, tcol, tval)) < 1e-4
+
+
+def test_epoch_of_an_empty_matrix_keeps_the_factors():
+    """No ratings: no groups, no rating bins; the epoch only rescales by reg = 1, so the decrypted
+    factors come back unchanged (and every residue stays reduced)."""
+    ctx = gpu_ctx("t10", SEED)
+    k = 3
+    ctx.add_rotation_keys(ctx.mf_rotation_steps(k))
+    plan = capi.MfPlan(ctx, 20, 15, k, np.zeros(21, dtype=np.int64), np.zeros(0, dtype=np.int32),
+                       np.zeros(0, dtype=np.float64))
+    assert plan.info.n_groups == 0 and plan.info.n_bins == 0
+    rng = np.random.default_rng(1)
+    U, V = rng.normal(0, 0.1, (20, k)), rng.normal(0, 0.1, (15, k))
+    UD, VD = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
+    plan.encrypt_factors(0, U, UD)
+    plan.encrypt_factors(1, V, VD)
+    plan.sgd_epoch(UD, VD, ctx.top, 0.01, 0.02)
+    lv = ctx.top - 2
+    assert np.abs(plan.decrypt_factors(0, UD, lv, 20) - U).max() < 1e-6
+    assert np.abs(plan.decrypt_factors(1, VD, lv, 15) - V).max() < 1e-6
