@@ -41,9 +41,10 @@ METRIC = "encrypted MF ratings/sec, served vs one-by-one on 1 GB300; p50/p99 lat
 # butterfly (product high half 5, two low halves 6, subtraction 2, range reduction 4, sum and
 # difference 3), assuming full issue
 ALU_PEAK_GBFLY = 152 * 128 * 2.07 / 20.0
-# DRAM bytes per limb row of a forward NTT pass at N = 2^15, from one ncu capture of the fused
-# ModUp passes (64 rotations at level 7, 2048 rows per pass): (614 MB + 1020 MB) / 2 passes / 2048
-NCU_FWD_DRAM_BYTES_PER_ROW = (614.0e6 + 1020.0e6) / 2 / 2048
+# DRAM bytes per limb row of a forward NTT pass at N = 2^15, from the ncu capture of the fused
+# ModUp passes of the current kernels (64 rotations at level 7, 2048 rows per pass; summary in
+# profiles/ks_modup_paper_N2e15.md): (615 MB + 1020 MB) / 2 passes / 2048 rows
+NCU_FWD_DRAM_BYTES_PER_ROW = (615.0e6 + 1020.0e6) / 2 / 2048
 UNIT = "ratings/s"
 SEED = 20250903
 LR, LAM, K_RANK = 0.005, 0.02, 10
