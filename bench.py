@@ -41,9 +41,9 @@ METRIC = "encrypted MF ratings/sec, served vs one-by-one on 1 GB300; p50/p99 lat
 # butterfly (product high half 5, two low halves 6, subtraction 2, range reduction 4, sum and
 # difference 3), assuming full issue
 ALU_PEAK_GBFLY = 152 * 128 * 2.07 / 20.0
-# DRAM bytes per limb row of a forward NTT pass at N = 2^15, from the ncu capture of the fused
-# ModUp passes of the current kernels (64 rotations at level 7, 2048 rows per pass; summary in
-# profiles/ks_modup_paper_N2e15.md): (615 MB + 1020 MB) / 2 passes / 2048 rows
+# DRAM bytes per limb row of a forward NTT pass at N = 2^15, from the ncu capture (dram__bytes_read
+# + write) of the fused ModUp passes of the current kernels (64 rotations at level 7, 2048 rows per
+# pass): (615 MB + 1020 MB) / 2 passes / 2048 rows
 NCU_FWD_DRAM_BYTES_PER_ROW = (615.0e6 + 1020.0e6) / 2 / 2048
 UNIT = "ratings/s"
 SEED = 20250903
