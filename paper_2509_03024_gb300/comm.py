@@ -1,8 +1,9 @@
 """Communication between the parties of the encrypted MF protocol (Sec. III-B), in ciphertexts
 and bytes.
 
-The key holder (CSP) generates the keys and publishes the public and evaluation keys; the data
-owners' ratings and the initial factors reach the recommender (RS) encrypted; the RS runs the
+The key holder (CSP) generates the keys and publishes the public and evaluation keys; the ratings
+(encrypted by the key holder, c0 and a seed for c1) and the initial factors reach the recommender
+(RS) encrypted; the RS runs the
 epochs on its GPU; when the modulus chain runs out the RS sends U and V to the key holder, which
 returns them re-encrypted at the top level (refresh); at the end the factors go to the key holder
 for decryption. A served request uploads the user's encrypted vector and ratings and downloads the
@@ -30,8 +31,10 @@ def mf_training(n: int, top: int, alpha: int, n_rot_keys: int, n_bins: int, n_ub
     refreshing U and V through the key holder whenever fewer than `levels_per_epoch` levels remain
     (the refreshed factors travel at the level they reached: out at that level, back at the top)."""
     keys = key_bytes(n, top, alpha)
+    # rating bins: encrypted by the key holder with a regenerable c1, so c0 at level top - 1 plus a
+    # 16-byte seed reference per bin travel
     setup = {"public_key": keys["public_key"], "eval_keys": keys["eval_key_each"] * (1 + n_rot_keys),
-             "rating_cts": n_bins, "rating_bytes": n_bins * ct_bytes(n, top),
+             "rating_cts": n_bins, "rating_bytes": n_bins * (top * n * 8 + 16),
              "factor_cts": n_ub + n_vb, "factor_bytes": (n_ub + n_vb) * ct_bytes(n, top)}
     level, refreshes, refresh_bytes = top, 0, 0
     for _ in range(epochs):

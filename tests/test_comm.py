@@ -14,7 +14,7 @@ def test_training_refresh_schedule():
     assert r["refreshes"] == 1 and r["final_level"] == 3
     per_ct = lambda l: 2 * (l + 1) * 16 * 8
     assert r["refresh_bytes"] == 6 * (per_ct(1) + per_ct(7))
-    assert r["setup"]["rating_bytes"] == 10 * per_ct(7)
+    assert r["setup"]["rating_bytes"] == 10 * (7 * 16 * 8 + 16)   # c0 at level 6 and a seed reference
     assert r["final_decrypt_bytes"] == 6 * per_ct(3)
 
 
