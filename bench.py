@@ -14,10 +14,10 @@ Multi-GPU runs are independent replicas (one per rank, weak scaling). The same
 line carries the served section (continuous batching of fold-in + predict
 requests against one-at-a-time execution, p50/p99 latency), the roofline of
 the dominant kernel class, the end-to-end rate with host copies, the
-communication report and the oracle's CPU rate.
+communication report and the oracle's CPU rate (all host cores, and one core alone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                  [--workload paper|large] [--served-rate R] [--served-sweep R1,R2,...]
+                  [--workload paper|large|batched] [--served-rate R] [--served-sweep R1,R2,...]
 """
 from __future__ import annotations
 
@@ -209,8 +209,9 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
 
-def oracle_setup(train, U, V, groups_sampled: int = 1):
-    """Keys, plan and the sampled groups' ciphertexts on the oracle (not timed)."""
+def oracle_setup(train, U, V, groups_sampled: int = 1, only=None):
+    """Keys, plan and the sampled groups' ciphertexts on the oracle (not timed). The sample is
+    `groups_sampled` groups spread evenly over the plan; `only` keeps one of them."""
     from oracle import ckks, mf
     from paper_2509_03024_gb300.workloads import PRESETS
     rows, cols, vals = train.triples()
@@ -221,6 +222,8 @@ def oracle_setup(train, U, V, groups_sampled: int = 1):
     emf = mf.EncryptedMF(he, plan)
     top = he.prm.top
     pick = list(range(0, len(plan.groups), max(1, len(plan.groups) // groups_sampled)))[:groups_sampled]
+    if only is not None:
+        pick = [pick[only]]
     emf.R = [None] * len(plan.bin_batch)
     for t in pick:
         bt = plan.bin_of[t]
@@ -233,34 +236,162 @@ def oracle_setup(train, U, V, groups_sampled: int = 1):
         c = plan.groups[t].c
         if c not in VDc:
             VDc[c] = he.encrypt(mf.pack_factors(V, plan, c), top, mf.V_NONCE_BASE + c)
-    return {"he": he, "plan": plan, "emf": emf, "pick": pick, "UD": UD, "VDc": VDc, "ratings": rows.size}
+    return {"he": he, "plan": plan, "emf": emf, "pick": pick, "UD": UD, "VDc": VDc, "ratings": rows.size,
+            "groups": len(plan.groups), "nodes": sum(len(c) for c in plan.closure)}
 
 
-def oracle_time(st):
-    """Time the oracle (as it stands) on the sampled groups' per-group work (product,
-    relinearise-rescale, rotate-and-sum, masks, tensors) plus one delta-tree rotation, and
-    extrapolate to an epoch: per-group time x groups + per-rotation time x 3 x tree nodes (the
-    rotation, relinearisation and back-rotation of every node). Returns (ratings/s, seconds
-    measured, description)."""
+def oracle_measure(st):
+    """Seconds the oracle (as it stands) takes for one sampled group's work (product,
+    relinearise-rescale, rotate-and-sum, masks, tensors; averaged over the sample) and for one
+    delta-tree rotation."""
     he, plan, emf, pick = st["he"], st["plan"], st["emf"], st["pick"]
     t0 = time.perf_counter()
     for t in pick:
         g = plan.groups[t]
         emf.group_terms(t, st["UD"][g.b], st["VDc"][g.c], LR)   # Vr of delta 0 stands in for the rotated copy
-    t_groups = (time.perf_counter() - t0) / len(pick)
+    t_group = (time.perf_counter() - t0) / len(pick)
     t1 = time.perf_counter()
     he.rotate(next(iter(st["VDc"].values())), plan.w)
-    t_rot = time.perf_counter() - t1
-    nodes = sum(len(c) for c in plan.closure)
-    est = t_groups * len(plan.groups) + t_rot * 3 * nodes
-    desc = (f"oracle on {len(pick)} of {len(plan.groups)} groups + 1 rotation at N=2^15, single thread; "
-            f"epoch extrapolated as groups x {t_groups:.2f} s + {3 * nodes} rotation-sized key switches x "
+    return t_group, time.perf_counter() - t1
+
+
+def oracle_epoch_s(st, t_group, t_rot, cores=1):
+    """Epoch time extrapolated from the sample: groups x t_group + 3 x tree nodes x t_rot (the
+    rotation, relinearisation and back-rotation of every node), spread over `cores` processes
+    (the groups and the nodes of one tree level are independent)."""
+    return (t_group * st["groups"] + t_rot * 3 * st["nodes"]) / cores
+
+
+def oracle_time(st):
+    """One single-thread sample, extrapolated to an epoch. Returns (ratings/s, seconds measured,
+    description)."""
+    t0 = time.perf_counter()
+    t_group, t_rot = oracle_measure(st)
+    est = oracle_epoch_s(st, t_group, t_rot)
+    desc = (f"oracle on {len(st['pick'])} of {st['groups']} groups + 1 rotation at N=2^15, single thread; "
+            f"epoch extrapolated as groups x {t_group:.2f} s + {3 * st['nodes']} rotation-sized key switches x "
             f"{t_rot:.2f} s = {est:.0f} s")
     return st["ratings"] / est, time.perf_counter() - t0, desc
 
 
 def oracle_sample(train, U, V, groups_sampled: int = 1):
     return oracle_time(oracle_setup(train, U, V, groups_sampled))
+
+
+def _oracle_worker(index, n_workers, cmd, res):
+    """One process of the all-core oracle baseline: sets up its own sampled group (group `index` of
+    `n_workers` spread over the plan), then times that group and one rotation whenever told to."""
+    try:
+        train, _, U, V = workload()
+        st = oracle_setup(train, U, V, groups_sampled=n_workers, only=index)
+        res.put(("ready", index, {k: st[k] for k in ("ratings", "groups", "nodes")}))
+        while cmd.get() == "go":
+            res.put(("time", index, oracle_measure(st)))
+    except Exception as e:   # reported to the parent, which then gives up on the all-core figure
+        res.put(("error", index, repr(e)))
+
+
+def oracle_workers(cap: int = 16, bytes_per_worker: float = 2.0 * 2**30) -> int:
+    """Worker processes for the all-core baseline: the CPUs this process may run on, at most
+    `cap`, and no more than available memory allows (about 1.3 GB peak per worker at N = 2^15)."""
+    cpus = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        with open("/sys/fs/cgroup/memory.max") as f:
+            lim = f.read().strip()
+        if lim != "max":
+            avail = min(avail or int(lim), int(lim))
+    except (OSError, ValueError):
+        pass
+    n = min(cpus, cap)
+    if avail is not None:
+        n = min(n, max(1, int(avail // bytes_per_worker)))
+    return max(1, n)
+
+
+class OracleCores:
+    """Independent single-threaded oracle processes (spawned, so no process inherits a CUDA
+    context), one sampled group each, timed concurrently on the host's cores."""
+
+    def __init__(self, n_workers: int, timeout_s: float = 900.0):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.n, self.timeout = n_workers, timeout_s
+        self.cmds = [ctx.Queue() for _ in range(n_workers)]
+        self.res = ctx.Queue()
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        os.environ.update({v: "1" for v in saved})   # one thread per worker
+        try:
+            self.procs = [ctx.Process(target=_oracle_worker, args=(i, n_workers, self.cmds[i], self.res),
+                                      daemon=True) for i in range(n_workers)]
+            for p in self.procs:
+                p.start()
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+        self.info = self._collect(n_workers)[0]
+
+    def _collect(self, count):
+        out = {}
+        while len(out) < count:
+            kind, i, v = self.res.get(timeout=self.timeout)
+            if kind == "error":
+                raise RuntimeError(f"oracle worker {i}: {v}")
+            out[i] = v
+        return out
+
+    def sample(self, workers):
+        """Time the given workers' groups concurrently: {worker: (t_group, t_rot)}."""
+        for i in workers:
+            self.cmds[i].put("go")
+        return self._collect(len(workers))
+
+    def rate(self, times):
+        """Ratings/s of an epoch spread over len(times) processes, from their concurrent samples."""
+        tg = statistics.mean(t[0] for t in times.values())
+        tr = statistics.mean(t[1] for t in times.values())
+        est = oracle_epoch_s(self.info, tg, tr, cores=len(times))
+        return self.info["ratings"] / est, tg, tr, est
+
+    def close(self):
+        for q in self.cmds:
+            q.put("stop")
+        for p in self.procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=10)
+
+
+def oracle_baseline():
+    """The GPU line's cpu_baseline: the oracle on every available core (one process per core, each
+    timing its own group concurrently), with the same sample on one core alone beside it."""
+    t0 = time.perf_counter()
+    pool = OracleCores(oracle_workers())
+    try:
+        one = pool.rate(pool.sample([0]))
+        allc = pool.rate(pool.sample(range(pool.n)))
+    finally:
+        pool.close()
+    G, nodes = pool.info["groups"], pool.info["nodes"]
+    desc = (f"oracle at N=2^15, {pool.n} single-threaded processes at once, each on its own group (of "
+            f"{G}) and one rotation; epoch extrapolated as (groups x {allc[1]:.2f} s + {3 * nodes} "
+            f"rotation-sized key switches x {allc[2]:.2f} s) / {pool.n} = {allc[3]:.0f} s")
+    return {"value": allc[0], "unit": UNIT, "cores": pool.n, "kind": "oracle", "sample": desc,
+            "single_thread": {"value": one[0], "unit": UNIT, "cores": 1,
+                              "sample": f"the same oracle on one group alone: groups x {one[1]:.2f} s + "
+                                        f"{3 * nodes} x {one[2]:.2f} s = {one[3]:.0f} s"},
+            "measured_s": round(time.perf_counter() - t0, 1)}
 
 
 # ----------------------------------------------------------------------------- served workload
@@ -547,9 +678,12 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
     if not args.no_served:
         out["served"] = run_served(args, torch_device_of(ctx))
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "paper":
-        rps, secs, desc = oracle_sample(train, U, V)
-        out["cpu_baseline"] = {"value": rps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                               "measured_s": round(secs, 1)}
+        try:
+            out["cpu_baseline"] = oracle_baseline()
+        except Exception as e:   # the worker pool failed: the single-thread sample in this process
+            rps, secs, desc = oracle_sample(train, U, V)
+            out["cpu_baseline"] = {"value": rps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                   "measured_s": round(secs, 1), "all_cores_error": repr(e)}
     if dist is not None:
         dist.destroy_process_group()
     return out
@@ -559,19 +693,27 @@ def run_reference(args, rank, world):
     """The oracle (CPU, as it stands) on the same workload and metric; rank 0 only."""
     if rank != 0:
         return None
-    train, test, U, V = workload()
-    st = oracle_setup(train, U, V, groups_sampled=1)
-    vals = []
-    for i in range(args.warmup + args.steps):
-        rps, secs, desc = oracle_time(st)
-        if i >= args.warmup:
-            vals.append(rps)
-    v = statistics.median(vals)
+    pool = OracleCores(oracle_workers())
+    vals, per_step = [], []
+    try:
+        for i in range(args.warmup + args.steps):
+            rps, tg, tr, est = pool.rate(pool.sample(range(pool.n)))
+            if i >= args.warmup:
+                vals.append(rps)
+                per_step.append((tg, tr, est))
+    finally:
+        pool.close()
+    v = statistics.median_low(vals)
+    tg, tr, est = per_step[vals.index(v)]
+    desc = (f"each step: {pool.n} single-threaded oracle processes at once at N=2^15, each on its own group "
+            f"(of {pool.info['groups']}) and one rotation; epoch extrapolated as (groups x {tg:.2f} s + "
+            f"{3 * pool.info['nodes']} rotation-sized key switches x {tr:.2f} s) / {pool.n} = {est:.0f} s; "
+            f"value = median over the timed steps")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.n, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

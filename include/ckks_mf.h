@@ -309,7 +309,9 @@ int fhe_mf_sgd_epoch(fhe_ctx* ctx, fhe_mf_plan* plan, uint64_t* U, uint64_t* V, 
 /* Encrypted predicted ratings of one user against every item (a row of
  * R-hat = U V^T, Alg. 1): out receives n_item_batches ciphertexts at level-2;
  * slot d*w of ciphertext c holds <u_user, v_(c*B+d)>. Needs rotation keys
- * for 2^t * w (t < log2 B) and 2^t (t < log2 kp). */
+ * for 2^t * w (t < log2 B) and those of fhe_rotate_sum with this kp (steps
+ * 1..kp-1 for kp <= 16, else the powers of two below kp); every one of them
+ * is in fhe_mf_rotation_steps. */
 int fhe_predict(fhe_ctx* ctx, const fhe_mf_plan* plan, const uint64_t* U, const uint64_t* V,
                 int32_t level, int32_t user, uint64_t* out, void* stream);
 
