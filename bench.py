@@ -611,6 +611,42 @@ def torch_device_of(ctx):
     return ctx.device
 
 
+# the bound of each kernel class: the NTT passes (fused rescales and conversions included) and the
+# key inner products run on the integer pipes, the element-wise classes stream HBM
+CLASS_BOUND = {"ntt_forward": "alu", "ntt_inverse": "alu", "ks_inner": "alu", "tensor": "hbm",
+               "elementwise": "hbm"}
+
+
+def butterflies_per_residue_pass(log_n: int) -> float:
+    """Butterflies per residue in one NTT pass: rings up to 2^13 run the log2(N) stages in one pass,
+    larger rings split them over two passes; a stage does N/2 butterflies."""
+    passes = 1 if log_n <= 13 else 2
+    return log_n / passes / 2.0
+
+
+def class_rooflines(stats, log_n: int, bfly_peak, hbm_peak: float):
+    """Per kernel class: launches, device time, algorithmic bytes, share of the device time and the
+    achieved fraction of the class's roofline: for NTT classes butterflies/s against the measured
+    butterfly rate (each pass reads and writes 16 bytes per residue), and for every class its
+    algorithmic bytes/s against the HBM peak. stats: {name: (launches, device_ms, bytes)}."""
+    total = sum(v[1] for v in stats.values()) or 1.0
+    out = {}
+    for name, (launches, dev_ms, alg_bytes) in stats.items():
+        if not launches:
+            continue
+        rec = {"launches": launches, "device_ms": round(dev_ms, 3), "alg_gb": round(alg_bytes / 1e9, 3),
+               "share": dev_ms / total, "bound": CLASS_BOUND.get(name, "hbm")}
+        if dev_ms > 0:
+            secs = dev_ms / 1e3
+            gbs = alg_bytes / secs / 1e9
+            rec["hbm_view"] = {"achieved_gbs": gbs, "frac": gbs / hbm_peak}
+            if name.startswith("ntt") and bfly_peak:
+                gbfly = alg_bytes / 16.0 * butterflies_per_residue_pass(log_n) / secs / 1e9
+                rec["alu"] = {"achieved_gbfly": gbfly, "frac": gbfly / bfly_peak}
+        out[name] = rec
+    return out
+
+
 def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
            train, U, V, dist):
     # roofline of the dominant kernel class (longest summed device time)
@@ -623,17 +659,18 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
     hbm_view = {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
                 "alg_bytes_per_launch": alg_bytes / launches}
+    # the butterfly rate on register-resident values, measured now on this GPU: the NTT classes' peak
+    bfly_peak = (ctx.probe_butterfly_rate(2000)
+                 if any(k.startswith("ntt") and v[0] for k, v in stats.items()) else None)
     if name.startswith("ntt"):
-        # one NTT pass sweeps every row once (16 bytes per residue) and runs log2(N)/2 butterfly stages,
-        # i.e. log2(N)/4 butterflies per residue
+        # one NTT pass sweeps every row once (16 bytes per residue)
         log_n = ctx.log_n
-        bfly = (alg_bytes / launches) / 16.0 * (log_n / 4.0)
+        bfly = (alg_bytes / launches) / 16.0 * butterflies_per_residue_pass(log_n)
         achieved = bfly / avg_s / 1e9
         rows_per_launch = (alg_bytes / launches) / (16.0 * 2 ** log_n)
         traffic = (NCU_FWD_DRAM_BYTES_PER_ROW * rows_per_launch
                    if name == "ntt_forward" and args.workload == "paper" else None)
-        # peak: the same butterfly arithmetic on register-resident values, measured now on this GPU
-        peak = ctx.probe_butterfly_rate(2000)
+        peak = bfly_peak
         roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Gbfly/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "traffic_source": "ncu dram__bytes_read+write per row of the fused forward passes, scaled "
@@ -666,8 +703,7 @@ def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, ra
                       "plan_device_gib": plan.info.device_bytes / 2 ** 30},
            "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
            "accuracy": {"max_abs_vs_fp64": err, "rmse_gap_test": rmse_gap},
-           "kernels": {k: {"launches": v[0], "device_ms": round(v[1], 3), "alg_gb": round(v[2] / 1e9, 3)}
-                       for k, v in stats.items() if v[0]}}
+           "kernels": class_rooflines(stats, ctx.log_n, bfly_peak, hbm_peak)}
     from paper_2509_03024_gb300 import comm
     out["communication"] = {
         "training_10_epochs": comm.mf_training(ctx.n, ctx.top, ctx.alpha,
