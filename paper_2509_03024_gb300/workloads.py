@@ -53,6 +53,9 @@ PRESETS = {
     "t11a2": CkksPreset("t11a2", 11, (50,) * 5, (60, 60), 50),
     "t12": CkksPreset("t12", 12, (60, 40, 40, 40, 40), (60,), 40),
     "t10s": CkksPreset("t10s", 10, (50,) * 13, (60, 60, 60), 50),
+    # the N = 2^16 ring of the batched, served and large workloads with a short chain: three special
+    # primes, two key-switch digits at the top level (the second holding one limb)
+    "t16a3": CkksPreset("t16a3", 16, (50,) * 4, (60, 60, 60), 50),
 }
 
 

@@ -202,3 +202,44 @@ def test_errors_are_reported_and_context_survives():
     # still usable
     ctx.rotate(a, out, 1, ctx.top, 1)
     assert np.abs(ctx.decrypt(out, ctx.top) - np.roll(_slots(ctx.slots, 1), -1)).max() < 1e-5
+
+
+def test_key_switches_bit_exact_at_n_2_16():
+    """The N = 2^16 instantiations of the fused key-switch passes (the ring of the batched, served and
+    large workloads) with three special primes and a one-limb last digit at the top level: rotation
+    both ways, the fused product, the rescale and the hoisted rotate-and-sum at kp = 16 (the block of
+    the k = 16 workloads) at two levels, bit for bit. Sparse slot vectors keep the oracle's encoding
+    short."""
+    from oracle import mf
+    steps = mf.rotsum_steps(16) + [32, -32]
+    ctx = gpu_ctx("t16a3", SEED, steps)
+    he = oracle_ctx("t16a3", SEED, steps)
+    L = ctx.top
+    xs = []
+    for i in range(2):
+        rng = np.random.default_rng(60 + i)
+        x = np.zeros(ctx.slots)
+        x[rng.choice(ctx.slots, 64, replace=False)] = rng.uniform(-1, 1, 64)
+        xs.append(x)
+    a = ctx.empty_ct(2)
+    for i, x in enumerate(xs):
+        ctx.encrypt(x, L, 70 + i, ct_slice(ctx, a, i))
+    oa = [he.encrypt(x, L, 70 + i) for i, x in enumerate(xs)]
+    A, B = ct_slice(ctx, a, 0), ct_slice(ctx, a, 1)
+    assert_ct_equal(to_coeff(ctx, A, L)[0], oa[0], "encrypt")
+    out = ctx.empty_ct()
+    for r in (32, -32):
+        ctx.rotate(A, out, 1, L, r)
+        assert_ct_equal(to_coeff(ctx, out, L)[0], he.rotate(oa[0], r), f"rotate {r}")
+    ctx.mul_relin_rescale(A, B, out, 1, L)
+    assert_ct_equal(to_coeff(ctx, out, L - 1)[0], he.relin_rescale(he.tensor(oa[0], oa[1])), "fused product")
+    assert np.abs(ctx.decrypt(out, L - 1) - xs[0] * xs[1]).max() < 1e-4
+    ctx.rescale(A, out, 1, L)
+    assert_ct_equal(to_coeff(ctx, out, L - 1)[0], he.rescale(oa[0]), "rescale")
+    ref = sum(np.roll(xs[0], -r) for r in range(16))
+    for level in (L, L - 1):
+        src = A.clone()
+        ctx.rotate_sum(src, out, 1, level, 16)
+        assert_ct_equal(to_coeff(ctx, out, level)[0], mf.block_sum(he, he.drop(oa[0], level), 16),
+                        f"rotate_sum kp=16 at level {level}")
+        assert np.abs(ctx.decrypt(out, level) - ref).max() < 1e-4
