@@ -171,14 +171,9 @@ struct Arena {
 
 // Kernel classes for launch counting and optional per-launch CUDA-event timing.
 enum KClass {
-    K_NTT_FWD = 0,
+    K_NTT_FWD = 0,  // every NTT pass, the fused conversion, rescale and combine passes included
     K_NTT_INV,
-    K_KS_GATHER,
-    K_MODUP,
-    K_KS_INNER,
-    K_MODDOWN,
-    K_KS_FINAL,
-    K_RESCALE,
+    K_KS_INNER,     // key inner products (plain, fan-out and hoisted)
     K_TENSOR,
     K_ELEMENTWISE,
     K_ENCODE,

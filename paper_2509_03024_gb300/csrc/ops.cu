@@ -52,9 +52,8 @@ Arena::~Arena() {
 
 // ============================================================================ launch accounting
 
-const char* const kKClassNames[K_COUNT] = {"ntt_forward", "ntt_inverse", "ks_gather", "modup", "ks_inner",
-                                           "moddown",     "ks_final",    "rescale",   "tensor", "elementwise",
-                                           "encode",      "other"};
+const char* const kKClassNames[K_COUNT] = {"ntt_forward", "ntt_inverse", "ks_inner", "tensor",
+                                           "elementwise", "encode",      "other"};
 
 cudaEvent_t Profiler::get_event() {
     if (pool_used == pool.size()) {
