@@ -341,3 +341,54 @@ def test_encrypt_seeded_exact_error_and_regenerable_c1():
     for i, q in enumerate(prm.q[: prm.top]):
         a = ckks.sample_uniform_indexed(ckks.stream_key(41, ckks.P_SEEDED_A, 77, 0, i), prm.n, q)
         assert (ct.c[1][i] == a).all()
+
+
+def _centred_plaintext(he, ct):
+    """c0 + c1 s over the ciphertext's two lowest limbs, lifted to Z_{q0 q1} by CRT and centred,
+    with the secret product taken in the integers (the decryption definition, written out)."""
+    q0, q1 = he.prm.q[0], he.prm.q[1]
+    Q, inv = q0 * q1, pow(q0, -1, q1)
+
+    def lift(comp):
+        x0, x1 = ct.c[comp][0].tolist(), ct.c[comp][1].tolist()
+        return [a + q0 * (((b - a) * inv) % q1) for a, b in zip(x0, x1)]
+    c0, c1s = lift(0), _int_negacyclic(lift(1), he.s.tolist())
+    out = []
+    for a, b in zip(c0, c1s):
+        v = (a + b) % Q
+        out.append(v - Q if v > Q // 2 else v)
+    return out
+
+
+def test_refresh_is_a_fresh_encryption_of_the_exact_plaintext():
+    """refresh(ct) = Enc_top(c0 + c1 s; nonce): encryption is (v pk0 + e0 + m, v pk1 + e1), so it
+    differs from the same nonce's encryption of zero by (m, 0) exactly, m the centred integer
+    plaintext of the level-1 input."""
+    prm = _params(log_n=5)
+    he = ckks.Ckks(prm)
+    he.keygen(13)
+    rng = np.random.default_rng(5)
+    m0 = rng.integers(-(1 << 38), 1 << 38, size=prm.n)
+    ct = he.drop(he.encrypt_coeffs(m0, prm.top, 5), 1)
+    pt = _centred_plaintext(he, ct)
+    assert max(abs(p - int(a)) for p, a in zip(pt, m0)) < 1 << 12      # m0 plus a fresh error
+    r = he.refresh(ct, 9)
+    z = he.encrypt_coeffs(np.zeros(prm.n, dtype=np.int64), prm.top, 9)
+    assert r.level == prm.top
+    for i, q in enumerate(prm.q[: prm.top + 1]):
+        assert all((int(x) - int(y) - p) % q == 0 for x, y, p in zip(r.c[0][i], z.c[0][i], pt))
+        assert (r.c[1][i] == z.c[1][i]).all()
+
+
+def test_mul_plain_multiplies_the_integer_plaintext():
+    """Eq. 9: the integer plaintext of ct (.) p is p times that of ct in Z[X]/(X^N + 1), exactly,
+    while it stays below q0 q1 / 2."""
+    prm = _params(log_n=5)
+    he = ckks.Ckks(prm)
+    he.keygen(17)
+    rng = np.random.default_rng(6)
+    ct = he.drop(he.encrypt_coeffs(rng.integers(-(1 << 30), 1 << 30, size=prm.n), prm.top, 3), 1)
+    p = np.zeros(prm.n, dtype=np.int64)
+    p[[0, 3, prm.n - 1]] = [1000, -7, 1 << 20]
+    got = _centred_plaintext(he, he.mul_plain(ct, p))
+    assert got == _int_negacyclic(p.tolist(), _centred_plaintext(he, ct))
