@@ -263,6 +263,19 @@ int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t ca
  * bin. Duplicate (i, j) pairs are rejected. */
 int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* row_ptr,
                  const int32_t* col_idx, const double* vals, fhe_mf_plan** out);
+/* Host only (no context, no device; runs on a machine without a GPU): the layout fhe_csr_pack
+ * computes for a ring of `slots` = N/2 slots (a power of two in [2^8, 2^15]), from the same CSR
+ * input with the same checks. counts (host int64[3]) receives the number of groups, rating bins
+ * and delta-tree nodes. Each other output may be NULL; the non-NULL group arrays (host int32,
+ * group_cap entries) receive, per group in (b, c, delta) order, its user batch, item batch, delta,
+ * rating count and bin; the non-NULL node arrays (host int32, node_cap entries) receive, per node
+ * in the plan's order (item batch, then delta ascending), its item batch and delta. Call with NULL
+ * arrays first to learn the counts. FHE_ERR_INVALID_ARG (counts written) if a non-NULL array is
+ * shorter than its count. */
+int fhe_mf_layout(int32_t slots, int32_t n, int32_t m, int32_t k, const int64_t* row_ptr,
+                  const int32_t* col_idx, const double* vals, int64_t* counts, int32_t* group_b,
+                  int32_t* group_c, int32_t* group_delta, int32_t* group_count, int32_t* bin_of_group,
+                  int64_t group_cap, int32_t* node_c, int32_t* node_delta, int64_t node_cap);
 void fhe_mf_plan_destroy(fhe_mf_plan* plan);
 int fhe_mf_plan_get_info(const fhe_mf_plan* plan, fhe_mf_plan_info* out);
 /* Copy the plan's groups to host arrays of n_groups entries (any may be NULL):

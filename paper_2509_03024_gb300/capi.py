@@ -29,7 +29,7 @@ EXPORTS = [
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
-    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_plan_destroy",
+    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_layout", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_get_bins", "fhe_mf_plan_set_chunk", "fhe_mf_plan_set_wave_budget", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
             "fhe_profile_end": [vp, vp, i32],
             "fhe_mf_rotation_steps": [vp, i32, vp, sz],
             "fhe_csr_pack": [vp, i32, i32, i32, vp, vp, vp, ctypes.POINTER(vp)],
+            "fhe_mf_layout": [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i64],
             "fhe_mf_plan_destroy": [vp],
             "fhe_mf_plan_get_info": [vp, ctypes.POINTER(PlanInfo)],
             "fhe_mf_plan_get_groups": [vp, vp, vp, vp, vp],
@@ -161,6 +162,30 @@ def _stream(s) -> Optional[int]:
     if s is None:
         return None
     return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def mf_layout(slots: int, n: int, m: int, k: int, row_ptr, col_idx, vals):
+    """The plan layout fhe_csr_pack computes for a ring of `slots` slots, on the host alone (no
+    context, no GPU): {"groups": int32 [G, 4] (b, c, delta, ratings), "bins": int32 [G],
+    "nodes": int32 [nodes, 2] (item batch, delta), "n_bins": int}."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(vals, dtype=np.float64)
+    counts = np.zeros(3, dtype=np.int64)
+    L = lib()
+
+    def call(arrays, gcap, ncap):
+        rc = L.fhe_mf_layout(slots, n, m, k, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, counts.ctypes.data,
+                             *[None if a is None else a.ctypes.data for a in arrays[:5]], gcap,
+                             *[None if a is None else a.ctypes.data for a in arrays[5:]], ncap)
+        if rc != FHE_OK:
+            raise FheError(rc, "fhe_mf_layout rejected its input")
+    call([None] * 7, 0, 0)
+    G, NB, ND = (int(x) for x in counts)
+    g = [np.zeros(G, dtype=np.int32) for _ in range(5)]
+    nd = [np.zeros(ND, dtype=np.int32) for _ in range(2)]
+    call(g + nd, G, ND)
+    return {"groups": np.stack(g[:4], axis=1), "bins": g[4], "nodes": np.stack(nd, axis=1), "n_bins": NB}
 
 
 class Context:

@@ -534,6 +534,127 @@ int guarded(Ctx* c, F&& f) {
     }
 }
 
+// CSR checks shared by fhe_csr_pack and fhe_mf_layout (the per-entry checks run while grouping).
+void check_csr(int n, int m, int k, const int64_t* row_ptr, const int32_t* col_idx, const double* vals) {
+    if (n < 1 || m < 1 || k < 1 || !row_ptr) fail(FHE_ERR_INVALID_ARG, "bad matrix shape");
+    const long long M = row_ptr[n];
+    if (row_ptr[0] != 0 || M < 0) fail(FHE_ERR_INVALID_ARG, "row_ptr must start at 0");
+    if (M > 0 && (!col_idx || !vals)) fail(FHE_ERR_INVALID_ARG, "null CSR arrays");
+    for (int i = 0; i < n; i++)
+        if (row_ptr[i + 1] < row_ptr[i]) fail(FHE_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
+}
+
+// The host-side layout of a plan for a ring of `slots` slots (Alg. 2 batch pairs, Fig. 5): batch
+// geometry, groups in (b, c, delta) order, delta-tree nodes, the execution order and item-batch
+// boundaries, and the rating bins. Touches no device.
+void build_layout(fhe_mf_plan& p, int slots, int n, int m, int k, const int64_t* row_ptr, const int32_t* col_idx,
+                  const double* vals) {
+    p.n = n;
+    p.m = m;
+    p.k = k;
+    p.kp = next_pow2(k);
+    p.w = 2 * p.kp;
+    if (p.w > slots) fail(FHE_ERR_INVALID_ARG, "rank too large for the ring");
+    p.B = slots / p.w;
+    p.beta = hbit(p.B);
+    p.log_kp = hbit(p.kp);
+    p.n_ub = (n + p.B - 1) / p.B;
+    p.n_vb = (m + p.B - 1) / p.B;
+    p.M = row_ptr[n];
+    p.nnz_u.assign(n, 0);
+    p.nnz_v.assign(m, 0);
+    std::map<std::tuple<int, int, int>, std::vector<std::pair<int, double>>> gm;
+    for (int i = 0; i < n; i++) {
+        std::vector<int> cols(col_idx + row_ptr[i], col_idx + row_ptr[i + 1]);
+        std::sort(cols.begin(), cols.end());
+        for (size_t t = 1; t < cols.size(); t++)
+            if (cols[t] == cols[t - 1]) fail(FHE_ERR_INVALID_ARG, "duplicate (user, item) rating");
+        for (long long e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+            int j = col_idx[e];
+            if (j < 0 || j >= m) fail(FHE_ERR_INVALID_ARG, "column index out of range");
+            if (!std::isfinite(vals[e])) fail(FHE_ERR_INVALID_ARG, "non-finite rating");
+            int a = i % p.B, b = i / p.B, d = j % p.B, cb = j / p.B;
+            int delta = ((d - a) % p.B + p.B) % p.B;
+            gm[std::make_tuple(b, cb, delta)].push_back({a, vals[e]});
+            p.nnz_u[i]++;
+            p.nnz_v[j]++;
+        }
+    }
+    for (auto& kv : gm) {
+        Group g;
+        std::tie(g.b, g.c, g.delta) = kv.first;
+        auto v = kv.second;
+        std::sort(v.begin(), v.end());
+        for (auto& pr : v) {
+            g.a.push_back(pr.first);
+            g.r.push_back(pr.second);
+        }
+        p.groups.push_back(std::move(g));
+    }
+    // delta trees
+    p.closure.assign(p.n_vb, {});
+    p.node_of.assign((size_t)p.n_vb * p.B, -1);
+    for (int cb = 0; cb < p.n_vb; cb++) {
+        std::vector<char> in(p.B, 0);
+        in[0] = 1;
+        for (const Group& g : p.groups)
+            if (g.c == cb)
+                for (int d = g.delta; d && !in[d]; d -= 1 << hbit(d)) in[d] = 1;
+        for (int d = 0; d < p.B; d++)
+            if (in[d]) {
+                p.closure[cb].push_back(d);
+                p.node_of[(size_t)cb * p.B + d] = (int)p.node_c.size();
+                p.node_c.push_back(cb);
+                p.node_delta.push_back(d);
+            }
+    }
+    for (const Group& g : p.groups) p.group_node.push_back(p.node(g.c, g.delta));
+    // execution order (c, b, delta), and the first position and first node of each item batch
+    {
+        const int G0 = (int)p.groups.size();
+        p.order.resize(G0);
+        for (int gi = 0; gi < G0; gi++) p.order[gi] = gi;
+        std::stable_sort(p.order.begin(), p.order.end(),
+                         [&](int x, int y) { return p.groups[x].c < p.groups[y].c; });
+        p.c_first_pos.assign(p.n_vb + 1, G0);
+        for (int pos = G0 - 1; pos >= 0; pos--) p.c_first_pos[p.groups[p.order[pos]].c] = pos;
+        for (int cb = p.n_vb - 1; cb >= 0; cb--)
+            p.c_first_pos[cb] = std::min(p.c_first_pos[cb], p.c_first_pos[cb + 1]);
+        p.c_first_node.assign(p.n_vb + 1, (int)p.node_c.size());
+        for (int nd = (int)p.node_c.size() - 1; nd >= 0; nd--) p.c_first_node[p.node_c[nd]] = nd;
+    }
+    // Rating bins: within each user batch, groups in plan order go to the first bin (in creation
+    // order) holding none of their users, else to a new bin; bins are numbered batch by batch.
+    const int G = (int)p.groups.size();
+    p.bin_of.assign(G, 0);
+    {
+        const int words = (p.B + 63) / 64;
+        std::vector<uint64_t> gbits(words);
+        int g = 0;
+        for (int b = 0; b < p.n_ub; b++) {
+            const int first = (int)p.bin_b.size();
+            std::vector<std::vector<uint64_t>> taken;
+            for (; g < G && p.groups[g].b == b; g++) {
+                std::fill(gbits.begin(), gbits.end(), 0);
+                for (int a : p.groups[g].a) gbits[a >> 6] |= 1ull << (a & 63);
+                int chosen = -1;
+                for (size_t t = 0; t < taken.size() && chosen < 0; t++) {
+                    bool clash = false;
+                    for (int x = 0; x < words && !clash; x++) clash = (taken[t][x] & gbits[x]) != 0;
+                    if (!clash) chosen = (int)t;
+                }
+                if (chosen < 0) {
+                    taken.emplace_back(words, 0);
+                    p.bin_b.push_back(b);
+                    chosen = (int)taken.size() - 1;
+                }
+                for (int x = 0; x < words; x++) taken[chosen][x] |= gbits[x];
+                p.bin_of[g] = first + chosen;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -563,119 +684,12 @@ int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* r
     if (!p) return FHE_ERR_OOM;
     Ctx& c = ctx->c;
     int rc = guarded(&c, [&] {
-        if (n < 1 || m < 1 || k < 1 || !row_ptr) fail(FHE_ERR_INVALID_ARG, "bad matrix shape");
-        const long long M = row_ptr[n];
-        if (row_ptr[0] != 0 || M < 0) fail(FHE_ERR_INVALID_ARG, "row_ptr must start at 0");
-        if (M > 0 && (!col_idx || !vals)) fail(FHE_ERR_INVALID_ARG, "null CSR arrays");
-        for (int i = 0; i < n; i++)
-            if (row_ptr[i + 1] < row_ptr[i]) fail(FHE_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
+        check_csr(n, m, k, row_ptr, col_idx, vals);
         if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
         p->c = &c;
-        p->n = n;
-        p->m = m;
-        p->k = k;
-        p->kp = next_pow2(k);
-        p->w = 2 * p->kp;
-        if (p->w > c.slots) fail(FHE_ERR_INVALID_ARG, "rank too large for the ring");
-        p->B = c.slots / p->w;
-        p->beta = hbit(p->B);
-        p->log_kp = hbit(p->kp);
-        p->n_ub = (n + p->B - 1) / p->B;
-        p->n_vb = (m + p->B - 1) / p->B;
-        p->M = M;
-        p->nnz_u.assign(n, 0);
-        p->nnz_v.assign(m, 0);
-        std::map<std::tuple<int, int, int>, std::vector<std::pair<int, double>>> gm;
-        for (int i = 0; i < n; i++) {
-            std::vector<int> cols(col_idx + row_ptr[i], col_idx + row_ptr[i + 1]);
-            std::sort(cols.begin(), cols.end());
-            for (size_t t = 1; t < cols.size(); t++)
-                if (cols[t] == cols[t - 1]) fail(FHE_ERR_INVALID_ARG, "duplicate (user, item) rating");
-            for (long long e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
-                int j = col_idx[e];
-                if (j < 0 || j >= m) fail(FHE_ERR_INVALID_ARG, "column index out of range");
-                if (!std::isfinite(vals[e])) fail(FHE_ERR_INVALID_ARG, "non-finite rating");
-                int a = i % p->B, b = i / p->B, d = j % p->B, cb = j / p->B;
-                int delta = ((d - a) % p->B + p->B) % p->B;
-                gm[std::make_tuple(b, cb, delta)].push_back({a, vals[e]});
-                p->nnz_u[i]++;
-                p->nnz_v[j]++;
-            }
-        }
-        for (auto& kv : gm) {
-            Group g;
-            std::tie(g.b, g.c, g.delta) = kv.first;
-            auto v = kv.second;
-            std::sort(v.begin(), v.end());
-            for (auto& pr : v) {
-                g.a.push_back(pr.first);
-                g.r.push_back(pr.second);
-            }
-            p->groups.push_back(std::move(g));
-        }
-        // delta trees
-        p->closure.assign(p->n_vb, {});
-        p->node_of.assign((size_t)p->n_vb * p->B, -1);
-        for (int cb = 0; cb < p->n_vb; cb++) {
-            std::vector<char> in(p->B, 0);
-            in[0] = 1;
-            for (const Group& g : p->groups)
-                if (g.c == cb)
-                    for (int d = g.delta; d && !in[d]; d -= 1 << hbit(d)) in[d] = 1;
-            for (int d = 0; d < p->B; d++)
-                if (in[d]) {
-                    p->closure[cb].push_back(d);
-                    p->node_of[(size_t)cb * p->B + d] = (int)p->node_c.size();
-                    p->node_c.push_back(cb);
-                    p->node_delta.push_back(d);
-                }
-        }
-        for (const Group& g : p->groups) p->group_node.push_back(p->node(g.c, g.delta));
-        // execution order (c, b, delta) and the item-batch waves of the node workspace
-        {
-            const int G0 = (int)p->groups.size();
-            p->order.resize(G0);
-            for (int gi = 0; gi < G0; gi++) p->order[gi] = gi;
-            std::stable_sort(p->order.begin(), p->order.end(),
-                             [&](int x, int y) { return p->groups[x].c < p->groups[y].c; });
-            p->c_first_pos.assign(p->n_vb + 1, G0);
-            for (int pos = G0 - 1; pos >= 0; pos--) p->c_first_pos[p->groups[p->order[pos]].c] = pos;
-            for (int cb = p->n_vb - 1; cb >= 0; cb--)
-                p->c_first_pos[cb] = std::min(p->c_first_pos[cb], p->c_first_pos[cb + 1]);
-            p->c_first_node.assign(p->n_vb + 1, (int)p->node_c.size());
-            for (int nd = (int)p->node_c.size() - 1; nd >= 0; nd--) p->c_first_node[p->node_c[nd]] = nd;
-            plan_waves(*p);
-        }
-        // Rating bins: within each user batch, groups in plan order go to the first bin (in creation
-        // order) holding none of their users, else to a new bin; bins are numbered batch by batch.
+        build_layout(*p, c.slots, n, m, k, row_ptr, col_idx, vals);
+        plan_waves(*p);
         const int G = (int)p->groups.size();
-        p->bin_of.assign(G, 0);
-        {
-            const int words = (p->B + 63) / 64;
-            std::vector<uint64_t> gbits(words);
-            int g = 0;
-            for (int b = 0; b < p->n_ub; b++) {
-                const int first = (int)p->bin_b.size();
-                std::vector<std::vector<uint64_t>> taken;
-                for (; g < G && p->groups[g].b == b; g++) {
-                    std::fill(gbits.begin(), gbits.end(), 0);
-                    for (int a : p->groups[g].a) gbits[a >> 6] |= 1ull << (a & 63);
-                    int chosen = -1;
-                    for (size_t t = 0; t < taken.size() && chosen < 0; t++) {
-                        bool clash = false;
-                        for (int x = 0; x < words && !clash; x++) clash = (taken[t][x] & gbits[x]) != 0;
-                        if (!clash) chosen = (int)t;
-                    }
-                    if (chosen < 0) {
-                        taken.emplace_back(words, 0);
-                        p->bin_b.push_back(b);
-                        chosen = (int)taken.size() - 1;
-                    }
-                    for (int x = 0; x < words; x++) taken[chosen][x] |= gbits[x];
-                    p->bin_of[g] = first + chosen;
-                }
-            }
-        }
         // EncryptCsrMatrix: one ciphertext per bin, each group's ratings in the first k slots of their
         // user blocks, encrypted by the key holder with a regenerable c1 (object 2^40 + bin) at level
         // L - 1, the highest level an epoch reads it at; only c0 is stored
@@ -719,6 +733,38 @@ int fhe_csr_pack(fhe_ctx* ctx, int32_t n, int32_t m, int32_t k, const int64_t* r
     }
     *out = p;
     return FHE_OK;
+}
+
+int fhe_mf_layout(int32_t slots, int32_t n, int32_t m, int32_t k, const int64_t* row_ptr, const int32_t* col_idx,
+                  const double* vals, int64_t* counts, int32_t* group_b, int32_t* group_c, int32_t* group_delta,
+                  int32_t* group_count, int32_t* bin_of_group, int64_t group_cap, int32_t* node_c,
+                  int32_t* node_delta, int64_t node_cap) {
+    if (!counts) return FHE_ERR_INVALID_ARG;
+    return guarded(nullptr, [&] {
+        if (slots < 256 || slots > 32768 || (slots & (slots - 1)))
+            fail(FHE_ERR_INVALID_ARG, "slots must be a power of two in [2^8, 2^15]");
+        check_csr(n, m, k, row_ptr, col_idx, vals);
+        fhe_mf_plan p;  // host fields only: nothing is allocated on a device
+        build_layout(p, slots, n, m, k, row_ptr, col_idx, vals);
+        const int64_t G = (int64_t)p.groups.size(), NB = (int64_t)p.bin_b.size(), ND = (int64_t)p.node_c.size();
+        counts[0] = G;
+        counts[1] = NB;
+        counts[2] = ND;
+        if ((group_b || group_c || group_delta || group_count || bin_of_group) && group_cap < G)
+            fail(FHE_ERR_INVALID_ARG, "group arrays shorter than the group count");
+        if ((node_c || node_delta) && node_cap < ND) fail(FHE_ERR_INVALID_ARG, "node arrays shorter than the node count");
+        for (int64_t g = 0; g < G; g++) {
+            if (group_b) group_b[g] = p.groups[g].b;
+            if (group_c) group_c[g] = p.groups[g].c;
+            if (group_delta) group_delta[g] = p.groups[g].delta;
+            if (group_count) group_count[g] = (int32_t)p.groups[g].a.size();
+            if (bin_of_group) bin_of_group[g] = p.bin_of[g];
+        }
+        for (int64_t d = 0; d < ND; d++) {
+            if (node_c) node_c[d] = p.node_c[d];
+            if (node_delta) node_delta[d] = p.node_delta[d];
+        }
+    });
 }
 
 void fhe_mf_plan_destroy(fhe_mf_plan* p) {
