@@ -150,10 +150,12 @@ def _ptr(x) -> Optional[int]:
     if x is None:
         return None
     if isinstance(x, np.ndarray):
-        assert x.flags["C_CONTIGUOUS"]
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be C-contiguous")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous()
+        if not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
         return x.data_ptr()
     return int(x)
 

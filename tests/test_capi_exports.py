@@ -111,3 +111,17 @@ def test_binding_structs_match_the_header(cname, pyname):
             assert ct is ctypes.c_char_p or hasattr(ct, "_type_"), (cname, name, ct)
         else:
             assert ct is _CTYPE[base], (cname, name, ct, base)
+
+
+def test_buffer_marshalling_refuses_strided_views():
+    import numpy as np
+    import torch
+    from paper_2509_03024_gb300 import capi
+    a = np.zeros((4, 4))
+    assert capi._ptr(a) == a.ctypes.data and capi._ptr(None) is None
+    with pytest.raises(ValueError):
+        capi._ptr(a[:, ::2])
+    t = torch.zeros(4, 4, dtype=torch.int64)
+    assert capi._ptr(t) == t.data_ptr()
+    with pytest.raises(ValueError):
+        capi._ptr(t.t())
