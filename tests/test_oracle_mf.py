@@ -170,3 +170,37 @@ def test_rating_bins_invariants():
     # the bin slot vectors carry every rating exactly once
     total = sum(mf.bin_slots(t, plan).sum() for t in range(len(plan.bin_batch)))
     assert abs(total - plan.k * vals.sum()) < 1e-6
+
+
+def test_slot_layouts_hand_example():
+    """The doubled-block layout (Sec. III-C's u_L0 || ... || u_Lk-1 padded to kp and written twice),
+    the rating, mask and regulariser slot vectors, written out by hand for k = 3 (kp = 4, w = 8) in
+    a ring of 32 slots (B = 4 entities per batch)."""
+    rows, cols, vals = [0, 0, 5], [1, 2, 1], [4.0, 2.0, 5.0]     # users 0, 0, 5; items 1, 2, 1
+    plan = mf.build_plan(6, 3, 3, rows, cols, vals, 32)
+    assert (plan.kp, plan.w, plan.B, plan.n_ub, plan.n_vb) == (4, 8, 4, 2, 1)
+    X = np.arange(1.0, 19.0).reshape(6, 3)                        # entity e holds 3e+1, 3e+2, 3e+3
+    z = mf.pack_factors(X, plan, 1)                               # entities 4, 5 in blocks 0, 1
+    want = np.zeros(32)
+    want[0:3] = want[4:7] = [13, 14, 15]
+    want[8:11] = want[12:15] = [16, 17, 18]
+    assert np.array_equal(z, want)
+    # group (b=0, c=0, delta=1): user 0 (a=0) rated item 1 (d=1); its rating sits in user 0's block
+    g = next(g for g in plan.groups if (g.b, g.c, g.delta) == (0, 0, 1))
+    assert g.a.tolist() == [0]
+    r = mf.rating_slots(g, plan)
+    want = np.zeros(32)
+    want[0:3] = 4.0
+    assert np.array_equal(r, want)
+    m = mf.mask_slots(g, plan, 0.5)
+    want = np.zeros(32)
+    want[0:3] = 0.5
+    assert np.array_equal(m, want)
+    # regulariser of user batch 0: user 0 has 2 ratings, users 1-3 none
+    reg = mf.reg_slots(plan.nnz_u, plan, 0, 0.1, 0.5)
+    want = np.ones(32)
+    want[0:8] = 1.0 - 0.1 * 0.5 * 2
+    assert np.array_equal(reg, want)
+    # user batch 1 holds users 4, 5 then two empty blocks (no entity: regulariser 1, factors 0)
+    reg1 = mf.reg_slots(plan.nnz_u, plan, 1, 0.1, 0.5)
+    assert np.array_equal(reg1[8:16], np.full(8, 1.0 - 0.05)) and np.array_equal(reg1[16:], np.ones(16))
