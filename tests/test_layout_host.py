@@ -73,3 +73,18 @@ def test_layout_matches_oracle_at_the_large_shape():
     train, _ = W.split_holdout(full, 0.1, 12)
     got, _ = _compare(train, 16, 1 << 15)
     assert got["groups"].shape[0] == 24576 and got["n_bins"] == 12204 and got["nodes"].shape[0] == 4096
+
+
+def test_layout_ignores_column_order_within_rows():
+    """CSR rows need not be sorted: permuting each row's entries gives the same layout."""
+    csr = W.uniform_ratings(150, 70, 0.05, seed=9)
+    ref = capi.mf_layout(512, csr.n, csr.m, 2, csr.row_ptr, csr.col_idx, csr.vals)
+    rng = np.random.default_rng(3)
+    ci, va = csr.col_idx.copy(), csr.vals.copy()
+    for i in range(csr.n):
+        lo, hi = csr.row_ptr[i], csr.row_ptr[i + 1]
+        p = rng.permutation(hi - lo) + lo
+        ci[lo:hi], va[lo:hi] = ci[p], va[p]
+    got = capi.mf_layout(512, csr.n, csr.m, 2, csr.row_ptr, ci, va)
+    for key in ("groups", "bins", "nodes"):
+        assert np.array_equal(got[key], ref[key])
