@@ -51,3 +51,28 @@ def test_encrypted_request_matches_fp64():
         assert np.abs(z[a * w + kp: a * w + kp + k] - u_ref).max() < 1e-6
     pred = np.concatenate([he.decrypt(P[c])[::w][:B] for c in range(n_vb)])[:m]
     assert np.abs(pred - pred_ref).max() < 1e-6
+
+
+def test_row_layout_hand_example():
+    """The served request's ROW layout written out by hand for k = 3 (kp = 4, w = 8) in 32 slots
+    (B = 4 blocks): u in every block, twice; item j = 4c + d rated in block d of batch c; the mask
+    on the first k slots of the rated blocks; the rotation amounts of a step."""
+    u = np.array([1.0, 2.0, 3.0])
+    z = serve.replicate_user(u, 3, 32)
+    want = np.zeros(32)
+    for a in range(4):
+        want[8 * a: 8 * a + 3] = want[8 * a + 4: 8 * a + 7] = u
+    assert np.array_equal(z, want)
+    items, ratings = [1, 6, 7], [4.0, 2.0, 5.0]        # item 1: batch 0 block 1; items 6, 7: batch 1 blocks 2, 3
+    R = serve.rating_batches(items, ratings, 3, 32, 2)
+    want0, want1 = np.zeros(32), np.zeros(32)
+    want0[8:11] = 4.0
+    want1[16:19], want1[24:27] = 2.0, 5.0
+    assert np.array_equal(R[0], want0) and np.array_equal(R[1], want1)
+    assert serve.rated_batches(items, 3, 32) == [0, 1]
+    m1 = serve.mask_batch(items, 1, 3, 32, 0.5)
+    want = np.zeros(32)
+    want[16:19] = want[24:27] = 0.5
+    assert np.array_equal(m1, want)
+    # in-block sums by 1, 2, 3 (hoisted, kp = 4), block sums by 8 and 16, the half-fill by -4
+    assert serve.rotation_steps(3, 32) == [1, 2, 3, 8, 16, -4]
