@@ -177,14 +177,16 @@ int fhe_rescale(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, 
  * the device) is not acceptable. It calls no cudaMalloc, cudaFree or other
  * allocating routine; its scratch space is a 16 MiB array compiled into the
  * library (held on every GPU that loads the library until the process exits).
- * Limit: 2 * N * (level + 1) <= 2^21, e.g. level <= 15 at N = 2^15 or level <= 7
+ * Limit: 2 * N * (level + 1) <= 2^21, i.e. level <= 31 at N = 2^15 or level <= 15
  * at N = 2^16; larger inputs are rejected with FHE_ERR_INVALID_ARG. The first
  * call on a device looks up the scratch array's device address (once per
  * device); make that first call before any stream capture. All calls share
  * the one scratch array: two calls whose work overlaps on the GPU (different
  * streams, or different host threads) race and corrupt each other's results;
- * order them on one stream. ct: device, level `level`; out: device, receives
- * level - 1 (may equal ct). */
+ * order them on one stream. The call counts its launches in the context's
+ * launch accounting but records no per-launch timing events (creating an event
+ * may allocate), on the calling host thread only. ct: device, level `level`;
+ * out: device, receives level - 1 (may equal ct). */
 int fhe_rescale_noalloc(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t level, void* stream);
 /* Left slot rotation by `step` (negative = right): automorphism X -> X^(5^step)
  * then key switching with that step's rotation key. out must not alias ct. */

@@ -198,6 +198,15 @@ struct Profiler {
     ~Profiler();
 };
 
+// Per host thread: while set, LaunchScope records no CUDA events (launches and bytes are still
+// counted). Lets one call skip event creation without touching the context's shared profiler state.
+extern thread_local bool tl_no_launch_events;
+struct NoLaunchEvents {
+    bool saved;
+    NoLaunchEvents() : saved(tl_no_launch_events) { tl_no_launch_events = true; }
+    ~NoLaunchEvents() { tl_no_launch_events = saved; }
+};
+
 // RAII scope around one kernel launch: counts it, adds its algorithmic bytes
 // and, when timing is on, brackets it with CUDA events on its stream.
 struct LaunchScope {

@@ -62,9 +62,11 @@ __global__ void na_spread(u64* spread, const u64* __restrict__ last, int level, 
         bool neg = r > (ql >> 1);
         u64 mag = neg ? ql - r : r;
         for (int i = 0; i < level; i++) {
-            u64 qi = pr[i].q;
-            u64 m = mag % qi;
-            spread[((p * level + i) << log_n) + k] = neg ? (m ? qi - m : 0) : m;
+            const Prime P = pr[i];
+            // mag mod q_i by a Shoup product with 1 (floor(2^64 / q_i)) and one correction
+            u64 m = mag - __umul64hi(mag, P.one_s) * P.q;
+            m = m >= P.q ? m - P.q : m;
+            spread[((p * level + i) << log_n) + k] = neg ? (m ? P.q - m : 0) : m;
         }
     }
 }
@@ -108,14 +110,9 @@ extern "C" int fhe_rescale_noalloc(fhe_ctx* ctx, const uint64_t* ct, uint64_t* o
             fail(FHE_ERR_INVALID_ARG, "ciphertext too large for the 16 MiB static scratch of fhe_rescale_noalloc "
                                       "(needs 2*N*(level+1) <= 2^21 words)");
         u64* scratch = noalloc_scratch(c.device);
-        // launch accounting stays on, but per-launch event timing (which may create events) is paused
-        const bool timing = c.prof.timing;
-        c.prof.timing = false;
-        struct Restore {
-            Profiler& p;
-            bool t;
-            ~Restore() { p.timing = t; }
-        } restore{c.prof, timing};
+        // launch accounting stays on, but this call records no per-launch events (creating one may
+        // allocate); the switch is per host thread, so other threads' profiling is unaffected
+        NoLaunchEvents no_events;
         u64* last = scratch;
         u64* spread = scratch + 2 * n;
         const size_t pw = (size_t)(c.L + 1) * n;

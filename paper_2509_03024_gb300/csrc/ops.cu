@@ -77,10 +77,12 @@ Profiler::~Profiler() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
+thread_local bool tl_no_launch_events = false;
+
 LaunchScope::LaunchScope(Profiler& prof, int k, double nbytes, cudaStream_t st) : p(prof), cls(k), s(st) {
     p.launches[k]++;
     p.bytes[k] += nbytes;
-    if (p.timing) {
+    if (p.timing && !tl_no_launch_events) {
         b = p.get_event();
         CK(cudaEventRecord(b, s));
     }

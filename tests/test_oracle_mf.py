@@ -204,3 +204,28 @@ def test_slot_layouts_hand_example():
     # user batch 1 holds users 4, 5 then two empty blocks (no entity: regulariser 1, factors 0)
     reg1 = mf.reg_slots(plan.nnz_u, plan, 1, 0.1, 0.5)
     assert np.array_equal(reg1[8:16], np.full(8, 1.0 - 0.05)) and np.array_equal(reg1[16:], np.ones(16))
+
+
+def test_encrypted_predict_matches_fp64_row():
+    """EncryptedMF.predict (the encrypted row of R-hat = U V^T, Alg. 1) decrypts to u_user . v_j for
+    every item j of every item batch. The user sits in the second user batch at a block other than 0,
+    and there are two item batches, so a mask on the wrong block, a missing replication round (some
+    blocks left empty) or a swapped batch index all change the row. (The replication sums all B
+    cyclic shifts of the masked block, so its rotation direction does not change the values.)"""
+    n, m, k = 40, 50, 4
+    csr = W.uniform_ratings(n, m, 0.08, 11)
+    rows, cols, vals = csr.triples()
+    rng = np.random.default_rng(12)
+    U, V = rng.normal(0, 0.3, (n, k)), rng.normal(0, 0.3, (m, k))
+    he = ckks.Ckks(ckks.Params(9, (60, 40, 40), (60,), 40))
+    plan = mf.build_plan(n, m, k, rows, cols, vals, he.prm.slots)
+    assert (plan.B, plan.n_ub, plan.n_vb) == (32, 2, 2)
+    he.keygen(13, plan.rotation_steps())
+    emf = mf.EncryptedMF(he, plan)
+    UD, VD = emf.encrypt_factors(U, V)
+    for user in (37, 3):            # (b, a) = (1, 5) and (0, 3)
+        out = emf.predict(UD, VD, user)
+        assert len(out) == plan.n_vb and out[0].level == he.prm.top - 2
+        got = np.concatenate([he.decrypt(ct)[::plan.w][:plan.B] for ct in out])[:m]
+        want = V @ U[user]
+        assert np.abs(got - want).max() < 1e-6
