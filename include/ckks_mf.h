@@ -215,6 +215,26 @@ int fhe_rotate_sum(fhe_ctx* ctx, uint64_t* ct, uint64_t* out, int32_t count, int
  * reps < 1 or a null output. */
 int fhe_probe_butterfly_rate(fhe_ctx* ctx, int32_t reps, double* gbfly_per_s);
 
+/* Measurement helper (no counterpart in the paper): issue rates of the 32-bit integer multiply
+ * instructions that 64-bit modular arithmetic is built from, and of four formulations of the
+ * 64 x 64 -> 128-bit multiply-accumulate of the key inner product, all on register operands with no
+ * memory traffic (152 SMs x 4 CTAs of 256 threads on GB300). The bench turns them into the integer
+ * ceilings of the NTT butterfly and of the key inner product. Rates are in 10^9 instructions (or
+ * multiply-accumulates) per second. reps: loop trips (each trip is 128 instructions or 32 MACs per
+ * thread; ~500 takes milliseconds). Runs on the default stream and synchronises. Errors:
+ * FHE_ERR_INVALID_ARG for reps < 1 or a null output. */
+typedef struct {
+    int32_t sms;
+    double imad_lo_gops;      /* mad.lo.u32            */
+    double imad_hi_gops;      /* mad.hi.u32            */
+    double imad_wide_gops;    /* mad.wide.u32          */
+    double mac_c_gmacs;       /* C: lo/hi halves + carry compare          */
+    double mac_ptx64_gmacs;   /* PTX mad.lo.cc.u64 / madc.hi.u64          */
+    double mac_ptx32_gmacs;   /* PTX 32-bit schoolbook chain with carries */
+    double mac_wide_gmacs;    /* four mad.wide.u32 into column sums       */
+} fhe_int_pipe_rates;
+int fhe_probe_int_pipe(fhe_ctx* ctx, int32_t reps, fhe_int_pipe_rates* out);
+
 /* Per kernel class: launches, summed device time (only when timing was
  * requested) and the algorithmic bytes those launches must move (inputs read
  * once plus outputs written once). `name` points to a static string. */

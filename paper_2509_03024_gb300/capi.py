@@ -29,7 +29,7 @@ EXPORTS = [
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
-    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_layout", "fhe_mf_plan_destroy",
+    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_probe_int_pipe", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_layout", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_get_bins", "fhe_mf_plan_set_chunk", "fhe_mf_plan_set_wave_budget", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
@@ -59,6 +59,13 @@ class CtxInfo(ctypes.Structure):
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("device_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
+
+
+class IntPipeRates(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int32), ("imad_lo_gops", ctypes.c_double), ("imad_hi_gops", ctypes.c_double),
+                ("imad_wide_gops", ctypes.c_double), ("mac_c_gmacs", ctypes.c_double),
+                ("mac_ptx64_gmacs", ctypes.c_double), ("mac_ptx32_gmacs", ctypes.c_double),
+                ("mac_wide_gmacs", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -108,6 +115,7 @@ def lib() -> ctypes.CDLL:
             "fhe_rotate": [vp, vp, vp, i32, i32, i32, vp],
             "fhe_rotate_sum": [vp, vp, vp, i32, i32, i32, vp],
             "fhe_probe_butterfly_rate": [vp, i32, vp],
+            "fhe_probe_int_pipe": [vp, i32, ctypes.POINTER(IntPipeRates)],
             "fhe_profile_begin": [vp, i32],
             "fhe_profile_end": [vp, vp, i32],
             "fhe_mf_rotation_steps": [vp, i32, vp, sz],
@@ -336,6 +344,13 @@ class Context:
         out = ctypes.c_double(0.0)
         self._check(lib().fhe_probe_butterfly_rate(self.h, reps, ctypes.byref(out)))
         return out.value
+
+    def probe_int_pipe(self, reps: int = 500) -> dict:
+        """Register-only issue rates of the 32-bit multiply instructions (10^9 instructions/s) and of
+        four 64 x 64 -> 128-bit multiply-accumulate formulations (10^9 MACs/s) on this GPU."""
+        out = IntPipeRates()
+        self._check(lib().fhe_probe_int_pipe(self.h, reps, ctypes.byref(out)))
+        return {name: getattr(out, name) for name, _ in IntPipeRates._fields_}
 
     def profile_begin(self, time_kernels: bool = False):
         self._check(lib().fhe_profile_begin(self.h, 1 if time_kernels else 0))

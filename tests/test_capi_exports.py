@@ -100,7 +100,8 @@ def _struct_fields(name):
 
 
 @pytest.mark.parametrize("cname,pyname", [("fhe_params", "Params"), ("fhe_ctx_info", "CtxInfo"),
-                                          ("fhe_kernel_stat", "KernelStat"), ("fhe_mf_plan_info", "PlanInfo")])
+                                          ("fhe_kernel_stat", "KernelStat"), ("fhe_mf_plan_info", "PlanInfo"),
+                                          ("fhe_int_pipe_rates", "IntPipeRates")])
 def test_binding_structs_match_the_header(cname, pyname):
     from paper_2509_03024_gb300 import capi
     fields = _struct_fields(cname)
