@@ -62,6 +62,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-requests", type=int, default=96)
     ap.add_argument("--served-rate", type=float, default=100.0)
@@ -529,6 +530,7 @@ def run_gpu(args, rank, world, local_rank):
     train, test, U, V = workload(args.workload)
     ctx = capi.Context.from_preset(PRESETS[preset], device=dev)
     ctx.keygen(SEED + rank, ctx.mf_rotation_steps(k_rank))
+    tuning = autotune(ctx, args)
     plan = capi.MfPlan(ctx, train.n, train.m, k_rank, train.row_ptr, train.col_idx, train.vals)
     U0, V0 = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
     plan.encrypt_factors(0, U, U0)
@@ -576,8 +578,25 @@ def run_gpu(args, rank, world, local_rank):
     e2e = None
     if args.e2e_steps > 0:
         e2e = run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier, lr)
-    return finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
-                  train, U, V, dist)
+    out = finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
+                 train, U, V, dist)
+    out["config"]["tuning"] = tuning
+    return out
+
+
+def autotune(ctx, args):
+    """Run the library's autotuner (untimed) unless --no-autotune; returns the chosen variant per
+    kernel family and every variant's time, for the bench line."""
+    if args.no_autotune:
+        return {"autotuned": False}
+    res = ctx.autotune()
+    out = {"autotuned": True, "level": ctx.top - 1}
+    for r in res:
+        fam = out.setdefault(r["family"], {"chosen": None, "ms": {}})
+        fam["ms"][r["variant"]] = round(r["ms"], 4)
+        if r["chosen"]:
+            fam["chosen"] = r["variant"]
+    return out
 
 
 def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier, lr):

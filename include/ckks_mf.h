@@ -235,6 +235,28 @@ typedef struct {
 } fhe_int_pipe_rates;
 int fhe_probe_int_pipe(fhe_ctx* ctx, int32_t reps, fhe_int_pipe_rates* out);
 
+/* Autotuner (no counterpart in the paper; the launch shapes are this library's). Several kernel
+ * families have launch variants that compute identical bits and differ only in speed. For each
+ * family fhe_autotune times every variant on a synthetic batch of this context's shape at `level`
+ * (1 <= level <= top level; the per-group products of an epoch run at top - 1), keeps the fastest
+ * for the context and writes one record per (family, variant) to host `out` (up to cap; `chosen`
+ * is 1 for the kept variant, `ms` the best of three timed launches). Returns the number of records
+ * or an error code. Synchronises the device; allocates and frees temporary device memory.
+ * Families: "ks_hoist_inner" (the hoisted rotate-and-sum's key inner product, 15 rotations) and
+ * "ks_inner" (a relinearisation's key inner product). A fresh context uses variant "v0" of each.
+ * `family` and `variant` point to static strings. */
+typedef struct {
+    const char* family;
+    const char* variant;
+    int32_t chosen;
+    double ms;
+} fhe_tune_result;
+int fhe_autotune(fhe_ctx* ctx, int32_t level, fhe_tune_result* out, int32_t cap);
+/* Select a variant by name (FHE_ERR_INVALID_ARG for an unknown family or variant); results do not
+ * change. fhe_get_variant writes the current variant's name (a static string) to *variant. */
+int fhe_set_variant(fhe_ctx* ctx, const char* family, const char* variant);
+int fhe_get_variant(const fhe_ctx* ctx, const char* family, const char** variant);
+
 /* Per kernel class: launches, summed device time (only when timing was
  * requested) and the algorithmic bytes those launches must move (inputs read
  * once plus outputs written once). `name` points to a static string. */

@@ -29,7 +29,7 @@ EXPORTS = [
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
-    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_probe_int_pipe", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_layout", "fhe_mf_plan_destroy",
+    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_probe_int_pipe", "fhe_autotune", "fhe_set_variant", "fhe_get_variant", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_layout", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_get_bins", "fhe_mf_plan_set_chunk", "fhe_mf_plan_set_wave_budget", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
@@ -66,6 +66,11 @@ class IntPipeRates(ctypes.Structure):
                 ("imad_wide_gops", ctypes.c_double), ("mac_c_gmacs", ctypes.c_double),
                 ("mac_ptx64_gmacs", ctypes.c_double), ("mac_ptx32_gmacs", ctypes.c_double),
                 ("mac_wide_gmacs", ctypes.c_double)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_char_p), ("variant", ctypes.c_char_p), ("chosen", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -116,6 +121,9 @@ def lib() -> ctypes.CDLL:
             "fhe_rotate_sum": [vp, vp, vp, i32, i32, i32, vp],
             "fhe_probe_butterfly_rate": [vp, i32, vp],
             "fhe_probe_int_pipe": [vp, i32, ctypes.POINTER(IntPipeRates)],
+            "fhe_autotune": [vp, i32, ctypes.POINTER(TuneResult), i32],
+            "fhe_set_variant": [vp, ctypes.c_char_p, ctypes.c_char_p],
+            "fhe_get_variant": [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_char_p)],
             "fhe_profile_begin": [vp, i32],
             "fhe_profile_end": [vp, vp, i32],
             "fhe_mf_rotation_steps": [vp, i32, vp, sz],
@@ -351,6 +359,26 @@ class Context:
         out = IntPipeRates()
         self._check(lib().fhe_probe_int_pipe(self.h, reps, ctypes.byref(out)))
         return {name: getattr(out, name) for name, _ in IntPipeRates._fields_}
+
+    def autotune(self, level: int = None) -> list:
+        """Time every launch variant of each tunable kernel family at `level` (default: one below the
+        top, the level of an epoch's per-group products) and keep the fastest. Returns
+        [{family, variant, chosen, ms}]."""
+        level = self.top - 1 if level is None else level
+        arr = (TuneResult * 64)()
+        n = lib().fhe_autotune(self.h, level, arr, 64)
+        if n < 0:
+            self._check(n)
+        return [{"family": r.family.decode(), "variant": r.variant.decode(), "chosen": bool(r.chosen),
+                 "ms": r.ms} for r in arr[:min(n, 64)]]
+
+    def set_variant(self, family: str, variant: str):
+        self._check(lib().fhe_set_variant(self.h, family.encode(), variant.encode()))
+
+    def get_variant(self, family: str) -> str:
+        out = ctypes.c_char_p()
+        self._check(lib().fhe_get_variant(self.h, family.encode(), ctypes.byref(out)))
+        return out.value.decode()
 
     def profile_begin(self, time_kernels: bool = False):
         self._check(lib().fhe_profile_begin(self.h, 1 if time_kernels else 0))

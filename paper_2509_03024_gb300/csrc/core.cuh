@@ -283,6 +283,13 @@ struct Ctx {
     u64* scratch_u64(const std::string& name, size_t words);
     void* scratch_bytes(const std::string& name, size_t bytes);
 
+    // launch variants chosen by the autotuner (fhe_autotune); every choice gives the same bits
+    struct Tune {
+        int inner = 0;  // plain / fan-out key inner product (InnerVariant of ks_inner.cuh)
+        int hoist = 0;  // hoisted rotate-and-sum inner product
+    } tune;
+    int max_prime_bits = 0;
+
     std::string last_error;
     Arena arena;
     mutable Profiler prof;

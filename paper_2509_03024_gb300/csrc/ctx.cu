@@ -1053,6 +1053,7 @@ int fhe_ctx_create(const fhe_params* p, fhe_ctx** out) {
         c.sigma = p->sigma > 0 ? p->sigma : 3.2;
         c.primes = choose_primes(c.log_n, bits);
         for (u64 q : c.primes) c.hprimes.push_back(make_prime(q));
+        for (const Prime& P : c.hprimes) c.max_prime_bits = std::max(c.max_prime_bits, (int)P.b);
         c.d_primes = dupload(c.hprimes);
         ntt_init();
         build_tables(c);

@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "ks_inner.cuh"
 #include "ntt_core.cuh"
 
 namespace fhe {
@@ -62,15 +63,6 @@ struct KsRow {
     const u64* src3;       // ST_RESCALE: when set, the input limb is src2 (.) src3 (a plaintext product)
 };
 
-// Evaluation slot k holds a(psi^(2 brev(k) + 1)); X -> X^g moves slot k' to slot k
-// with 2 brev(k') + 1 = g (2 brev(k) + 1) mod 2N.
-__device__ __forceinline__ int auto_src(int k, int g, int log_n) {
-    const unsigned sh = 32 - log_n;
-    unsigned bk = __brev((unsigned)k) >> sh;
-    unsigned e = (unsigned)(((unsigned long long)g * (2ull * bk + 1ull)) & ((2ull << log_n) - 1ull));
-    return (int)(__brev((e - 1u) >> 1) >> sh);
-}
-
 constexpr int kMaxHoist = 31;
 
 // Rotation keys of a hoisted rotate-and-sum (host side).
@@ -78,12 +70,6 @@ struct HoistKeys {
     const u64* key[kMaxHoist];
     int galois[kMaxHoist];
     int count;
-};
-
-// One rotation of a hoisted rotate-and-sum, as the kernel reads it from a device table.
-struct HoistStep {
-    const u64* key;
-    long long galois;
 };
 
 struct CombineArgs {
@@ -333,150 +319,7 @@ void ks_transform(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs
     }
 }
 
-// (hi * 2^64 + lo) mod q for hi, lo < 2^64: hi and lo reduced with floor(2^64 / q), then
-// hi * (2^64 mod q) + lo.
-__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const Prime& P) {
-    const u64 q = P.q;
-    const u64 h = nttc::reduce_any(hi, q, P.one_s);
-    const u64 l = nttc::reduce_any(lo, q, P.one_s);
-    const u64 r64 = (u64)0 - q * P.one_s;  // 2^64 mod q
-    return add_mod(mul_mod(h, r64, P), l, q);
-}
-
-// (hi, lo) += a * b: mac128 in C, mac128_cc as one PTX multiply-add with carry. The hoisted kernel
-// runs faster with the former and the plain key inner product with the latter (measured).
-__device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 a, u64 b) {
-    const u64 pl = a * b;
-    const u64 ph = __umul64hi(a, b);
-    lo += pl;
-    hi += ph + (lo < pl ? 1 : 0);
-}
-__device__ __forceinline__ void mac128_cc(u64& lo, u64& hi, u64 a, u64 b) {
-    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
-}
-
-// Slots (2 k2, 2 k2 + 1) of phi_g(row): the automorphism maps the aligned pair onto an aligned pair.
-__device__ __forceinline__ void load_pair_auto(const u64* __restrict__ row, int k2, int g, int log_n, u64& vx, u64& vy) {
-    const int src = auto_src(2 * k2, g, log_n);
-    const ulonglong2 v = reinterpret_cast<const ulonglong2*>(row)[src >> 1];
-    vx = (src & 1) ? v.y : v.x;
-    vy = (src & 1) ? v.x : v.y;
-}
-
-// acc[t][h][x][k] = sum_j M_j[x][k] * key_t[j][h][px][k], where M_j[x] = ext[t][j][x] for x
-// outside digit j and the item's input d (through its automorphism) for x in digit j. The
-// products are summed in 128 bits and reduced once; the limb index is the slowest, so one limb's
-// rows of a shared key stay in L2 while every item reads them.
-// FANOUT: item t's raised digits are those of source src_of[t] (its c1 raised once for all the
-// items that rotate it) and every digit is read through item t's automorphism.
-template <bool FANOUT>
-__global__ void __launch_bounds__(256, 4) ks_inner_kernel(u64* acc, const u64* __restrict__ ext,
-                                                          const KsItem* __restrict__ tab, const int* __restrict__ src_of,
-                                                          int items, int dn, int alpha, int next, int level, int L,
-                                                          int n_ext, int log_n, const Prime* __restrict__ pr) {
-    const size_t half = (size_t)1 << (log_n - 1);
-    const size_t total = (size_t)items * next * half;
-    const int l1 = level + 1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int k2 = (int)(e & (half - 1));
-        const size_t row = e >> (log_n - 1);
-        const int t = (int)(row % items), x = (int)(row / items);
-        const int px = x < l1 ? x : x + (L - level);
-        const Prime P = pr[px];
-        const KsItem it = tab[t];
-        const int own = x < l1 ? x / alpha : -1;
-        u64 a0x = 0, h0x = 0, a0y = 0, h0y = 0, a1x = 0, h1x = 0, a1y = 0, h1y = 0;
-        const int st = FANOUT ? src_of[t] : t;
-        for (int j = 0; j < dn; j++) {
-            u64 vx, vy;
-            if (FANOUT) {
-                const u64* src = j == own ? it.d + ((size_t)x << log_n) : ext + ((size_t)((st * dn + j) * next + x) << log_n);
-                load_pair_auto(src, k2, (int)it.galois, log_n, vx, vy);
-            } else if (j == own && it.galois != 1) {
-                load_pair_auto(it.d + ((size_t)x << log_n), k2, (int)it.galois, log_n, vx, vy);
-            } else {
-                const u64* src = j == own ? it.d + ((size_t)x << log_n) : ext + ((size_t)((t * dn + j) * next + x) << log_n);
-                const ulonglong2 v = reinterpret_cast<const ulonglong2*>(src)[k2];
-                vx = v.x;
-                vy = v.y;
-            }
-            const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 0) * n_ext + px) << log_n))[k2];
-            const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 1) * n_ext + px) << log_n))[k2];
-            mac128_cc(a0x, h0x, vx, kb.x);
-            mac128_cc(a0y, h0y, vy, kb.y);
-            mac128_cc(a1x, h1x, vx, ka.x);
-            mac128_cc(a1y, h1y, vy, ka.y);
-        }
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] =
-            make_ulonglong2(reduce128(a0x, h0x, P), reduce128(a0y, h0y, P));
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] =
-            make_ulonglong2(reduce128(a1x, h1x, P), reduce128(a1y, h1y, P));
-    }
-}
-
-// Hoisted inner product: acc[t][h][x][k] = sum_r sum_j M_j[x][pi_r(k)] * key_r[j][h][px][k], where
-// pi_r is the slot map of rotation r and M_j[x] is ext[t][j][x] outside digit j and the item's c1
-// inside it; the 128-bit sums are reduced once. For x < l1 also c0sum[t][x][k] = c0[x][k] +
-// sum_r c0[x][pi_r(k)]. The limb index is the slowest, so one limb's rows of all kp - 1 keys stay in
-// L2 while every item reads them.
-__global__ void __launch_bounds__(256, 3) ks_hoist_inner_kernel(
-    u64* acc, u64* c0sum, const u64* __restrict__ ext, const KsItem* __restrict__ tab,
-    const HoistStep* __restrict__ steps, int n_steps, int items, int dn, int alpha, int next, int level, int L, int n_ext,
-    int log_n, const Prime* __restrict__ pr) {
-    const size_t half = (size_t)1 << (log_n - 1);
-    const size_t total = (size_t)items * next * half;
-    const int l1 = level + 1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int k2 = (int)(e & (half - 1));
-        const size_t row = e >> (log_n - 1);
-        const int t = (int)(row % items), x = (int)(row / items);
-        const int px = x < l1 ? x : x + (L - level);
-        const int own = x < l1 ? x / alpha : -1;
-        // digit j's row of this limb, in pairs: ext rows (stride next*N) and the item's c1 for its own digit
-        const ulonglong2* ext0 = reinterpret_cast<const ulonglong2*>(ext) + (((size_t)t * dn * next + x) << (log_n - 1));
-        const ulonglong2* own_row = reinterpret_cast<const ulonglong2*>(tab[t].d) + ((size_t)x << (log_n - 1));
-        const size_t dstride = (size_t)next << (log_n - 1);
-        const size_t kstride = (size_t)n_ext << (log_n - 1);
-        const size_t koff = ((size_t)px << (log_n - 1)) + k2;
-        u64 a0x = 0, h0x = 0, a0y = 0, h0y = 0, a1x = 0, h1x = 0, a1y = 0, h1y = 0;
-        for (int r = 0; r < n_steps; r++) {
-            const HoistStep st = steps[r];
-            const int src = auto_src(2 * k2, (int)st.galois, log_n);
-            const int sp = src >> 1;
-            const bool sw = src & 1;
-            const ulonglong2* kr = reinterpret_cast<const ulonglong2*>(st.key) + koff;
-            for (int j = 0; j < dn; j++) {
-                const ulonglong2 v = (j == own ? own_row : ext0 + (size_t)j * dstride)[sp];
-                const u64 vx = sw ? v.y : v.x, vy = sw ? v.x : v.y;
-                const ulonglong2 kb = kr[(size_t)(2 * j) * kstride];
-                const ulonglong2 ka = kr[(size_t)(2 * j + 1) * kstride];
-                mac128(a0x, h0x, vx, kb.x);
-                mac128(a0y, h0y, vy, kb.y);
-                mac128(a1x, h1x, vx, ka.x);
-                mac128(a1y, h1y, vy, ka.y);
-            }
-        }
-        const Prime P = pr[px];
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 0) * next + x) << log_n))[k2] =
-            make_ulonglong2(reduce128(a0x, h0x, P), reduce128(a0y, h0y, P));
-        reinterpret_cast<ulonglong2*>(acc + ((size_t)((t * 2 + 1) * next + x) << log_n))[k2] =
-            make_ulonglong2(reduce128(a1x, h1x, P), reduce128(a1y, h1y, P));
-        if (x < l1) {
-            const u64* c0 = tab[t].addP0 + ((size_t)x << log_n);
-            const ulonglong2 self = reinterpret_cast<const ulonglong2*>(c0)[k2];
-            u64 sx = self.x, sy = self.y;
-            for (int r = 0; r < n_steps; r++) {
-                u64 vx, vy;
-                load_pair_auto(c0, k2, (int)steps[r].galois, log_n, vx, vy);
-                sx = add_mod(sx, vx, P.q);
-                sy = add_mod(sy, vy, P.q);
-            }
-            reinterpret_cast<ulonglong2*>(c0sum + ((size_t)(t * l1 + x) << log_n))[k2] = make_ulonglong2(sx, sy);
-        }
-    }
-}
-
-inline unsigned grid1(size_t work) {
+[[maybe_unused]] inline unsigned grid1(size_t work) {
     size_t b = (work + 255) / 256;
     return (unsigned)std::min<size_t>(std::max<size_t>(b, 1), (size_t)1 << 30);
 }
@@ -579,17 +422,30 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
         ks_transform<false, LD_CONV, ST_LAST>(c, d_r2, (int)r2.size(), none, K_NTT_FWD, 16.0 * r2.size() * n, s);
 
         // K3: key inner product
+        InnerArgs ia{};
+        ia.acc = acc;
+        ia.ext = ext;
+        ia.tab = d_items;
+        ia.src_of = d_src_of;
+        ia.items = items;
+        ia.dn = dn;
+        ia.alpha = A;
+        ia.next = next;
+        ia.level = level;
+        ia.L = L;
+        ia.n_ext = c.n_ext;
+        ia.log_n = c.log_n;
+        ia.pr = c.d_primes;
         if (!hk) {
             LaunchScope _ls(c.prof, K_KS_INNER,
                             8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next),
                             s);
-            if (fan)
-                ks_inner_kernel<true><<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(
-                    acc, ext, d_items, d_src_of, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
-            else
-                ks_inner_kernel<false><<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(
-                    acc, ext, d_items, nullptr, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
-            CK(cudaGetLastError());
+            bool shared = !fan;
+            for (int t = 1; t < items && shared; t++)
+                shared = it[t].key == it[0].key && it[t].galois == it[0].galois;
+            ia.shared_key = shared ? it[0].key : nullptr;
+            ia.shared_galois = shared ? it[0].galois : 1;
+            launch_ks_inner(ia, fan, c.tune.inner, c.max_prime_bits, s);
         } else {
             // reads: the raised digits and c0 once per item, every key once; writes acc and c0sum
             u64* c0sum = c.scratch_u64("ks_c0sum", (size_t)items * l1 * n);
@@ -599,10 +455,10 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
                             s);
             std::vector<HoistStep> hs;
             for (int r = 0; r < hk->count; r++) hs.push_back({hk->key[r], (long long)hk->galois[r]});
-            const HoistStep* d_hs = c.arena.push_vec(hs, s);
-            ks_hoist_inner_kernel<<<grid1((size_t)items * next * n / 2), 256, 0, s>>>(
-                acc, c0sum, ext, d_items, d_hs, hk->count, items, dn, A, next, level, L, c.n_ext, c.log_n, c.d_primes);
-            CK(cudaGetLastError());
+            ia.steps = c.arena.push_vec(hs, s);
+            ia.n_steps = hk->count;
+            ia.c0sum = c0sum;
+            launch_ks_hoist_inner(ia, c.tune.hoist, c.max_prime_bits, s);
             // the combine adds c0sum to component 0 and c1 to component 1
             std::vector<KsItem> it5(it);
             for (int t = 0; t < items; t++) {

@@ -1,0 +1,216 @@
+// tune.cu — the autotuner: times every launch variant of a kernel family on a synthetic batch of the
+// context's own shape and keeps the fastest for the context. Every variant of a family computes the
+// same bits (the choice changes speed only), so tuning never changes a result.
+//
+// Families:
+//   ks_hoist_inner  K3 of the hoisted rotate-and-sum (kp - 1 = 15 rotations, the epoch's per-group
+//                   rotate-and-sum), variants of ks_inner.cuh
+//   ks_inner        K3 of a relinearisation (every item shares the key), variants of ks_inner.cuh
+// The synthetic operands are uniform residues below each prime; the kernels' work does not depend
+// on the values.
+#include <cstring>
+#include <vector>
+
+#include "ks_inner.cuh"
+
+using namespace fhe;
+
+namespace {
+
+struct Family {
+    const char* name;
+    int n_variants;
+    const char* const* variant_names;
+    int Ctx::Tune::*field;
+};
+
+const Family kFamilies[] = {
+    {"ks_hoist_inner", INNER_N_VARIANTS, kInnerVariantNames, &Ctx::Tune::hoist},
+    {"ks_inner", INNER_N_VARIANTS, kInnerVariantNames, &Ctx::Tune::inner},
+};
+constexpr int kNumFamilies = sizeof(kFamilies) / sizeof(kFamilies[0]);
+
+__global__ void fill_residues(u64* p, size_t words, int log_n, int n_limbs, const Prime* __restrict__ pr, u64 seed) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < words; e += (size_t)gridDim.x * blockDim.x) {
+        const int limb = (int)((e >> log_n) % (size_t)n_limbs);
+        u64 z = (e + seed) * 0x9E3779B97F4A7C15ull;
+        z ^= z >> 31;
+        p[e] = z % pr[limb].q;
+    }
+}
+
+struct DevTmp {
+    std::vector<void*> ptrs;
+    u64* get(size_t words) {
+        void* p = nullptr;
+        CK(cudaMalloc(&p, words * sizeof(u64)));
+        ptrs.push_back(p);
+        return (u64*)p;
+    }
+    ~DevTmp() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+};
+
+template <typename F>
+double time_ms(F&& run, int reps) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    run();  // warm-up
+    double best = 1e30;
+    for (int r = 0; r < reps; r++) {
+        CK(cudaEventRecord(e0));
+        run();
+        CK(cudaEventRecord(e1));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+// Time every variant of the two inner-product families at `level`.
+void tune_inner(Ctx& c, int level, std::vector<fhe_tune_result>& out) {
+    const int n = c.n, A = c.alpha, l1 = level + 1, next = l1 + A, dn = c.dnum(level);
+    const int items = c.log_n >= 16 ? 32 : 64, steps = 15;
+    DevTmp tmp;
+    // ext: [items][dn][next][N]; keys: [steps][dnum_top][2][n_ext][N]; inputs [items][L+1][N]; acc, c0sum
+    const size_t key_words = c.key_words();
+    u64* ext = tmp.get((size_t)items * dn * next * n);
+    u64* keys = tmp.get((size_t)steps * key_words);
+    u64* din = tmp.get((size_t)items * (c.L + 1) * n);
+    u64* c0 = tmp.get((size_t)items * (c.L + 1) * n);
+    u64* acc = tmp.get((size_t)items * 2 * next * n);
+    u64* c0sum = tmp.get((size_t)items * l1 * n);
+    // the key rows are laid out [digit][2][n_ext]; residues below the smallest prime serve every row
+    fill_residues<<<1024, 256>>>(ext, (size_t)items * dn * next * n, c.log_n, 1, c.d_primes, 1);
+    fill_residues<<<1024, 256>>>(keys, (size_t)steps * key_words, c.log_n, 1, c.d_primes, 2);
+    fill_residues<<<1024, 256>>>(din, (size_t)items * (c.L + 1) * n, c.log_n, 1, c.d_primes, 3);
+    fill_residues<<<1024, 256>>>(c0, (size_t)items * (c.L + 1) * n, c.log_n, 1, c.d_primes, 4);
+    CK(cudaGetLastError());
+    std::vector<KsItem> it(items);
+    for (int t = 0; t < items; t++) {
+        it[t] = KsItem{din + (size_t)t * (c.L + 1) * n, keys, c0 + (size_t)t * (c.L + 1) * n, nullptr, nullptr,
+                       nullptr, nullptr, 1};
+    }
+    std::vector<HoistStep> hs(steps);
+    for (int r = 0; r < steps; r++) hs[r] = {keys + (size_t)r * key_words, (long long)c.galois(r + 1)};
+    KsItem* d_it = nullptr;
+    HoistStep* d_hs = nullptr;
+    CK(cudaMalloc(&d_it, sizeof(KsItem) * items));
+    CK(cudaMalloc(&d_hs, sizeof(HoistStep) * steps));
+    tmp.ptrs.push_back(d_it);
+    tmp.ptrs.push_back(d_hs);
+    CK(cudaMemcpy(d_it, it.data(), sizeof(KsItem) * items, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_hs, hs.data(), sizeof(HoistStep) * steps, cudaMemcpyHostToDevice));
+    InnerArgs ia{};
+    ia.acc = acc;
+    ia.c0sum = c0sum;
+    ia.ext = ext;
+    ia.tab = d_it;
+    ia.items = items;
+    ia.dn = dn;
+    ia.alpha = A;
+    ia.next = next;
+    ia.level = level;
+    ia.L = c.L;
+    ia.n_ext = c.n_ext;
+    ia.log_n = c.log_n;
+    ia.pr = c.d_primes;
+    for (int f = 0; f < kNumFamilies; f++) {
+        const Family& fam = kFamilies[f];
+        const bool hoist = f == 0;
+        InnerArgs a = ia;
+        if (hoist) {
+            a.steps = d_hs;
+            a.n_steps = steps;
+        } else {
+            a.shared_key = keys;
+            a.shared_galois = 1;
+        }
+        double best = 1e30;
+        int best_v = 0;
+        const size_t first = out.size();
+        for (int v = 0; v < fam.n_variants; v++) {
+            const double ms = time_ms([&] {
+                if (hoist) launch_ks_hoist_inner(a, v, c.max_prime_bits, (cudaStream_t)0);
+                else launch_ks_inner(a, false, v, c.max_prime_bits, (cudaStream_t)0);
+            }, 3);
+            out.push_back(fhe_tune_result{fam.name, fam.variant_names[v], 0, ms});
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        out[first + best_v].chosen = 1;
+        c.tune.*fam.field = best_v;
+    }
+    CK(cudaDeviceSynchronize());
+}
+
+template <typename F>
+int guarded(Ctx& c, F&& f) {
+    try {
+        c.last_error.clear();
+        CK(cudaSetDevice(c.device));
+        f();
+        return FHE_OK;
+    } catch (const FheException& e) {
+        c.last_error = e.msg;
+        return e.code;
+    } catch (const std::exception& e) {
+        c.last_error = e.what();
+        return FHE_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace
+
+extern "C" int fhe_autotune(fhe_ctx* ctx, int32_t level, fhe_tune_result* out, int32_t cap) {
+    if (!ctx) return FHE_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    std::vector<fhe_tune_result> res;
+    int rc = guarded(c, [&] {
+        if (level < 1 || level > c.L) fail(FHE_ERR_INVALID_ARG, "autotune level out of range");
+        if (cap < 0 || (cap > 0 && !out)) fail(FHE_ERR_INVALID_ARG, "bad output array");
+        CK(cudaDeviceSynchronize());
+        tune_inner(c, level, res);
+    });
+    if (rc) return rc;
+    const int n = (int)std::min<size_t>(res.size(), (size_t)cap);
+    for (int i = 0; i < n; i++) out[i] = res[i];
+    return (int)res.size();
+}
+
+extern "C" int fhe_set_variant(fhe_ctx* ctx, const char* family, const char* variant) {
+    if (!ctx) return FHE_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    return guarded(c, [&] {
+        if (!family || !variant) fail(FHE_ERR_INVALID_ARG, "null family or variant");
+        for (const Family& fam : kFamilies) {
+            if (std::strcmp(fam.name, family) != 0) continue;
+            for (int v = 0; v < fam.n_variants; v++)
+                if (std::strcmp(fam.variant_names[v], variant) == 0) {
+                    c.tune.*fam.field = v;
+                    return;
+                }
+            fail(FHE_ERR_INVALID_ARG, std::string("unknown variant ") + variant + " of " + family);
+        }
+        fail(FHE_ERR_INVALID_ARG, std::string("unknown kernel family ") + family);
+    });
+}
+
+extern "C" int fhe_get_variant(const fhe_ctx* ctx, const char* family, const char** variant) {
+    if (!ctx || !family || !variant) return FHE_ERR_INVALID_ARG;
+    const Ctx& c = ctx->c;
+    for (const Family& fam : kFamilies)
+        if (std::strcmp(fam.name, family) == 0) {
+            *variant = fam.variant_names[c.tune.*fam.field];
+            return FHE_OK;
+        }
+    return FHE_ERR_INVALID_ARG;
+}

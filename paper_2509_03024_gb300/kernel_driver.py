@@ -4,6 +4,7 @@
   python -m paper_2509_03024_gb300.kernel_driver keyswitch --preset paper --count 64 [--reps 3]
   python -m paper_2509_03024_gb300.kernel_driver rotsum --preset paper --count 64 --kp 16 [--reps 3]
   python -m paper_2509_03024_gb300.kernel_driver probe --preset paper [--reps 2000]
+  python -m paper_2509_03024_gb300.kernel_driver tune --preset paper [--level L]
 
 `ntt` transforms `rows` limbs of N residues in place (rows / (L+1) polynomials
 of L+1 limbs); `keyswitch` rotates `count` top-level ciphertexts by one slot
@@ -11,7 +12,9 @@ of L+1 limbs); `keyswitch` rotates `count` top-level ciphertexts by one slot
 slots on `count` ciphertexts one level below the top (the level of the per-group
 product in an epoch). Prints CUDA-event timings per repetition and, for the last
 repetition, the device time of each kernel class; `probe` prints the register-only
-butterfly rate of fhe_probe_butterfly_rate (`reps` loop trips).
+butterfly rate of fhe_probe_butterfly_rate (`reps` loop trips) and the integer-pipe rates of
+fhe_probe_int_pipe; `tune` runs the autotuner at `level` (default top - 1) and prints every
+variant's time.
 """
 from __future__ import annotations
 
@@ -27,7 +30,9 @@ def main():
     from paper_2509_03024_gb300.workloads import PRESETS
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("kind", choices=["ntt", "keyswitch", "rotsum", "probe"])
+    ap.add_argument("kind", choices=["ntt", "keyswitch", "rotsum", "probe", "tune"])
+    ap.add_argument("--level", type=int, default=None)
+    ap.add_argument("--variant", default=None, help="inner-product variant to use (ks_inner and ks_hoist_inner)")
     ap.add_argument("--kp", type=int, default=16)
     ap.add_argument("--preset", default="paper")
     ap.add_argument("--rows", type=int, default=1024)
@@ -39,8 +44,15 @@ def main():
     ctx = capi.Context.from_preset(PRESETS[args.preset])
     if args.kind == "probe":
         print(json.dumps({"kind": "probe", "preset": args.preset, "reps": args.reps,
-                          "gbfly_per_s": ctx.probe_butterfly_rate(args.reps)}))
+                          "gbfly_per_s": ctx.probe_butterfly_rate(args.reps),
+                          "int_pipe": ctx.probe_int_pipe(max(1, args.reps // 4))}))
         return
+    if args.kind == "tune":
+        print(json.dumps({"kind": "tune", "preset": args.preset, "results": ctx.autotune(args.level)}))
+        return
+    if args.variant:
+        ctx.set_variant("ks_inner", args.variant)
+        ctx.set_variant("ks_hoist_inner", args.variant)
     if args.kind == "keyswitch":
         ctx.keygen(1, [1])
     elif args.kind == "rotsum":

@@ -60,6 +60,8 @@ def _prototypes():
 def _matches(ct, base, stars):
     if stars == 0:
         return ct is _CTYPE[base]
+    if base == "char":      # strings in, and an out-parameter receiving a static string
+        return ct is (ctypes.c_char_p if stars == 1 else ctypes.POINTER(ctypes.c_char_p))
     if stars == 2:          # an out-parameter receiving a handle
         return ct is ctypes.POINTER(ctypes.c_void_p)
     # one level of pointer: plain buffers and handles are void*, struct pointers may be typed
@@ -101,7 +103,8 @@ def _struct_fields(name):
 
 @pytest.mark.parametrize("cname,pyname", [("fhe_params", "Params"), ("fhe_ctx_info", "CtxInfo"),
                                           ("fhe_kernel_stat", "KernelStat"), ("fhe_mf_plan_info", "PlanInfo"),
-                                          ("fhe_int_pipe_rates", "IntPipeRates")])
+                                          ("fhe_int_pipe_rates", "IntPipeRates"),
+                                          ("fhe_tune_result", "TuneResult")])
 def test_binding_structs_match_the_header(cname, pyname):
     from paper_2509_03024_gb300 import capi
     fields = _struct_fields(cname)

@@ -1,0 +1,78 @@
+"""Every launch variant the autotuner chooses between gives the same bits: the key inner products
+of a hoisted rotate-and-sum, a relinearisation, a rotation and an epoch (tree fan-out included) are
+compared across variants, and fhe_autotune keeps exactly one variant per family."""
+import numpy as np
+import pytest
+
+from paper_2509_03024_gb300 import capi
+from paper_2509_03024_gb300 import workloads as W
+from tests.gpu_common import ct_slice, gpu_ctx, torch
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["v0", "c1", "w1", "c2", "w2", "w4"]
+
+
+@pytest.mark.parametrize("preset", ["t11a2", "paper"])
+def test_inner_variants_bit_identical(preset):
+    ctx = gpu_ctx(preset, 21, list(range(1, 16)))
+    rng = np.random.default_rng(1)
+    count = 5                                    # odd: the multi-item variants have a ragged tail
+    a, b = ctx.empty_ct(count), ctx.empty_ct(count)
+    for t in range(count):
+        ctx.encrypt(rng.normal(size=64), ctx.top, 100 + t, ct_slice(ctx, a, t))
+        ctx.encrypt(rng.normal(size=64), ctx.top, 200 + t, ct_slice(ctx, b, t))
+    ref = {}
+    for v in VARIANTS:
+        ctx.set_variant("ks_hoist_inner", v)
+        ctx.set_variant("ks_inner", v)
+        assert ctx.get_variant("ks_inner") == v
+        rs, pr, ro = ctx.empty_ct(count), ctx.empty_ct(count), ctx.empty_ct(count)
+        ctx.rotate_sum(a.clone(), rs, count, ctx.top - 1, 16)
+        ctx.mul_relin_rescale(a, b, pr, count, ctx.top)
+        ctx.rotate(a, ro, count, ctx.top, 3)
+        torch.cuda.synchronize()
+        got = (rs, pr, ro)
+        if not ref:
+            ref = got
+        for name, x, y in zip(("rotate_sum", "mul_relin_rescale", "rotate"), got, ref):
+            assert torch.equal(x, y), f"{preset}: variant {v} changes {name}"
+
+
+def test_epoch_identical_under_every_variant():
+    csr = W.uniform_ratings(60, 200, 0.04, 9)
+    rng = np.random.default_rng(2)
+    k = 10
+    U, V = rng.normal(0, 0.1, (csr.n, k)), rng.normal(0, 0.1, (csr.m, k))
+    ctx = gpu_ctx("t11a2", 23)
+    ctx.add_rotation_keys(ctx.mf_rotation_steps(k))
+    plan = capi.MfPlan(ctx, csr.n, csr.m, k, csr.row_ptr, csr.col_idx, csr.vals)
+    U0, V0 = ctx.empty_ct(plan.n_ub), ctx.empty_ct(plan.n_vb)
+    plan.encrypt_factors(0, U, U0)
+    plan.encrypt_factors(1, V, V0)
+    ref = None
+    for v in ("v0", "w2", "c1", "w4"):
+        ctx.set_variant("ks_hoist_inner", v)
+        ctx.set_variant("ks_inner", v)
+        UD, VD = U0.clone(), V0.clone()
+        plan.sgd_epoch(UD, VD, ctx.top, 0.01, 0.02)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = (UD, VD)
+        assert torch.equal(UD, ref[0]) and torch.equal(VD, ref[1]), f"variant {v} changes the epoch"
+
+
+def test_autotune_keeps_one_variant_per_family():
+    ctx = gpu_ctx("t11a2", 24)
+    res = ctx.autotune()
+    fams = {r["family"] for r in res}
+    assert fams == {"ks_hoist_inner", "ks_inner"}
+    for f in fams:
+        rows = [r for r in res if r["family"] == f]
+        assert sorted(r["variant"] for r in rows) == sorted(VARIANTS)
+        chosen = [r for r in rows if r["chosen"]]
+        assert len(chosen) == 1 and all(r["ms"] > 0 for r in rows)
+        assert chosen[0]["ms"] == min(r["ms"] for r in rows)
+        assert ctx.get_variant(f) == chosen[0]["variant"]
+    with pytest.raises(capi.FheError, match="INVALID_ARG"):
+        ctx.set_variant("ks_inner", "nope")
