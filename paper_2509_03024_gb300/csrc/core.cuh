@@ -288,7 +288,8 @@ struct Ctx {
         int inner = 0;  // plain / fan-out key inner product (InnerVariant of ks_inner.cuh)
         int hoist = 0;  // hoisted rotate-and-sum inner product
     } tune;
-    int max_prime_bits = 0;
+    int max_prime_bits = 0;       // over every prime
+    int max_data_prime_bits = 0;  // over the data primes q_0..q_L
 
     std::string last_error;
     Arena arena;

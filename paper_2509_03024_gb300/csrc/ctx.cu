@@ -1054,6 +1054,7 @@ int fhe_ctx_create(const fhe_params* p, fhe_ctx** out) {
         c.primes = choose_primes(c.log_n, bits);
         for (u64 q : c.primes) c.hprimes.push_back(make_prime(q));
         for (const Prime& P : c.hprimes) c.max_prime_bits = std::max(c.max_prime_bits, (int)P.b);
+        for (int i = 0; i <= c.L; i++) c.max_data_prime_bits = std::max(c.max_data_prime_bits, (int)c.hprimes[i].b);
         c.d_primes = dupload(c.hprimes);
         ntt_init();
         build_tables(c);

@@ -445,7 +445,7 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
                 shared = it[t].key == it[0].key && it[t].galois == it[0].galois;
             ia.shared_key = shared ? it[0].key : nullptr;
             ia.shared_galois = shared ? it[0].galois : 1;
-            launch_ks_inner(ia, fan, c.tune.inner, c.max_prime_bits, s);
+            launch_ks_inner(ia, fan, c.tune.inner, c.max_data_prime_bits, s);
         } else {
             // reads: the raised digits and c0 once per item, every key once; writes acc and c0sum
             u64* c0sum = c.scratch_u64("ks_c0sum", (size_t)items * l1 * n);
@@ -458,7 +458,7 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
             ia.steps = c.arena.push_vec(hs, s);
             ia.n_steps = hk->count;
             ia.c0sum = c0sum;
-            launch_ks_hoist_inner(ia, c.tune.hoist, c.max_prime_bits, s);
+            launch_ks_hoist_inner(ia, c.tune.hoist, c.max_data_prime_bits, s);
             // the combine adds c0sum to component 0 and c1 to component 1
             std::vector<KsItem> it5(it);
             for (int t = 0; t < items; t++) {

@@ -6,10 +6,10 @@
 // M_j[x] is the raised digit j at extended limb x (the item's own input on the limbs of digit j),
 // pi_r the slot map of rotation r. Products are summed exactly in 128 bits and reduced once, so the
 // result is independent of the formulation; the variants differ in
-//   * the multiply-accumulate: "C" (the product's low and high halves in C and a carry compare) or
-//     "W" (four 32 x 32 -> 64-bit partial products folded into three 64-bit column sums by
-//     mad.wide.u32, with 32-bit carry counters for the two columns that can wrap; needs operands
-//     below 2^60 and at most 256 terms so the top column cannot wrap),
+//   * the multiply-accumulate: "C" (the product's low and high halves in C and a carry compare),
+//     "P32" (a schoolbook chain of 32-bit mad.lo / mad.hi with carries) or, for data primes below
+//     2^50, "S25" (operands split at bit 25: four mad.wide.u32 partial products into three 64-bit
+//     column sums that cannot wrap, no additions at all),
 //   * items per thread: items that share a key read each key pair once for all of them,
 //   * the launch shape: blockIdx.y is the extended limb, so every block of one limb runs before the
 //     next limb's, keeping that limb's key rows in L2 while every item reads them.
@@ -22,7 +22,7 @@
 
 namespace fhe {
 
-const char* const kInnerVariantNames[INNER_N_VARIANTS] = {"v0", "c1", "w1", "c2", "w2", "w4"};
+const char* const kInnerVariantNames[INNER_N_VARIANTS] = {"v0", "c1", "p1", "s1", "s2"};
 
 namespace {
 
@@ -56,31 +56,53 @@ struct MacP {  // PTX 64-bit multiply-add with carry (the one-item legacy form o
     __device__ __forceinline__ u64 reduce(const Prime& P) const { return reduce128(lo, hi, P); }
 };
 
-// a = a0 + 2^32 a1, b = b0 + 2^32 b1 (a1, b1 < 2^28): a b = a0 b0 + 2^32 (a0 b1 + a1 b0) + 2^64 a1 b1.
-// L = sum a0 b0 and X = sum (a0 b1 + a1 b0) wrap mod 2^64 and count their wraps in cl, cx; H = sum a1 b1
-// stays below 2^64 for at most 256 terms.
-struct MacW {
-    u64 L = 0, X = 0, H = 0;
-    u32 cl = 0, cx = 0;
+// Schoolbook on 32-bit words in one carry chain per row: a0 b0 and a1 b1 first, then each cross
+// product (eight mad.lo / mad.hi with carries and two carry propagations).
+struct MacP32 {
+    u32 r0 = 0, r1 = 0, r2 = 0, r3 = 0;
     __device__ __forceinline__ void mac(u64 a, u64 b) {
         const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
-        u64 t;
-        asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(t) : "r"(a0), "r"(b0), "l"(L));
-        cl += t < L ? 1u : 0u;
-        L = t;
-        asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(t) : "r"(a0), "r"(b1), "l"(X));
-        cx += t < X ? 1u : 0u;
-        X = t;
-        asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(t) : "r"(a1), "r"(b0), "l"(X));
-        cx += t < X ? 1u : 0u;
-        X = t;
-        asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(H) : "r"(a1), "r"(b1));
+        asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+            "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+            "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+            "madc.hi.u32 %3, %5, %7, %3;\n\t"
+            "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+            "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+            "addc.u32 %3, %3, 0;\n\t"
+            "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+            "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+            "addc.u32 %3, %3, 0;"
+            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+            : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
     }
     __device__ __forceinline__ u64 reduce(const Prime& P) const {
-        // sum = L + 2^64 cl + 2^32 (X + 2^64 cx) + 2^64 H
-        const u64 lo = L + (X << 32);
-        const u64 hi = H + (X >> 32) + ((u64)cx << 32) + cl + (lo < L ? 1 : 0);
-        return reduce128(lo, hi, P);
+        return reduce128(((u64)r1 << 32) | r0, ((u64)r3 << 32) | r2, P);
+    }
+};
+
+// Operands below 2^50 split at bit 25: a b = a0 b0 + 2^25 (a0 b1 + a1 b0) + 2^50 a1 b1 with every
+// partial product below 2^50, so three 64-bit column sums take up to 2^13 terms without a carry:
+// four mad.wide.u32 per multiply-accumulate and no additions.
+struct MacS25 {
+    u64 C0 = 0, C1 = 0, C2 = 0;
+    __device__ __forceinline__ void mac(u64 a, u64 b) {
+        const u32 m = (1u << 25) - 1u;
+        const u32 a0 = (u32)a & m, a1 = (u32)(a >> 25), b0 = (u32)b & m, b1 = (u32)(b >> 25);
+        asm("mad.wide.u32 %0, %3, %5, %0;\n\t"
+            "mad.wide.u32 %1, %3, %6, %1;\n\t"
+            "mad.wide.u32 %1, %4, %5, %1;\n\t"
+            "mad.wide.u32 %2, %4, %6, %2;"
+            : "+l"(C0), "+l"(C1), "+l"(C2)
+            : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    }
+    __device__ __forceinline__ u64 reduce(const Prime& P) const {
+        // C0 + 2^25 C1 + 2^50 C2 as (hi, lo)
+        u64 lo = C0 + (C1 << 25);
+        u64 hi = (C1 >> 39) + (lo < C0 ? 1 : 0);
+        const u64 add = C2 << 50;
+        const u64 lo2 = lo + add;
+        hi += (C2 >> 14) + (lo2 < lo ? 1 : 0);
+        return reduce128(lo2, hi, P);
     }
 };
 
@@ -193,18 +215,15 @@ __global__ void __launch_bounds__(256, 3) hoist_v0_kernel(InnerArgs a) {
 
 // Thread (blockIdx.x * 256 + threadIdx.x) = (item group, pair k2) with k2 fastest; blockIdx.y = limb x.
 // Items t0 .. t0 + IPT - 1 of a group; a ragged last group repeats its last item and skips its stores.
+// The data limbs (x <= level) use the multiply-accumulate MACD when every data prime has at most 50
+// bits (a.split25), the special limbs and every other case MACS; the branch is uniform per block.
 
 // Plain / fan-out: every item of a thread uses the key `key` and the automorphism `g` (IPT > 1 only
 // when the items share them); FANOUT reads item t's digits from source src_of[t] through its
 // automorphism.
 template <class MAC, int IPT, bool FANOUT>
-__global__ void __launch_bounds__(256) inner2_kernel(InnerArgs a) {
+__device__ __forceinline__ void inner2_body(const InnerArgs& a, int x, int k2, int t0) {
     const int log_n = a.log_n, hl = log_n - 1;
-    const int x = blockIdx.y;
-    const unsigned e = blockIdx.x * 256u + threadIdx.x;
-    const int k2 = (int)(e & ((1u << hl) - 1u));
-    const int t0 = (int)(e >> hl) * IPT;
-    if (t0 >= a.items) return;
     const int l1 = a.level + 1;
     const int px = x < l1 ? x : x + (a.L - a.level);
     const int own = x < l1 ? x / a.alpha : -1;
@@ -260,14 +279,21 @@ __global__ void __launch_bounds__(256) inner2_kernel(InnerArgs a) {
     }
 }
 
-template <class MAC, int IPT>
-__global__ void __launch_bounds__(256) hoist2_kernel(InnerArgs a) {
-    const int log_n = a.log_n, hl = log_n - 1;
+template <class MACD, class MACS, int IPT, bool FANOUT>
+__global__ void __launch_bounds__(256) inner2_kernel(InnerArgs a) {
+    const int hl = a.log_n - 1;
     const int x = blockIdx.y;
     const unsigned e = blockIdx.x * 256u + threadIdx.x;
     const int k2 = (int)(e & ((1u << hl) - 1u));
     const int t0 = (int)(e >> hl) * IPT;
     if (t0 >= a.items) return;
+    if (x <= a.level && a.split25) inner2_body<MACD, IPT, FANOUT>(a, x, k2, t0);
+    else inner2_body<MACS, IPT, FANOUT>(a, x, k2, t0);
+}
+
+template <class MAC, int IPT>
+__device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, int t0) {
+    const int log_n = a.log_n, hl = log_n - 1;
     const int l1 = a.level + 1;
     const int px = x < l1 ? x : x + (a.L - a.level);
     const int own = x < l1 ? x / a.alpha : -1;
@@ -327,6 +353,18 @@ __global__ void __launch_bounds__(256) hoist2_kernel(InnerArgs a) {
     }
 }
 
+template <class MACD, class MACS, int IPT>
+__global__ void __launch_bounds__(256) hoist2_kernel(InnerArgs a) {
+    const int hl = a.log_n - 1;
+    const int x = blockIdx.y;
+    const unsigned e = blockIdx.x * 256u + threadIdx.x;
+    const int k2 = (int)(e & ((1u << hl) - 1u));
+    const int t0 = (int)(e >> hl) * IPT;
+    if (t0 >= a.items) return;
+    if (x <= a.level && a.split25) hoist2_body<MACD, IPT>(a, x, k2, t0);
+    else hoist2_body<MACS, IPT>(a, x, k2, t0);
+}
+
 inline unsigned grid1(size_t work) {
     size_t b = (work + 255) / 256;
     return (unsigned)std::min<size_t>(std::max<size_t>(b, 1), (size_t)1 << 30);
@@ -338,16 +376,11 @@ inline dim3 grid2(const InnerArgs& a, int ipt) {
     return dim3((unsigned)((threads + 255) / 256), (unsigned)a.next);
 }
 
-// variant -> (column sums?, items per thread)
-void variant_shape(int v, bool& wide, int& ipt) {
-    wide = v == INNER_W1 || v == INNER_W2 || v == INNER_W4;
-    ipt = v == INNER_W4 ? 4 : (v == INNER_C2 || v == INNER_W2) ? 2 : 1;
-}
-
 }  // namespace
 
-void launch_ks_inner(const InnerArgs& a, bool fanout, int variant, int max_prime_bits, cudaStream_t s) {
-    if (a.items == 0) return;
+void launch_ks_inner(const InnerArgs& a0, bool fanout, int variant, int max_data_prime_bits, cudaStream_t s) {
+    if (a0.items == 0) return;
+    InnerArgs a = a0;
     if (variant <= INNER_V0 || variant >= INNER_N_VARIANTS) {
         if (fanout)
             inner_v0_kernel<true><<<grid1((size_t)a.items * a.next << (a.log_n - 1)), 256, 0, s>>>(a);
@@ -356,46 +389,44 @@ void launch_ks_inner(const InnerArgs& a, bool fanout, int variant, int max_prime
         CK(cudaGetLastError());
         return;
     }
-    bool wide;
-    int ipt;
-    variant_shape(variant, wide, ipt);
-    if (wide && (max_prime_bits > 60 || a.dn > 256)) wide = false;
-    if (fanout || !a.shared_key) ipt = 1;
-#define L2(M, I, F) inner2_kernel<M, I, F><<<grid2(a, I), 256, 0, s>>>(a)
-    if (fanout) {
-        if (wide) L2(MacW, 1, true);
-        else L2(MacC, 1, true);
-    } else if (wide) {
-        if (ipt == 4) L2(MacW, 4, false);
-        else if (ipt == 2) L2(MacW, 2, false);
-        else L2(MacW, 1, false);
-    } else {
-        if (ipt == 2) L2(MacC, 2, false);
-        else L2(MacC, 1, false);
+    // split at bit 25 needs data primes below 2^50 and at most 2^13 terms per sum
+    a.split25 = max_data_prime_bits <= 50 && a.dn <= (1 << 13);
+    const bool two = variant == INNER_S2 && !fanout && a.shared_key;
+#define L2(MD, MS, I, F) inner2_kernel<MD, MS, I, F><<<grid2(a, I), 256, 0, s>>>(a)
+    switch (variant) {
+        case INNER_C1:
+            if (fanout) L2(MacC, MacC, 1, true);
+            else L2(MacC, MacC, 1, false);
+            break;
+        case INNER_P1:
+            if (fanout) L2(MacP32, MacP32, 1, true);
+            else L2(MacP32, MacP32, 1, false);
+            break;
+        default:  // S1, S2
+            if (fanout) L2(MacS25, MacP32, 1, true);
+            else if (two) L2(MacS25, MacP32, 2, false);
+            else L2(MacS25, MacP32, 1, false);
+            break;
     }
 #undef L2
     CK(cudaGetLastError());
 }
 
-void launch_ks_hoist_inner(const InnerArgs& a, int variant, int max_prime_bits, cudaStream_t s) {
-    if (a.items == 0) return;
+void launch_ks_hoist_inner(const InnerArgs& a0, int variant, int max_data_prime_bits, cudaStream_t s) {
+    if (a0.items == 0) return;
+    InnerArgs a = a0;
     if (variant <= INNER_V0 || variant >= INNER_N_VARIANTS) {
         hoist_v0_kernel<<<grid1((size_t)a.items * a.next << (a.log_n - 1)), 256, 0, s>>>(a);
         CK(cudaGetLastError());
         return;
     }
-    bool wide;
-    int ipt;
-    variant_shape(variant, wide, ipt);
-    if (wide && (max_prime_bits > 60 || (long long)a.dn * a.n_steps > 256)) wide = false;
-#define H2(M, I) hoist2_kernel<M, I><<<grid2(a, I), 256, 0, s>>>(a)
-    if (wide) {
-        if (ipt == 4) H2(MacW, 4);
-        else if (ipt == 2) H2(MacW, 2);
-        else H2(MacW, 1);
-    } else {
-        if (ipt == 2) H2(MacC, 2);
-        else H2(MacC, 1);
+    a.split25 = max_data_prime_bits <= 50 && (long long)a.dn * a.n_steps <= (1 << 13);
+#define H2(MD, MS, I) hoist2_kernel<MD, MS, I><<<grid2(a, I), 256, 0, s>>>(a)
+    switch (variant) {
+        case INNER_C1: H2(MacC, MacC, 1); break;
+        case INNER_P1: H2(MacP32, MacP32, 1); break;
+        case INNER_S2: H2(MacS25, MacP32, 2); break;
+        default: H2(MacS25, MacP32, 1); break;
     }
 #undef H2
     CK(cudaGetLastError());

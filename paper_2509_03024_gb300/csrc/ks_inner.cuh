@@ -35,24 +35,24 @@ struct InnerArgs {
     const Prime* pr;
     const u64* shared_key;    // plain: non-null when every item uses this key ...
     long long shared_galois;  // ... and this automorphism (then several items per thread may run)
+    int split25;              // set by the launchers: data limbs use the split-at-bit-25 sums
 };
 
 // Launch variants (the autotuner times them; all give identical bits).
 enum InnerVariant {
     INNER_V0 = 0,   // one coefficient pair per thread, grid-stride over (limb, item, pair)
     INNER_C1,       // 2-D grid (pair, item group) x limb; C halves + carry compare; 1 item per thread
-    INNER_W1,       // ... column sums of 32 x 32 -> 64 partial products with carry counters; 1 item
-    INNER_C2,       // C formulation, 2 items per thread sharing the key loads
-    INNER_W2,       // column sums, 2 items per thread
-    INNER_W4,       // column sums, 4 items per thread
+    INNER_P1,       // ... 32-bit schoolbook carry chain; 1 item per thread
+    INNER_S1,       // ... data limbs split at bit 25 into carry-free column sums, special limbs P32
+    INNER_S2,       // S1 with 2 items per thread sharing the key loads (plain: when the items share a key)
     INNER_N_VARIANTS
 };
 extern const char* const kInnerVariantNames[INNER_N_VARIANTS];
 
-// K3 of a plain or fan-out key switch. Falls back to the one-item form when the items do not share
-// a key, and to the C formulation when the column sums could overflow.
-void launch_ks_inner(const InnerArgs& a, bool fanout, int variant, int max_prime_bits, cudaStream_t s);
+// K3 of a plain or fan-out key switch. Falls back to one item per thread when the items do not share
+// a key, and to the 32-bit schoolbook form on data limbs whose primes exceed 50 bits.
+void launch_ks_inner(const InnerArgs& a, bool fanout, int variant, int max_data_prime_bits, cudaStream_t s);
 // K3 of a hoisted rotate-and-sum.
-void launch_ks_hoist_inner(const InnerArgs& a, int variant, int max_prime_bits, cudaStream_t s);
+void launch_ks_hoist_inner(const InnerArgs& a, int variant, int max_data_prime_bits, cudaStream_t s);
 
 }  // namespace fhe

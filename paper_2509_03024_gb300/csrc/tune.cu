@@ -137,8 +137,8 @@ void tune_inner(Ctx& c, int level, std::vector<fhe_tune_result>& out) {
         const size_t first = out.size();
         for (int v = 0; v < fam.n_variants; v++) {
             const double ms = time_ms([&] {
-                if (hoist) launch_ks_hoist_inner(a, v, c.max_prime_bits, (cudaStream_t)0);
-                else launch_ks_inner(a, false, v, c.max_prime_bits, (cudaStream_t)0);
+                if (hoist) launch_ks_hoist_inner(a, v, c.max_data_prime_bits, (cudaStream_t)0);
+                else launch_ks_inner(a, false, v, c.max_data_prime_bits, (cudaStream_t)0);
             }, 3);
             out.push_back(fhe_tune_result{fam.name, fam.variant_names[v], 0, ms});
             if (ms < best) {
