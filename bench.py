@@ -1,28 +1,37 @@
 #!/usr/bin/env python
-"""Throughput of the encrypted CSR matrix-factorisation epoch on one GB300.
+"""Served encrypted matrix factorisation on one GB300: ratings/s with p50/p99 latency, continuous
+batching against one request at a time.
 
-Workload (the paper-scale configuration): 943 users x 1682 items with 100,000
-synthetic ratings shaped like MovieLens-100K (Zipf(1.0) item popularity, >= 20
-ratings per user, MovieLens rating law), a 10 % held-out split, rank k = 10;
-RNS-CKKS with N = 2^15, eight 50-bit data primes, two 60-bit special primes,
-scale 2^50. One step = one encrypted SGD epoch (lr 0.005, lambda 0.02) over the
-90 % training split, starting from top-level encrypted factors (restored from a
-resident copy at the start of each step; the chain holds three epochs).
+Headline workload (the served configuration): resident encrypted item factors, 3706 items x k = 16,
+RNS-CKKS N = 2^16 with thirteen 50-bit data primes and three 60-bit special primes, scale 2^50.
+Requests arrive as a Poisson stream; each carries one user's encrypted CSR rating row (nnz
+log-uniform 5..300, Zipf(1.0) items, MovieLens rating law) and an initial user factor, and is
+answered with the encrypted predicted-rating row over every item after 5 encrypted SGD fold-in
+steps (lr 0.005, lambda 0.02). For every arrival rate in 50, 100, 200, 500, 1000, 2000 req/s the
+same request stream (1000 requests) runs through the continuous-batching server (48 request slots
+under a memory budget) and through the same server with one slot (one request at a time). The line's
+`value`, p50_ms and p99_ms are the batched server's at the top rate; the one-by-one numbers and the
+whole sweep sit beside them. `e2e` repeats the top rate with request ciphertexts uploaded from
+page-locked host memory and predictions downloaded to host memory inside the timed loop.
 
-Metric: training ratings processed per second (whole job over all ranks).
-Multi-GPU runs are independent replicas (one per rank, weak scaling). The same
-line carries the served section (continuous batching of fold-in + predict
-requests against one-at-a-time execution, p50/p99 latency), the roofline of
-the dominant kernel class, the end-to-end rate with host copies, the
-communication report and the oracle's CPU rate (all host cores, and one core alone).
+Sub-record `epoch`: one encrypted SGD epoch of the paper-scale configuration (943 users x 1682
+items, 100,000 synthetic MovieLens-shaped ratings, k = 10, N = 2^15, 8 x 50-bit + 2 x 60-bit primes)
+per step, with its decrypted accuracy against FP64.
+
+Each part carries the per-kernel-class rooflines: NTT classes in butterflies/s and the key inner
+products in multiply-accumulates/s against integer ceilings from the integer-pipe rates measured in
+the same run, every class in algorithmic bytes/s against the measured HBM bandwidth. Multi-GPU runs
+are independent replicas (weak scaling). The CPU baseline is the oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                  [--workload paper|large|batched] [--served-rate R] [--served-sweep R1,R2,...]
+                  [--workload served|paper|large|batched] [--served-sweep R1,R2,...]
+                  [--served-requests R] [--no-epoch] [--no-cpu-baseline]
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -36,15 +45,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 METRIC = "encrypted MF ratings/sec, served vs one-by-one on 1 GB300; p50/p99 latency"
-# nominal integer-issue ceiling of the NTT butterfly, reported beside the measured one: 152 SMs x 4
-# schedulers x 32 lanes x 2.07 GHz issue slots at 20 32-bit instructions per lazy 64-bit Shoup
-# butterfly (product high half 5, two low halves 6, subtraction 2, range reduction 4, sum and
-# difference 3), assuming full issue
-ALU_PEAK_GBFLY = 152 * 128 * 2.07 / 20.0
 # DRAM bytes per limb row of a forward NTT pass at N = 2^15, from the ncu capture (dram__bytes_read
 # + write) of the fused ModUp passes of the current kernels (64 rotations at level 7, 2048 rows per
 # pass): (615 MB + 1020 MB) / 2 passes / 2048 rows
 NCU_FWD_DRAM_BYTES_PER_ROW = (615.0e6 + 1020.0e6) / 2 / 2048
+# the same for the served workload's forward passes at N = 2^16 (None until captured)
+NCU_SERVED_FWD_DRAM_BYTES_PER_ROW = None
 UNIT = "ratings/s"
 SEED = 20250903
 LR, LAM, K_RANK = 0.005, 0.02, 10
@@ -63,14 +69,18 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--served-requests", type=int, default=96)
-    ap.add_argument("--served-rate", type=float, default=100.0)
+    ap.add_argument("--served-requests", type=int, default=1000, help="requests per arrival rate")
+    ap.add_argument("--served-pool", type=int, default=256, help="distinct pre-encrypted requests")
     ap.add_argument("--served-slots", type=int, default=48)
-    ap.add_argument("--served-sweep", default="", help="comma-separated arrival rates (req/s) to sweep")
-    ap.add_argument("--workload", choices=["paper", "large", "batched"], default="paper",
-                    help="paper: the headline paper-scale epoch; large: the 6040 x 3706 workload at N=2^16; "
-                         "batched: independent instances one after another")
+    ap.add_argument("--served-sweep", default="", help="comma-separated arrival rates (req/s); default "
+                                                       "50,100,200,500,1000,2000 (the last one is the headline)")
+    ap.add_argument("--e2e-requests", type=int, default=300)
+    ap.add_argument("--epoch-steps", type=int, default=3, help="timed epochs of the epoch sub-record")
+    ap.add_argument("--no-epoch", action="store_true")
+    ap.add_argument("--workload", choices=["served", "paper", "large", "batched"], default="served",
+                    help="served: the served fold-in + predict workload (headline) with the paper-scale epoch "
+                         "as a sub-record; paper: the paper-scale epoch alone; large: the 6040 x 3706 workload "
+                         "at N=2^16; batched: independent instances")
     ap.add_argument("--instances", type=int, default=64, help="instances of the batched workload")
     return ap.parse_args()
 
@@ -398,100 +408,143 @@ def oracle_baseline():
 # ----------------------------------------------------------------------------- served workload
 
 SERVED = ("served fold-in + predict: resident encrypted item factors 3706 x k=16 (N=2^16, 13x50-bit + "
-          "3x60-bit primes); Poisson arrivals; per request one user's encrypted CSR row (nnz log-uniform "
-          "5..300, MovieLens rating law), 5 encrypted SGD fold-in steps (lr 0.005, lambda 0.02) then the "
-          "encrypted predicted-rating row over all items")
+          "3x60-bit primes, scale 2^50); Poisson arrivals at 50-2000 req/s; per request one user's encrypted "
+          "CSR row (nnz log-uniform 5..300, Zipf(1.0) items, MovieLens rating law), 5 encrypted SGD fold-in "
+          "steps (lr 0.005, lambda 0.02) then the encrypted predicted-rating row over all 3706 items; "
+          "memory-based admission into request slots")
+SERVED_M, SERVED_K, SERVED_STEPS, SERVED_LR, SERVED_LAM = 3706, 16, 5, 0.005, 0.02
+SERVED_RATES = (50.0, 100.0, 200.0, 500.0, 1000.0, 2000.0)
 
 
-def serve_loop(server, reqs, enc, take_buf):
-    """Wall-clock request loop: admit arrived requests FIFO while slots are free, tick, collect."""
+class ServedSetup:
+    """The served context (keys, resident item factors) and a pool of distinct client requests
+    encrypted once before any timing (client-side work): request i of a stream uses pool entry
+    i mod P, so a stream of any length keeps the same nnz mix without holding one ciphertext set
+    per request. The pool is also copied to page-locked host memory for the end-to-end runs."""
+
+    def __init__(self, args, dev):
+        import torch
+        from paper_2509_03024_gb300 import capi
+        from paper_2509_03024_gb300 import workloads as W
+        self.torch, self.capi = torch, capi
+        m, k = SERVED_M, SERVED_K
+        self.ctx = ctx = capi.Context.from_preset(W.PRESETS["served"], device=dev)
+        ctx.keygen(SEED, ctx.serve_rotation_steps(k))
+        self.tuning = autotune(ctx, args)
+        V = W.init_factors(m, k, SEED + 5)
+        plan = capi.MfPlan(ctx, 1, m, k, [0, 1], [0], [1.0])  # item packing of the resident factors
+        self.n_vb, self.B = plan.n_vb, plan.B
+        self.VD = ctx.empty_ct(self.n_vb)
+        plan.encrypt_factors(1, V, self.VD)
+        self.stream = torch.cuda.Stream(device=dev)
+        self.reqs = W.served_requests(args.served_pool, 100.0, m, k, SEED + 6)
+        self.pool = []
+        for i, r in enumerate(self.reqs):
+            UR, R = ctx.empty_ct(1), ctx.empty_ct(self.n_vb)
+            ctx.encrypt_request(m, k, r.u0, r.items, r.ratings, (1 << 44) + 64 * i, UR, R)
+            self.pool.append((UR, R))
+        torch.cuda.synchronize()
+        self.take_buf = ctx.empty_ct(self.n_vb)
+        self.host_pool = None
+        self.host_take = None
+
+    def host_buffers(self):
+        torch = self.torch
+        if self.host_pool is None:
+            self.host_pool = [(UR.cpu().pin_memory(), R.cpu().pin_memory()) for UR, R in self.pool]
+            self.host_take = torch.empty(self.take_buf.numel(), dtype=torch.int64).pin_memory()
+        return self.host_pool, self.host_take
+
+    def server(self, slots, budget=48 << 30):
+        return self.capi.Server(self.ctx, self.VD, SERVED_M, SERVED_K, SERVED_STEPS, SERVED_LR, SERVED_LAM,
+                                max_slots=slots, memory_budget_bytes=budget)
+
+
+def arrival_times(count, rate, seed):
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
+def serve_loop(st, server, arrivals, host=False):
+    """Wall-clock request loop: admit arrived requests FIFO while slots are free, tick (each tick only
+    enqueues its work), collect completed requests and download their predictions. Request i carries
+    pool entry i mod P. With host=True the request ciphertexts are uploaded from page-locked host
+    memory at admission and the predictions downloaded to host memory (end to end)."""
     import collections
+    torch = st.torch
+    pool, take = (st.host_buffers() if host else (st.pool, st.take_buf))
+    P = len(pool)
+    n = len(arrivals)
     queue = collections.deque()
-    arrivals = [r.arrival_s for r in reqs]
-    done_at = [None] * len(reqs)
-    nxt = 0
+    done_at = [None] * n
+    nxt, inflight, ticks, finished = 0, 0, 0, 0
+    nnz = 0
+    stream = st.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
-    inflight = 0
-    ticks = 0
-    while any(d is None for d in done_at):
+    e0.record(stream)
+    while finished < n:
         now = time.perf_counter() - t0
-        while nxt < len(reqs) and arrivals[nxt] <= now:
+        while nxt < n and arrivals[nxt] <= now:
             queue.append(nxt)
             nxt += 1
-        while queue and server.submit(queue[0], reqs[queue[0]].items, *enc[queue[0]]):
+        while queue:
+            i = queue[0]
+            UR, R = pool[i % P]
+            if not server.submit(i, st.reqs[i % P].items, UR, R, stream):
+                break
             queue.popleft()
             inflight += 1
         if inflight:
-            server.tick()
+            server.tick(stream)
             ticks += 1
-            now = time.perf_counter() - t0
             for rid in server.poll():
-                server.take(rid, take_buf)
-                done_at[rid] = now
+                server.take(rid, take, stream)
+                done_at[rid] = time.perf_counter() - t0
+                nnz += int(st.reqs[rid % P].items.size)
                 inflight -= 1
-        elif nxt < len(reqs):
+                finished += 1
+        elif nxt < n:
             time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
-    lat = np.array([d - a for d, a in zip(done_at, arrivals)]) * 1e3
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lat = (np.array(done_at) - arrivals) * 1e3
     span = max(done_at) - arrivals[0]
-    nnz = sum(int(r.items.size) for r in reqs)
-    return {"ratings_per_s": nnz / span, "requests_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "ticks": ticks,
-            "wall_s": span}
-
-
-def run_served(args, dev):
-    """Served fold-in + predict at --served-rate (and at every rate of --served-sweep): continuous
-    batching against the same server with one slot (one request at a time)."""
-    import torch
-    from paper_2509_03024_gb300 import capi
-    from paper_2509_03024_gb300 import workloads as W
-    m, k, steps, lr, lam = 3706, 16, 5, 0.005, 0.02
-    ctx = capi.Context.from_preset(W.PRESETS["served"], device=dev)
-    ctx.keygen(SEED, ctx.serve_rotation_steps(k))
-    V = W.init_factors(m, k, SEED + 5)
-    plan = capi.MfPlan(ctx, 1, m, k, [0, 1], [0], [1.0])  # item packing of the resident factors
-    n_vb = plan.n_vb
-    VD = ctx.empty_ct(n_vb)
-    plan.encrypt_factors(1, V, VD)
-    take_buf = ctx.empty_ct(n_vb)
-
-    def at_rate(rate):
-        reqs = W.served_requests(args.served_requests, rate, m, k, SEED + 6)
-        enc = []
-        for i, r in enumerate(reqs):  # client-side encryption, before the timed loop
-            UR, R = ctx.empty_ct(1), ctx.empty_ct(n_vb)
-            ctx.encrypt_request(m, k, r.u0, r.items, r.ratings, (1 << 44) + 64 * i, UR, R)
-            enc.append((UR, R))
-        server = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=args.served_slots,
-                             memory_budget_bytes=48 << 30)
-        batched = serve_loop(server, reqs, enc, take_buf)
-        batched["slots"] = server.n_slots
-        server.close()
-        single = capi.Server(ctx, VD, m, k, steps, lr, lam, max_slots=1)
-        one = serve_loop(single, reqs, enc, take_buf)
-        single.close()
-        return len(reqs), batched, one
-
-    n, batched, one = at_rate(args.served_rate)
-    from paper_2509_03024_gb300 import comm
-    B = plan.B
-    reqs = W.served_requests(args.served_requests, args.served_rate, m, k, SEED + 6)
-    per_req = [comm.served_request(ctx.n, ctx.top, n_vb, len(set((r.items // B).tolist())), steps) for r in reqs]
-    out_comm = {"mean_up_bytes": sum(x["up_bytes"] for x in per_req) / len(per_req),
-                "down_bytes": per_req[0]["down_bytes"], "down_level": per_req[0]["out_level"]}
-    out = {"workload": SERVED, "requests": n, "arrival_rate_req_s": args.served_rate, "communication": out_comm,
-           "value": batched["ratings_per_s"], "unit": UNIT, "p50_ms": batched["p50_ms"],
-           "p99_ms": batched["p99_ms"], "continuous_batching": batched, "one_by_one": one,
-           "speedup_vs_one_by_one": batched["ratings_per_s"] / one["ratings_per_s"]}
-    if args.served_sweep:
-        sweep = []
-        for rate in (float(x) for x in args.served_sweep.split(",")):
-            _, b, o = at_rate(rate)
-            sweep.append({"rate_req_s": rate,
-                          "batched": {k2: b[k2] for k2 in ("ratings_per_s", "p50_ms", "p99_ms")},
-                          "one_by_one": {k2: o[k2] for k2 in ("ratings_per_s", "p50_ms", "p99_ms")}})
-        out["sweep"] = sweep
+    out = {"requests": n, "ratings": nnz, "ratings_per_s": nnz / span, "requests_per_s": n / span,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_ms": float(lat.mean()), "ticks": ticks, "wall_s": span,
+           "device_span_ms": e0.elapsed_time(e1), "slots": server.n_slots}
     return out
+
+
+def run_served(args, st):
+    """Every arrival rate of the served workload: continuous batching against the same server with one
+    slot (one request at a time), args.served_requests requests each. Returns (sweep, headline)."""
+    rates = [float(x) for x in args.served_sweep.split(",")] if args.served_sweep else list(SERVED_RATES)
+    sweep = []
+    for r_i, rate in enumerate(rates):
+        arr = arrival_times(args.served_requests, rate, SEED + 100 + r_i)
+        sv = st.server(args.served_slots)
+        batched = serve_loop(st, sv, arr)
+        sv.close()
+        one_sv = st.server(1)
+        one = serve_loop(st, one_sv, arr)
+        one_sv.close()
+        sweep.append({"rate_req_s": rate, "continuous_batching": batched, "one_by_one": one,
+                      "speedup_vs_one_by_one": batched["ratings_per_s"] / one["ratings_per_s"]})
+    return sweep
+
+
+def served_profile(args, st, rate):
+    """One more batched run at `rate` with every launch timed by CUDA events (for the per-kernel
+    roofline; its own throughput is not reported): {class: (launches, device_ms, bytes)}."""
+    arr = arrival_times(min(args.served_requests, 200), rate, SEED + 99)
+    sv = st.server(args.served_slots)
+    st.ctx.profile_begin(time_kernels=True)
+    serve_loop(st, sv, arr)
+    stats = st.ctx.profile_end()
+    sv.close()
+    return stats
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -507,27 +560,142 @@ def job_throughput(elapsed_ms, ratings, steps, world, dist, device):
     return elapsed_ms, world * ratings * steps / (elapsed_ms / 1e3)
 
 
+def job_rate(ratings, seconds, dist, device):
+    """Whole-job served rate: ratings summed over ranks / the slowest rank's wall time."""
+    if dist is None:
+        return ratings / seconds
+    import torch
+    t = torch.tensor([float(ratings), float(seconds)], dtype=torch.float64, device=device)
+    r = t[:1].clone()
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    m = t[1:].clone()
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(r.item()) / float(m.item())
+
+
+def init_dist(world, dev):
+    import torch
+    if world <= 1:
+        return None
+    import torch.distributed as dist_mod
+    dist_mod.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    return dist_mod
+
+
 def run_gpu(args, rank, world, local_rank):
+    """The served workload (the headline), then the paper-scale training epoch as a sub-record."""
     import torch
     from paper_2509_03024_gb300 import build as B
     B.build()
-    from paper_2509_03024_gb300 import capi
-    from paper_2509_03024_gb300.workloads import PRESETS
-
     dev = local_rank
     torch.cuda.set_device(dev)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist_mod
-        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", dev))
-        dist = dist_mod
+    dist = init_dist(world, dev)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    preset, k_rank, lr, _ = workload_spec(args.workload)
-    train, test, U, V = workload(args.workload)
+    if args.workload != "served":
+        out = run_epoch(args, rank, world, dev, dist, barrier)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "paper":
+            out["cpu_baseline"] = cpu_baseline_epoch()
+        if dist is not None:
+            dist.destroy_process_group()
+        return out
+
+    st = ServedSetup(args, dev)
+    for w in range(args.warmup):          # untimed: short bursts through a fresh server
+        sv = st.server(args.served_slots)
+        serve_loop(st, sv, arrival_times(16, SERVED_RATES[-1], SEED + 50 + w))
+        sv.close()
+    torch.cuda.synchronize()
+    barrier()
+    clk, clk_path = start_clocks(dev)
+    sweep = run_served(args, st)
+    clocks = stop_clocks(clk, clk_path)
+    barrier()
+    head = sweep[-1]
+    hb = head["continuous_batching"]
+    value = job_rate(hb["ratings"], hb["wall_s"], dist, f"cuda:{dev}")
+    one_value = job_rate(head["one_by_one"]["ratings"], head["one_by_one"]["wall_s"], dist, f"cuda:{dev}")
+
+    # end to end: the same request stream with the ciphertexts uploaded from page-locked host memory at
+    # admission and the predictions downloaded to host memory, inside the timed loop
+    e2e = None
+    if args.e2e_requests > 0:
+        sv = st.server(args.served_slots)
+        r = serve_loop(st, sv, arrival_times(args.e2e_requests, head["rate_req_s"], SEED + 77), host=True)
+        sv.close()
+        ct_bytes = st.take_buf.numel() // st.n_vb * 8
+        pool_up = sum((UR.numel() + R.numel()) * 8 for UR, R in st.pool) / len(st.pool)
+        e2e = {"value": job_rate(r["ratings"], r["wall_s"], dist, f"cuda:{dev}"), "unit": UNIT,
+               "h2d_bytes_per_step": int(pool_up), "d2h_bytes_per_step": int(st.n_vb * ct_bytes * 2 // (st.ctx.top + 1)),
+               "step": "one request: its user and rating ciphertexts up, its prediction ciphertexts (limbs 0..1) down",
+               "requests": r["requests"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "rate_req_s": head["rate_req_s"]}
+
+    stats = served_profile(args, st, head["rate_req_s"])
+    ceil = int_ceilings(st.ctx)
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    roofline = roofline_of(stats, ceil, hbm_peak, peaks is not None, NCU_SERVED_FWD_DRAM_BYTES_PER_ROW, st.ctx.log_n)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": hb["wall_s"] * 1e3 / max(1, hb["ticks"]),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "p50_ms": hb["p50_ms"], "p99_ms": hb["p99_ms"],
+           "one_by_one": {"value": one_value, "unit": UNIT, "p50_ms": head["one_by_one"]["p50_ms"],
+                          "p99_ms": head["one_by_one"]["p99_ms"]},
+           "speedup_vs_one_by_one": value / one_value,
+           "config": {"workload": SERVED, "arrival_rate_req_s": head["rate_req_s"],
+                      "requests_per_rate": args.served_requests, "distinct_requests": len(st.pool),
+                      "slots": hb["slots"], "parallelism": "replicas",
+                      "step": "one server tick (every admitted request advances one fold-in step or its "
+                              "prediction); ms_per_step = wall time per tick of the headline run",
+                      "steps_warmup": "warm-up = that many untimed 16-request bursts; the timed region is "
+                                      "the request stream at every arrival rate",
+                      "l2": "inputs larger than L2 (resident item factors 4 x 13 MiB, every request 65 MiB of "
+                            "ciphertexts, evaluation keys 2.1 GB)",
+                      "tuning": st.tuning},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": int(sum(v[0] for v in stats.values())),
+           "gpu_launches_scope": "the profiled served run (" + str(min(args.served_requests, 200)) + " requests)",
+           "clocks": clocks,
+           "kernels": class_rooflines(stats, ceil, hbm_peak),
+           "int_pipe": ceil,
+           "served": {"sweep": [{"rate_req_s": x["rate_req_s"],
+                                 "continuous_batching": {k: x["continuous_batching"][k] for k in
+                                                         ("ratings_per_s", "requests_per_s", "p50_ms", "p99_ms",
+                                                          "mean_ms", "ticks", "wall_s", "device_span_ms",
+                                                          "slots", "requests")},
+                                 "one_by_one": {k: x["one_by_one"][k] for k in
+                                                ("ratings_per_s", "requests_per_s", "p50_ms", "p99_ms", "mean_ms",
+                                                 "ticks", "wall_s", "requests")},
+                                 "speedup_vs_one_by_one": x["speedup_vs_one_by_one"]} for x in sweep]}}
+    from paper_2509_03024_gb300 import comm
+    per_req = [comm.served_request(st.ctx.n, st.ctx.top, st.n_vb, len(set((r.items // st.B).tolist())),
+                                   SERVED_STEPS) for r in st.reqs]
+    out["served"]["communication"] = {"mean_up_bytes": sum(x["up_bytes"] for x in per_req) / len(per_req),
+                                      "down_bytes": per_req[0]["down_bytes"], "down_level": per_req[0]["out_level"]}
+    del st
+    if not args.no_epoch:
+        out["epoch"] = run_epoch(args, rank, world, dev, dist, barrier, sub=True)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = served_cpu_baseline(rounds=1)
+        except Exception as e:
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "kind": "oracle", "error": repr(e)}
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def run_epoch(args, rank, world, dev, dist, barrier, sub=False):
+    """The encrypted SGD epoch of the paper-scale (or large) workload: W warm-up epochs, K timed epochs
+    from the same top-level factors; decrypted accuracy against FP64; per-class rooflines."""
+    import torch
+    from paper_2509_03024_gb300 import capi
+    from paper_2509_03024_gb300.workloads import PRESETS
+    wl = "paper" if args.workload == "served" else args.workload
+    preset, k_rank, lr, desc = workload_spec(wl)
+    train, test, U, V = workload(wl)
     ctx = capi.Context.from_preset(PRESETS[preset], device=dev)
     ctx.keygen(SEED + rank, ctx.mf_rotation_steps(k_rank))
     tuning = autotune(ctx, args)
@@ -539,6 +707,7 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     ratings = train.nnz
     top = ctx.top
+    steps = args.epoch_steps if sub else args.steps
 
     def step():
         with torch.cuda.stream(stream):
@@ -551,18 +720,18 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    clk, clk_path = start_clocks(dev)
+    clk, clk_path = (None, None) if sub else start_clocks(dev)
     ctx.profile_begin(time_kernels=not args.no_kernel_timing)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
     stats = ctx.profile_end()
-    clocks = stop_clocks(clk, clk_path)
+    clocks = None if sub else stop_clocks(clk, clk_path)
     barrier()
-    elapsed_ms, value = job_throughput(ev0.elapsed_time(ev1), ratings, args.steps, world, dist, f"cuda:{dev}")
+    elapsed_ms, value = job_throughput(ev0.elapsed_time(ev1), ratings, steps, world, dist, f"cuda:{dev}")
 
     # decrypted accuracy of the last step against the FP64 epoch (sanity, not timed)
     from oracle import mf as omf
@@ -574,13 +743,36 @@ def run_gpu(args, rank, world, local_rank):
     trow, tcol, tval = test.triples()
     rmse_gap = abs(omf.rmse(Ud, Vd, trow, tcol, tval) - omf.rmse(U1, V1, trow, tcol, tval))
 
-    # end to end through the C ABI with host buffers: H2D of the encrypted factors, epoch, D2H
     e2e = None
     if args.e2e_steps > 0:
         e2e = run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world, dev, barrier, lr)
-    out = finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
-                 train, U, V, dist)
-    out["config"]["tuning"] = tuning
+    ceil = int_ceilings(ctx)
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic_row = NCU_FWD_DRAM_BYTES_PER_ROW if wl == "paper" else None
+    out = {"metric": METRIC if not sub else "encrypted MF training ratings/sec (one SGD epoch per step)",
+           "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": elapsed_ms / steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": desc, "ratings_per_step": ratings, "parallelism": "replicas",
+                      "l2": "inputs larger than L2 (the rating ciphertexts alone are %.1f GiB)" % (
+                          plan.info.n_bins * ctx.top * ctx.n * 8 / 2 ** 30),
+                      "rating_bins": int(plan.info.n_bins),
+                      "groups": int(plan.info.n_groups), "tree_nodes": int(plan.info.n_tree_nodes),
+                      "plan_device_gib": plan.info.device_bytes / 2 ** 30, "tuning": tuning},
+           "roofline": roofline_of(stats, ceil, hbm_peak, peaks is not None, traffic_row, ctx.log_n),
+           "e2e": e2e, "gpu_launches": int(sum(v[0] for v in stats.values())),
+           "accuracy": {"max_abs_vs_fp64": err, "rmse_gap_test": rmse_gap},
+           "kernels": class_rooflines(stats, ceil, hbm_peak)}
+    if clocks is not None:
+        out["clocks"] = clocks
+    from paper_2509_03024_gb300 import comm
+    out["communication"] = {
+        "training_10_epochs": comm.mf_training(ctx.n, ctx.top, ctx.alpha, len(ctx.mf_rotation_steps(k_rank)),
+                                               int(plan.info.n_bins), plan.n_ub, plan.n_vb, epochs=10),
+        "note": "bytes between the parties (key holder, data owners, recommender); the epochs themselves move "
+                "nothing off the GPU"}
+    del plan, ctx
     return out
 
 
@@ -626,31 +818,43 @@ def run_e2e(args, torch, dist, plan, U0, V0, UD, VD, stream, ratings, top, world
             "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d}
 
 
-def torch_device_of(ctx):
-    return ctx.device
-
-
 # the bound of each kernel class: the NTT passes (fused rescales and conversions included) and the
 # key inner products run on the integer pipes, the element-wise classes stream HBM
 CLASS_BOUND = {"ntt_forward": "alu", "ntt_inverse": "alu", "ks_inner": "alu", "tensor": "hbm",
                "elementwise": "hbm"}
 
+# Minimum 32-bit multiply instructions (each a 32 x 32 (+ 64) -> 64-bit mad.wide or a 32-bit mad.lo on
+# the integer multiply pipe) of one lazy Shoup butterfly on 64-bit residues: the high half of y ws (four
+# partial products), the low halves of y w and of qhat q (one wide and two low products each) = 10; and
+# of one 64 x 64 -> 128-bit multiply-accumulate: four partial products. Additions and carries run on the
+# ALU pipe alongside.
+BFLY_MIN_IMAD = 10
+MAC_MIN_IMAD = 4
 
-def butterflies_per_residue_pass(log_n: int) -> float:
-    """Butterflies per residue in one NTT pass: rings up to 2^13 run the log2(N) stages in one pass,
-    larger rings split them over two passes; a stage does N/2 butterflies."""
-    passes = 1 if log_n <= 13 else 2
-    return log_n / passes / 2.0
+
+def int_ceilings(ctx):
+    """Integer ceilings from the integer-pipe rates measured now on this GPU: butterflies/s = multiply
+    issue rate / BFLY_MIN_IMAD, multiply-accumulates/s = rate / MAC_MIN_IMAD (the slower of mad.wide and
+    mad.lo counts), with the register-only rate of this library's own butterfly code beside it."""
+    r = ctx.probe_int_pipe(500)
+    rate = min(r["imad_wide_gops"], r["imad_lo_gops"])
+    return {"butterfly_gbfly": rate / BFLY_MIN_IMAD, "mac_gmacs": rate / MAC_MIN_IMAD,
+            "probe_butterfly_gbfly": ctx.probe_butterfly_rate(2000), "rates_gops": r,
+            "source": "fhe_probe_int_pipe: mad.lo / mad.hi / mad.wide.u32 issue rates on register operands "
+                      "(152 SMs x 4 CTAs of 256 threads); ceilings = the mad rate / %d per butterfly and / %d "
+                      "per 64 x 64 -> 128-bit multiply-accumulate" % (BFLY_MIN_IMAD, MAC_MIN_IMAD)}
 
 
-def class_rooflines(stats, log_n: int, bfly_peak, hbm_peak: float):
-    """Per kernel class: launches, device time, algorithmic bytes, share of the device time and the
-    achieved fraction of the class's roofline: for NTT classes butterflies/s against the measured
-    butterfly rate (each pass reads and writes 16 bytes per residue), and for every class its
-    algorithmic bytes/s against the HBM peak. stats: {name: (launches, device_ms, bytes)}."""
+def class_rooflines(stats, ceil, hbm_peak: float):
+    """Per kernel class: launches, device time, algorithmic bytes, share of the device time, its
+    algorithmic bytes/s against the HBM peak, and for the integer classes the arithmetic rate against
+    the integer ceiling: butterflies/s (NTT classes) or multiply-accumulates/s (ks_inner).
+    stats: {name: (launches, device_ms, bytes, work)}."""
     total = sum(v[1] for v in stats.values()) or 1.0
     out = {}
-    for name, (launches, dev_ms, alg_bytes) in stats.items():
+    for name, v in stats.items():
+        launches, dev_ms, alg_bytes = v[0], v[1], v[2]
+        work = v[3] if len(v) > 3 else 0.0
         if not launches:
             continue
         rec = {"launches": launches, "device_ms": round(dev_ms, 3), "alg_gb": round(alg_bytes / 1e9, 3),
@@ -659,95 +863,242 @@ def class_rooflines(stats, log_n: int, bfly_peak, hbm_peak: float):
             secs = dev_ms / 1e3
             gbs = alg_bytes / secs / 1e9
             rec["hbm_view"] = {"achieved_gbs": gbs, "frac": gbs / hbm_peak}
-            if name.startswith("ntt") and bfly_peak:
-                gbfly = alg_bytes / 16.0 * butterflies_per_residue_pass(log_n) / secs / 1e9
-                rec["alu"] = {"achieved_gbfly": gbfly, "frac": gbfly / bfly_peak}
+            if ceil and work > 0 and name.startswith("ntt"):
+                g = work / secs / 1e9
+                rec["alu"] = {"achieved_gbfly": g, "frac": g / ceil["butterfly_gbfly"],
+                              "frac_of_probe": g / ceil["probe_butterfly_gbfly"]}
+            elif ceil and work > 0 and name == "ks_inner":
+                g = work / secs / 1e9
+                rec["alu"] = {"achieved_gmacs": g, "frac": g / ceil["mac_gmacs"]}
         out[name] = rec
     return out
 
 
-def finish(args, ctx, plan, stats, clocks, elapsed_ms, value, ratings, world, rank, e2e, err, rmse_gap,
-           train, U, V, dist):
-    # roofline of the dominant kernel class (longest summed device time)
-    peaks = measured_peaks()
-    dom = max(stats.items(), key=lambda kv: kv[1][1])
-    name, (launches, dev_ms, alg_bytes) = dom
+def roofline_of(stats, ceil, hbm_peak, measured, traffic_per_row, log_n):
+    """The bench line's roofline object for the dominant kernel class (longest summed device time)."""
+    name, v = max(stats.items(), key=lambda kv: kv[1][1])
+    launches, dev_ms, alg_bytes, work = v[0], v[1], v[2], (v[3] if len(v) > 3 else 0.0)
     avg_s = (dev_ms / launches) / 1e3
-    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     hbm_achieved = (alg_bytes / launches) / avg_s / 1e9
     hbm_view = {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if measured else "fallback 6.8 TB/s",
                 "alg_bytes_per_launch": alg_bytes / launches}
-    # the butterfly rate on register-resident values, measured now on this GPU: the NTT classes' peak
-    bfly_peak = (ctx.probe_butterfly_rate(2000)
-                 if any(k.startswith("ntt") and v[0] for k, v in stats.items()) else None)
-    if name.startswith("ntt"):
-        # one NTT pass sweeps every row once (16 bytes per residue)
-        log_n = ctx.log_n
-        bfly = (alg_bytes / launches) / 16.0 * butterflies_per_residue_pass(log_n)
-        achieved = bfly / avg_s / 1e9
-        rows_per_launch = (alg_bytes / launches) / (16.0 * 2 ** log_n)
-        traffic = (NCU_FWD_DRAM_BYTES_PER_ROW * rows_per_launch
-                   if name == "ntt_forward" and args.workload == "paper" else None)
-        peak = bfly_peak
-        roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Gbfly/s",
-                    "frac": achieved / peak, "traffic": traffic,
-                    "traffic_source": "ncu dram__bytes_read+write per row of the fused forward passes, scaled "
-                                      "by the rows of the average launch",
-                    "peak_source": ("measured by fhe_probe_butterfly_rate: the forward transform's lazy Shoup "
-                                    "butterflies on register-resident values (no shared-memory, twiddle or HBM "
-                                    "traffic), 152 SMs x 3 CTAs of 256 threads"),
-                    "nominal_peak": {"value": ALU_PEAK_GBFLY, "frac": achieved / ALU_PEAK_GBFLY,
-                                     "source": "152 SMs x 128 lanes x 2.07 GHz / 20 32-bit instructions per "
-                                               "butterfly at full issue (not reached: the probe issues 23.8 "
-                                               "instructions per butterfly at 53 % issue)"},
-                    "launches": launches, "avg_launch_us": avg_s * 1e6, "butterflies_per_launch": bfly,
-                    "hbm_view": hbm_view}
-    else:
-        roofline = {"bound": "hbm", "kernel": name, "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_source": hbm_view["peak_source"],
-                    "launches": launches, "avg_launch_us": avg_s * 1e6,
-                    "alg_bytes_per_launch": alg_bytes / launches}
-    roofline["share_of_timed_device_time"] = dev_ms / sum(v[1] for v in stats.values())
-    gpu_launches = sum(v[0] for v in stats.values())
+    rows_per_launch = (alg_bytes / launches) / (16.0 * 2 ** log_n)
+    base = {"kernel": name, "launches": launches, "avg_launch_us": avg_s * 1e6,
+            "share_of_timed_device_time": dev_ms / sum(x[1] for x in stats.values())}
+    if name.startswith("ntt") and work > 0:
+        achieved = (work / launches) / avg_s / 1e9
+        traffic = traffic_per_row * rows_per_launch if (traffic_per_row and name == "ntt_forward") else None
+        return {"bound": "alu", "achieved": achieved, "peak": ceil["butterfly_gbfly"], "unit": "Gbfly/s",
+                "frac": achieved / ceil["butterfly_gbfly"], "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read+write per limb row of this workload's forward passes, "
+                                  "scaled by the rows of the average launch" if traffic else None,
+                "peak_source": ceil["source"],
+                "probe_peak": {"value": ceil["probe_butterfly_gbfly"], "frac": achieved / ceil["probe_butterfly_gbfly"],
+                               "source": "fhe_probe_butterfly_rate: this library's lazy Shoup butterfly code on "
+                                         "register-resident values (no memory traffic)"},
+                "butterflies_per_launch": work / launches, "hbm_view": hbm_view, **base}
+    if name == "ks_inner" and work > 0:
+        achieved = (work / launches) / avg_s / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": ceil["mac_gmacs"], "unit": "GMAC/s",
+                "frac": achieved / ceil["mac_gmacs"], "traffic": None, "peak_source": ceil["source"],
+                "macs_per_launch": work / launches, "hbm_view": hbm_view, **base}
+    return {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_source": hbm_view["peak_source"],
+            "alg_bytes_per_launch": alg_bytes / launches, **base}
 
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-           "config": {"workload": workload_spec(args.workload)[3], "ratings_per_step": ratings, "parallelism": "replicas",
-                      "l2": "inputs larger than L2 (the rating ciphertexts alone are %.1f GiB)" % (
-                          plan.info.n_bins * ctx.top * ctx.n * 8 / 2 ** 30),
-                      "rating_bins": int(plan.info.n_bins),
-                      "groups": int(plan.info.n_groups), "tree_nodes": int(plan.info.n_tree_nodes),
-                      "plan_device_gib": plan.info.device_bytes / 2 ** 30},
-           "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
-           "accuracy": {"max_abs_vs_fp64": err, "rmse_gap_test": rmse_gap},
-           "kernels": class_rooflines(stats, ctx.log_n, bfly_peak, hbm_peak)}
-    from paper_2509_03024_gb300 import comm
-    out["communication"] = {
-        "training_10_epochs": comm.mf_training(ctx.n, ctx.top, ctx.alpha,
-                                               len(ctx.mf_rotation_steps(workload_spec(args.workload)[1])),
-                                               int(plan.info.n_bins), plan.n_ub, plan.n_vb, epochs=10),
-        "note": "bytes between the parties (key holder, data owners, recommender) for the paper-scale workload; "
-                "the epochs themselves move nothing off the GPU"}
-    if not args.no_served:
-        out["served"] = run_served(args, torch_device_of(ctx))
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "paper":
+
+def cpu_baseline_epoch():
+    """The epoch workload's oracle baseline: every available core, with one core alone beside it."""
+    try:
+        return oracle_baseline()
+    except Exception as e:   # the worker pool failed: the single-thread sample in this process
+        train, _, U, V = workload()
+        rps, secs, desc = oracle_sample(train, U, V)
+        return {"value": rps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                "measured_s": round(secs, 1), "all_cores_error": repr(e)}
+
+
+# ----------------------------------------------------------------------------- served CPU baseline
+
+# Operations of a served request, as the oracle runs them (oracle/serve.py), timed at the top level:
+#   ip     one item batch's inner products: mul_relin_rescale(UR, V_c) then the hoisted rotate-and-sum
+#   mask   E = R_c - S, MV = rescale(V_c (.) mask), E (x) MV
+#   relin  relin_rescale of the summed three-component tensor
+#   rot    one block-sum rotation and its addition
+#   reg    the regulariser: constant product, rescale, addition
+SERVED_OPS = ("ip", "mask", "relin", "rot", "reg")
+
+
+def _served_oracle_worker(index, cmd, res):
+    try:
+        from oracle import ckks, mf, serve
+        from paper_2509_03024_gb300 import workloads as W
+        he = ckks.Ckks(ckks.Params.from_preset(W.PRESETS["served"]))
+        k = SERVED_K
+        kp, w, B = serve.layout(k, he.prm.slots)
+        he.keygen(SEED, mf.rotsum_steps(kp) + [w, -kp])
+        top = he.prm.top
+        z = np.zeros(he.prm.slots)
+        z[: 4 * w] = 0.25                       # sparse slot vectors: fast to encode, full-size ciphertexts
+        UR = he.encrypt(z, top, 1)
+        Vc = he.encrypt(z, top, 2)
+        Rc = he.encrypt(z, top, 3)
+        mask = he.enc.encode(z)
+        t3 = he.tensor(UR, Vc)
+        res.put(("ready", index, None))
+
+        def timed(op):
+            t0 = time.perf_counter()
+            if op == "ip":
+                mf.block_sum(he, he.mul_relin_rescale(UR, Vc), kp)
+            elif op == "mask":
+                S = he.drop(Rc, top - 1)
+                E = he.sub(he.drop(Rc, top - 1), S)
+                MV = he.rescale(he.mul_plain(Vc, mask))
+                he.tensor(E, MV)
+            elif op == "relin":
+                he.relin_rescale(t3)
+            elif op == "rot":
+                G = he.drop(UR, top - 2)
+                he.add(G, he.rotate(G, w))
+            else:
+                base = he.rescale(serve.const_mul(he, UR, 0.99))
+                he.add(he.drop(base, top - 2), he.drop(UR, top - 2))
+            return time.perf_counter() - t0
+
+        while True:
+            c = cmd.get()
+            if c == "stop":
+                break
+            res.put(("time", index, {op: timed(op) for op in c}))
+    except Exception as e:
+        res.put(("error", index, repr(e)))
+
+
+class ServedOracleCores:
+    """Single-threaded oracle processes (spawned), one per core, each with its own served-ring context
+    and keys; a round times every served operation on every process at once."""
+
+    def __init__(self, n_workers, timeout_s=1800.0):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.n, self.timeout = n_workers, timeout_s
+        self.cmds = [ctx.Queue() for _ in range(n_workers)]
+        self.res = ctx.Queue()
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        os.environ.update({v: "1" for v in saved})
         try:
-            out["cpu_baseline"] = oracle_baseline()
-        except Exception as e:   # the worker pool failed: the single-thread sample in this process
-            rps, secs, desc = oracle_sample(train, U, V)
-            out["cpu_baseline"] = {"value": rps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                                   "measured_s": round(secs, 1), "all_cores_error": repr(e)}
-    if dist is not None:
-        dist.destroy_process_group()
-    return out
+            self.procs = [ctx.Process(target=_served_oracle_worker, args=(i, self.cmds[i], self.res), daemon=True)
+                          for i in range(n_workers)]
+            for p in self.procs:
+                p.start()
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+        self._collect(n_workers)
+
+    def _collect(self, count):
+        out = {}
+        while len(out) < count:
+            kind, i, v = self.res.get(timeout=self.timeout)
+            if kind == "error":
+                raise RuntimeError(f"oracle worker {i}: {v}")
+            out[i] = v
+        return out
+
+    def round(self):
+        """Every worker times every operation, all workers at once: {op: mean seconds}."""
+        for q in self.cmds:
+            q.put(SERVED_OPS)
+        times = self._collect(self.n)
+        return {op: statistics.mean(t[op] for t in times.values()) for op in SERVED_OPS}
+
+    def close(self):
+        for q in self.cmds:
+            q.put("stop")
+        for p in self.procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=10)
+
+
+def served_request_seconds(op_s, nnz_batches, top, n_vb, B, steps=SERVED_STEPS, alpha=3):
+    """Oracle seconds of one served request, from the top-level operation times: step s runs at level
+    l = top - 2 s (every rated batch: ip + mask; then relin at l - 1, log2(B) + 1 rotations at l - 2 and
+    the regulariser at l), the prediction runs ip on every batch at top - 2 steps; an operation at level
+    l is taken to cost its top-level time scaled by the extended limbs (l + 1 + alpha) / (top + 1 + alpha)."""
+    def at(op, lv):
+        return op_s[op] * (lv + 1 + alpha) / (top + 1 + alpha)
+    beta = int(math.log2(B))
+    total = 0.0
+    for s in range(steps):
+        lv = top - 2 * s
+        total += nnz_batches * (at("ip", lv) + at("mask", lv)) + at("relin", lv - 1)
+        total += (beta + 1) * at("rot", lv - 2) + at("reg", lv)
+    total += n_vb * at("ip", top - 2 * steps)
+    return total
+
+
+def served_cpu_rate(op_s, cores):
+    """Ratings/s of the served request mix on `cores` independent single-threaded oracle processes."""
+    from paper_2509_03024_gb300 import workloads as W
+    reqs = W.served_requests(256, 100.0, SERVED_M, SERVED_K, SEED + 6)
+    top, B = len(W.PRESETS["served"].data_bits) - 1, (1 << 15) // (2 * SERVED_K)
+    n_vb = -(-SERVED_M // B)
+    secs = sum(served_request_seconds(op_s, len(set((r.items // B).tolist())), top, n_vb, B) for r in reqs)
+    nnz = sum(int(r.items.size) for r in reqs)
+    return nnz / secs * cores, secs / len(reqs)
+
+
+def served_cpu_baseline(rounds=1, budget_s=None):
+    t0 = time.perf_counter()
+    pool = ServedOracleCores(oracle_workers(bytes_per_worker=2.5 * 2**30))
+    setup_s = time.perf_counter() - t0
+    vals = []
+    try:
+        while True:
+            op_s = pool.round()
+            rate, per_req = served_cpu_rate(op_s, pool.n)
+            vals.append((rate, per_req, op_s))
+            if len(vals) >= rounds or (budget_s is not None and time.perf_counter() - t0 > budget_s):
+                break
+    finally:
+        pool.close()
+    vals.sort(key=lambda v: v[0])
+    rate, per_req, op_s = vals[(len(vals) - 1) // 2]
+    desc = (f"{pool.n} single-threaded oracle processes at once on the served ring (N=2^16, 13+3 primes), each "
+            f"timing every operation of a served request at the top level ({', '.join(f'{k} {v:.2f} s' for k, v in op_s.items())}); "
+            f"per-request seconds extrapolated over the 5 fold-in steps and the prediction with the level's limb "
+            f"count (mean {per_req:.0f} s per request over 256 requests of the served mix); rate = ratings / "
+            f"request seconds x {pool.n} processes; extrapolated, {len(vals)} round(s)")
+    return {"value": rate, "unit": UNIT, "cores": pool.n, "kind": "oracle", "sample": desc,
+            "rounds": len(vals), "setup_s": round(setup_s, 1), "measured_s": round(time.perf_counter() - t0, 1)}
 
 
 def run_reference(args, rank, world):
-    """The oracle (CPU, as it stands) on the same workload and metric; rank 0 only."""
+    """The oracle (CPU, as it stands) on the served workload and metric; rank 0 only. The W warm-up
+    steps are not repeated on the CPU (nothing there warms up); timed rounds run until K are done or
+    about three minutes have passed, whichever comes first."""
     if rank != 0:
         return None
+    if args.workload != "served":
+        return run_reference_epoch(args)
+    cb = served_cpu_baseline(rounds=max(1, args.steps), budget_s=180.0)
+    return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world,
+            "steps": cb["rounds"], "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": SERVED, "arrival_rate_req_s": SERVED_RATES[-1]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_reference_epoch(args):
+    """The oracle (CPU, as it stands) on the epoch workload; extrapolated from sampled groups."""
     pool = OracleCores(oracle_workers())
     vals, per_step = [], []
     try:
@@ -764,8 +1115,8 @@ def run_reference(args, rank, world):
             f"(of {pool.info['groups']}) and one rotation; epoch extrapolated as (groups x {tg:.2f} s + "
             f"{3 * pool.info['nodes']} rotation-sized key switches x {tr:.2f} s) / {pool.n} = {est:.0f} s; "
             f"value = median over the timed steps")
-    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+    return {"impl": "reference", "metric": "encrypted MF training ratings/sec", "value": v, "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.n, "kind": "oracle", "sample": desc},

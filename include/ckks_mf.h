@@ -258,13 +258,17 @@ int fhe_set_variant(fhe_ctx* ctx, const char* family, const char* variant);
 int fhe_get_variant(const fhe_ctx* ctx, const char* family, const char** variant);
 
 /* Per kernel class: launches, summed device time (only when timing was
- * requested) and the algorithmic bytes those launches must move (inputs read
- * once plus outputs written once). `name` points to a static string. */
+ * requested), the algorithmic bytes those launches must move (inputs read
+ * once plus outputs written once) and their arithmetic work: butterflies for
+ * the NTT classes (a pass of S stages over R rows does R * S * N / 2), 64 x 64-bit
+ * multiply-accumulates for the key inner products, 0 otherwise. `name` points
+ * to a static string. */
 typedef struct {
     const char* name;
     int64_t launches;
     double device_ms;
     double bytes;
+    double work;
 } fhe_kernel_stat;
 
 /* Reset the counters. With time_kernels != 0 every launch is also bracketed
@@ -397,8 +401,11 @@ int fhe_predict(fhe_ctx* ctx, const fhe_mf_plan* plan, const uint64_t* U, const 
  * caller keeps the request queued and retries after a tick frees a slot.
  * Every tick advances every admitted request by one step in shared batched
  * launches (requests at different levels are grouped per level); a request
- * admitted between ticks joins at the next tick. Results do not depend on
- * which other requests share a tick. */
+ * admitted between ticks joins at the next tick. A tick only enqueues its work
+ * on the stream and returns: the host may admit requests and build the next
+ * tick while the GPU runs this one (the library keeps at most two calls'
+ * descriptor tables in flight). Results do not depend on which other requests
+ * share a tick. */
 typedef struct fhe_server fhe_server;
 
 /* Rotation steps a server for rank k needs. Same return convention as fhe_mf_rotation_steps. */
@@ -411,15 +418,19 @@ void fhe_serve_destroy(fhe_server* server);
 /* Slots the server actually allocated (after the memory cap) and slots now free. */
 int fhe_serve_slots(const fhe_server* server, int32_t* total, int32_t* free_slots);
 /* Admit a request if a slot is free. items: host int32 [nnz] distinct item
- * indices < m; UR: device ciphertext (u in every block), R: device, ceil(m/B)
- * ciphertexts (rating of item c*B+d on the first k slots of block d of R_c);
- * both at the top level; copied on `stream`. FHE_ERR_STATE if no slot is free. */
+ * indices < m; UR: one ciphertext (u in every block), R: ceil(m/B) ciphertexts
+ * (rating of item c*B+d on the first k slots of block d of R_c); both at the
+ * top level, in device memory or in host memory (page-locked host memory keeps
+ * the upload asynchronous); copied on `stream` before the call returns for
+ * pageable memory, else in stream order. FHE_ERR_STATE if no slot is free. */
 int fhe_serve_submit(fhe_server* server, int64_t request_id, const int32_t* items, int32_t nnz,
                      const uint64_t* UR, const uint64_t* R, void* stream);
-/* Advance every admitted request by one step; synchronises `stream` at the
- * end. Returns the number of requests still in flight (>= 0) or an error. */
+/* Advance every admitted request by one step: enqueue the step on `stream`
+ * without waiting for it. Returns the number of admitted requests whose last
+ * step has not been enqueued yet (>= 0) or an error. */
 int fhe_serve_tick(fhe_server* server, void* stream);
-/* Ids of requests completed since the last poll (up to cap; host). Returns the count. */
+/* Ids of requests whose whole computation has completed on the device since the
+ * last poll (up to cap; host; never blocks). Returns the count. */
 int fhe_serve_poll(fhe_server* server, int64_t* ids, int32_t cap);
 /* Client-side helper: pack and encrypt one request at the top level. u0: host
  * double [k]; items/ratings: host [nnz]. UR receives u0 in every block (nonce
@@ -427,8 +438,10 @@ int fhe_serve_poll(fhe_server* server, int64_t* ids, int32_t cap);
 int fhe_serve_encrypt_request(fhe_ctx* ctx, int32_t m, int32_t k, const double* u0, const int32_t* items,
                               const double* ratings, int32_t nnz, uint64_t nonce_base, uint64_t* UR,
                               uint64_t* R, void* stream);
-/* Copy a completed request's prediction (ceil(m/B) ciphertexts at *level) to
- * device `out` and free its slot. */
+/* Copy a completed request's prediction (ceil(m/B) ciphertexts at *level;
+ * limbs 0..*level of each component, the other limbs of `out` are left as they
+ * are) to `out` (device or host memory, capacity layout) and free its slot.
+ * Synchronises `stream`. */
 int fhe_serve_take(fhe_server* server, int64_t request_id, uint64_t* out, int32_t* level, void* stream);
 
 #ifdef __cplusplus

@@ -58,7 +58,7 @@ class CtxInfo(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("device_ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("work", ctypes.c_double)]
 
 
 class IntPipeRates(ctypes.Structure):
@@ -384,13 +384,14 @@ class Context:
         self._check(lib().fhe_profile_begin(self.h, 1 if time_kernels else 0))
 
     def profile_end(self):
-        """-> {class name: (launches, device_ms, algorithmic_bytes)}"""
+        """-> {class name: (launches, device_ms, algorithmic_bytes, work)}; work is butterflies for the NTT
+        classes and 64 x 64-bit multiply-accumulates for ks_inner."""
         arr = (KernelStat * 32)()
         rc = lib().fhe_profile_end(self.h, ctypes.cast(arr, ctypes.c_void_p), 32)
         if rc < 0:
             self._check(rc)
-        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].device_ms), float(arr[i].bytes))
-                for i in range(rc)}
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].device_ms), float(arr[i].bytes),
+                                       float(arr[i].work)) for i in range(rc)}
 
     # ---- matrix factorisation
     def mf_rotation_steps(self, k: int):

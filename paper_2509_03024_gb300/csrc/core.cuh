@@ -148,16 +148,26 @@ struct EvalKey {
 
 // Pinned host staging + device memory for per-launch descriptor tables
 // (pointer arrays). push() copies a table into pinned memory and enqueues its
-// upload on the stream; the returned device address is valid until reset().
-// reset() synchronises the stream first, so earlier uploads have completed.
+// upload on the stream; the returned device address stays valid for the work
+// enqueued before the next-but-one reset(). The arena has two halves that
+// alternate at every reset(): reset() marks the end of the current half's use
+// with an event on the stream, switches halves and waits (on the host) only
+// for the event that ended the other half's previous use. So a call can build
+// and upload its tables while the GPU still runs the previous call's kernels.
 struct Arena {
     struct Block {
         char* host = nullptr;
         char* dev = nullptr;
         size_t cap = 0, used = 0;
     };
-    std::vector<Block> blocks;
-    size_t cur = 0;
+    struct Half {
+        std::vector<Block> blocks;
+        size_t cur = 0;
+        cudaEvent_t done = nullptr;
+        bool pending = false;
+    };
+    Half halves[2];
+    int h = 0;
     void reset(cudaStream_t s);
     void* push(const void* data, size_t bytes, cudaStream_t s);
     template <typename T>
@@ -186,6 +196,7 @@ struct Profiler {
     bool timing = false;
     long long launches[K_COUNT] = {};
     double bytes[K_COUNT] = {};
+    double work[K_COUNT] = {};  // butterflies (NTT classes) or 64 x 64-bit multiply-accumulates (ks_inner)
     struct Rec {
         int cls;
         cudaEvent_t a, b;
@@ -207,14 +218,14 @@ struct NoLaunchEvents {
     ~NoLaunchEvents() { tl_no_launch_events = saved; }
 };
 
-// RAII scope around one kernel launch: counts it, adds its algorithmic bytes
+// RAII scope around one kernel launch: counts it, adds its algorithmic bytes and arithmetic work
 // and, when timing is on, brackets it with CUDA events on its stream.
 struct LaunchScope {
     Profiler& p;
     int cls;
     cudaStream_t s;
     cudaEvent_t b = nullptr;
-    LaunchScope(Profiler& prof, int k, double bytes, cudaStream_t st);
+    LaunchScope(Profiler& prof, int k, double bytes, cudaStream_t st, double work = 0.0);
     ~LaunchScope();
 };
 

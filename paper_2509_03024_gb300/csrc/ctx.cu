@@ -1410,6 +1410,7 @@ int fhe_profile_end(fhe_ctx* ctx, fhe_kernel_stat* out, int32_t cap) {
             out[k].launches = p.launches[k];
             out[k].device_ms = ms[k];
             out[k].bytes = p.bytes[k];
+            out[k].work = p.work[k];
         }
         p.timing = false;
         p.recs.clear();

@@ -265,7 +265,7 @@ void launch_pass(const Ctx& c, const KsRow* rows, int n_rows, int tiles, const C
     if (smem > 48 * 1024)
         CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE, RB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LaunchScope _ls(c.prof, cls, bytes, s);
+    LaunchScope _ls(c.prof, cls, bytes, s, (double)n_rows * ((size_t)1 << (c.log_n - 1)) * LOGM);
     ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE, RB><<<dim3(n_rows, tiles), T, smem, s>>>(rows, c.d_primes, tw, c.d_ninv,
                                                                                         ca, c.log_n);
     CK(cudaGetLastError());
@@ -439,7 +439,7 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
         if (!hk) {
             LaunchScope _ls(c.prof, K_KS_INNER,
                             8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next),
-                            s);
+                            s, 2.0 * items * next * n * dn);
             bool shared = !fan;
             for (int t = 1; t < items && shared; t++)
                 shared = it[t].key == it[0].key && it[t].galois == it[0].galois;
@@ -452,7 +452,7 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
             LaunchScope _ls(c.prof, K_KS_INNER,
                             8.0 * n * ((double)items * (dn * next + l1) + (double)hk->count * dn * 2 * next +
                                        (double)items * (2 * next + l1)),
-                            s);
+                            s, 2.0 * items * next * n * dn * hk->count);
             std::vector<HoistStep> hs;
             for (int r = 0; r < hk->count; r++) hs.push_back({hk->key[r], (long long)hk->galois[r]});
             ia.steps = c.arena.push_vec(hs, s);

@@ -170,7 +170,8 @@ void launch_tile(const Ctx& c, const PolyBatch& pb, int tiles, cudaStream_t s, d
     if (smem > 48 * 1024)
         CK(cudaFuncSetAttribute(ntt_tile_kernel<LOGM, R, INV, PASS, LAST, RB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LaunchScope _ls(c.prof, INV ? K_NTT_INV : K_NTT_FWD, bytes, s);
+    // this pass runs LOGM butterfly stages over every row: N/2 butterflies per stage
+    LaunchScope _ls(c.prof, INV ? K_NTT_INV : K_NTT_FWD, bytes, s, (double)pb.rows() * ((size_t)1 << (c.log_n - 1)) * LOGM);
     ntt_tile_kernel<LOGM, R, INV, PASS, LAST, RB><<<dim3(pb.rows(), tiles), T, smem, s>>>(pb, c.d_primes, tw,
                                                                                       c.d_ninv, c.log_n);
     CK(cudaGetLastError());

@@ -17,36 +17,50 @@ namespace fhe {
 // ============================================================================ arena
 
 void Arena::reset(cudaStream_t s) {
-    CK(cudaStreamSynchronize(s));
-    for (auto& b : blocks) b.used = 0;
-    cur = 0;
+    Half& used = halves[h];
+    if (!used.done) CK(cudaEventCreateWithFlags(&used.done, cudaEventDisableTiming));
+    CK(cudaEventRecord(used.done, s));
+    used.pending = true;
+    h ^= 1;
+    Half& next = halves[h];
+    if (next.pending) {
+        CK(cudaEventSynchronize(next.done));  // its tables and staging may be overwritten now
+        next.pending = false;
+    }
+    for (auto& b : next.blocks) b.used = 0;
+    next.cur = 0;
 }
 
 void* Arena::push(const void* data, size_t bytes, cudaStream_t s) {
+    Half& hf = halves[h];
     const size_t span = std::max<size_t>((bytes + 255) & ~(size_t)255, 256);
-    while (cur < blocks.size() && blocks[cur].used + span > blocks[cur].cap) cur++;
-    if (cur == blocks.size()) {
+    while (hf.cur < hf.blocks.size() && hf.blocks[hf.cur].used + span > hf.blocks[hf.cur].cap) hf.cur++;
+    if (hf.cur == hf.blocks.size()) {
         Block b;
         b.cap = std::max<size_t>(span, (size_t)4 << 20);
         CK(cudaMallocHost((void**)&b.host, b.cap));
         CK(cudaMalloc((void**)&b.dev, b.cap));
-        blocks.push_back(b);
+        hf.blocks.push_back(b);
     }
-    Block& b = blocks[cur];
-    char* h = b.host + b.used;
+    Block& b = hf.blocks[hf.cur];
+    char* hp = b.host + b.used;
     char* d = b.dev + b.used;
     b.used += span;
     if (bytes) {
-        std::memcpy(h, data, bytes);
-        CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
+        std::memcpy(hp, data, bytes);
+        CK(cudaMemcpyAsync(d, hp, bytes, cudaMemcpyHostToDevice, s));
     }
     return d;
 }
 
 Arena::~Arena() {
-    for (auto& b : blocks) {
-        if (b.host) cudaFreeHost(b.host);
-        if (b.dev) cudaFree(b.dev);
+    for (auto& hf : halves) {
+        if (hf.pending) cudaEventSynchronize(hf.done);
+        if (hf.done) cudaEventDestroy(hf.done);
+        for (auto& b : hf.blocks) {
+            if (b.host) cudaFreeHost(b.host);
+            if (b.dev) cudaFree(b.dev);
+        }
     }
 }
 
@@ -68,6 +82,7 @@ void Profiler::reset() {
     for (int k = 0; k < K_COUNT; k++) {
         launches[k] = 0;
         bytes[k] = 0;
+        work[k] = 0;
     }
     recs.clear();
     pool_used = 0;
@@ -79,9 +94,11 @@ Profiler::~Profiler() {
 
 thread_local bool tl_no_launch_events = false;
 
-LaunchScope::LaunchScope(Profiler& prof, int k, double nbytes, cudaStream_t st) : p(prof), cls(k), s(st) {
+LaunchScope::LaunchScope(Profiler& prof, int k, double nbytes, cudaStream_t st, double work)
+    : p(prof), cls(k), s(st) {
     p.launches[k]++;
     p.bytes[k] += nbytes;
+    p.work[k] += work;
     if (p.timing && !tl_no_launch_events) {
         b = p.get_event();
         CK(cudaEventRecord(b, s));

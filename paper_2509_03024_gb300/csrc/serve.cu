@@ -48,8 +48,18 @@ struct fhe_server {
     u64* V = nullptr;
     std::vector<Slot> slots;
     std::vector<void*> allocs;
-    std::vector<long long> completed;
+    // requests whose last step was enqueued by a tick, with the event recorded after that tick's work;
+    // poll() reports them once the event has completed
+    struct Done {
+        cudaEvent_t ev;
+        std::vector<long long> ids;
+    };
+    std::vector<long long> finishing;   // filled while a tick is being enqueued
+    std::vector<Done> done_q;
+    std::vector<cudaEvent_t> ev_pool;
     ~fhe_server() {
+        for (Done& d : done_q) ev_pool.push_back(d.ev);
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         for (void* p : allocs) cudaFree(p);
         if (V) cudaFree(V);
     }
@@ -205,7 +215,7 @@ void predict_pass(fhe_server& sv, const std::vector<Slot*>& group, int level, cu
     for (Slot* sl : group) {
         sl->level = level - 1;
         sl->done = true;
-        sv.completed.push_back(sl->id);
+        sv.finishing.push_back(sl->id);
     }
 }
 
@@ -344,8 +354,8 @@ int fhe_serve_submit(fhe_server* sv, int64_t id, const int32_t* items, int32_t n
         cudaStream_t s = (cudaStream_t)stream;
         Slot& sl = *free_slot;
         const size_t w = c.ct_words();
-        CK(cudaMemcpyAsync(sl.UR, UR, sizeof(u64) * w, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(sl.R, R, sizeof(u64) * w * sv->n_vb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(sl.UR, UR, sizeof(u64) * w, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(sl.R, R, sizeof(u64) * w * sv->n_vb, cudaMemcpyDefault, s));
         // learning-rate masks of the rated blocks, one encoding per item batch
         std::vector<int> idx, off{0};
         std::vector<double> val;
@@ -388,9 +398,22 @@ int fhe_serve_tick(fhe_server* sv, void* stream) {
             if (sl.step < sv->steps) fold[sl.level].push_back(&sl);
             else pred[sl.level].push_back(&sl);
         }
+        sv->finishing.clear();
         for (auto& kv : fold) fold_in_step(*sv, kv.second, kv.first, s);
         for (auto& kv : pred) predict_pass(*sv, kv.second, kv.first, s);
-        CK(cudaStreamSynchronize(s));
+        if (!sv->finishing.empty()) {
+            // no host wait: the tick's completions are reported by poll() once this event completes
+            cudaEvent_t ev;
+            if (sv->ev_pool.empty()) {
+                CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            } else {
+                ev = sv->ev_pool.back();
+                sv->ev_pool.pop_back();
+            }
+            CK(cudaEventRecord(ev, s));
+            sv->done_q.push_back({ev, sv->finishing});
+            sv->finishing.clear();
+        }
         for (Slot& sl : sv->slots) inflight += sl.used && !sl.done;
     });
     return rc ? rc : inflight;
@@ -398,10 +421,22 @@ int fhe_serve_tick(fhe_server* sv, void* stream) {
 
 int fhe_serve_poll(fhe_server* sv, int64_t* ids, int32_t cap) {
     if (!sv || (cap > 0 && !ids)) return FHE_ERR_INVALID_ARG;
-    int n = (int)std::min<size_t>(cap, sv->completed.size());
-    for (int i = 0; i < n; i++) ids[i] = sv->completed[i];
-    sv->completed.erase(sv->completed.begin(), sv->completed.begin() + n);
-    return n;
+    Ctx& c = *sv->c;
+    int n = 0;
+    int rc = guarded(&c, [&] {
+        // ticks complete in order: report the requests of every completed tick at the front
+        while (!sv->done_q.empty()) {
+            fhe_server::Done& d = sv->done_q.front();
+            if (n + (int)d.ids.size() > cap) break;
+            const cudaError_t q = cudaEventQuery(d.ev);
+            if (q == cudaErrorNotReady) break;
+            CK(q);
+            for (long long id : d.ids) ids[n++] = id;
+            sv->ev_pool.push_back(d.ev);
+            sv->done_q.erase(sv->done_q.begin());
+        }
+    });
+    return rc ? rc : n;
 }
 
 int fhe_serve_encrypt_request(fhe_ctx* ctx, int32_t m, int32_t k, const double* u0, const int32_t* items,
@@ -459,8 +494,10 @@ int fhe_serve_take(fhe_server* sv, int64_t id, uint64_t* out, int32_t* level, vo
         for (Slot& sl : sv->slots)
             if (sl.used && sl.id == id) {
                 if (!sl.done) fail(FHE_ERR_STATE, "request not complete");
-                CK(cudaMemcpyAsync(out, sl.out, sizeof(u64) * c.ct_words() * sv->n_vb, cudaMemcpyDeviceToDevice,
-                                   (cudaStream_t)stream));
+                // limbs 0..level of both components of every prediction ciphertext: one 2-D copy
+                const size_t pitch = sizeof(u64) * (size_t)(c.L + 1) * c.n;
+                CK(cudaMemcpy2DAsync(out, pitch, sl.out, pitch, sizeof(u64) * (size_t)(sl.level + 1) * c.n,
+                                     (size_t)2 * sv->n_vb, cudaMemcpyDefault, (cudaStream_t)stream));
                 CK(cudaStreamSynchronize((cudaStream_t)stream));
                 if (level) *level = sl.level;
                 sl.used = false;

@@ -103,6 +103,7 @@ def test_served_preset_request_bit_exact():
     assert server.submit(7, items, UR, R)
     for _ in range(steps + 1):
         server.tick()
+    torch.cuda.synchronize()              # ticks only enqueue; poll reports completed device work
     assert server.poll() == [7]
     buf = ctx.empty_ct(n_vb)
     lv = server.take(7, buf)

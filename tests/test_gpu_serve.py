@@ -113,6 +113,7 @@ def test_admission_is_bounded_by_slots():
         server.submit(0, reqs[0][0], *enc[0])               # duplicate id in flight
     for _ in range(STEPS + 1):
         server.tick()
+    torch.cuda.synchronize()               # ticks only enqueue; poll reports completed device work
     done = server.poll()
     assert sorted(done) == [0, 1]
     buf = ctx.empty_ct(n_vb)

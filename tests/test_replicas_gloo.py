@@ -39,3 +39,22 @@ def test_two_replicas_max_over_ranks():
 def test_single_rank_needs_no_collective():
     import bench
     assert bench.job_throughput(200.0, 1000, 5, 1, None, "cpu") == (200.0, 25000.0)
+
+
+def _rank_served(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ratings, secs = [(3000, 2.0), (5000, 4.0)][rank]
+    out[rank] = bench.job_rate(ratings, secs, dist, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_served_replicas_sum_ratings_over_slowest_rank():
+    """Served replicas: the job's rate is every rank's ratings over the slowest rank's wall time."""
+    world = 2
+    out = mp.Manager().dict()
+    mp.spawn(_rank_served, args=(world, _free_port(), out), nprocs=world, join=True)
+    assert out[0] == out[1] == pytest.approx((3000 + 5000) / 4.0)
