@@ -389,8 +389,12 @@ int fhe_predict(fhe_ctx* ctx, const fhe_mf_plan* plan, const uint64_t* U, const 
  * Step at level l (two levels): for each item batch c holding a rated item,
  * S_c = rotsum_kp(rescale(relin(UR (x) V_c))), E_c = R_c - S_c,
  * T += E_c (x) rescale(V_c (.) mask_c) (mask_c = lr on the first k slots of the
- * rated blocks); G = rescale(relin(T)); G += rot(G, 2^t w) for t < log2 B;
- * G += rot(G, -kp); UR <- drop(rescale(UR * round((1 - lr lambda nnz) Delta))) + G.
+ * rated blocks); G = rescale(relin(T)); G = sum_{a<B} rot(G, a w) (the block sum)
+ * then G += rot(G, -kp) (the half-fill), both as rounds of hoisted rotate-and-sums
+ * (G <- sum over the round's steps r of rot(G, r)): radix-4 rounds of steps
+ * 0, s, 2s, 3s with strides s = w, 4w, 16w, ..., a radix-2 round (0, s) when
+ * log2 B is odd, and the last round's steps r extended by r - kp;
+ * UR <- drop(rescale(UR * round((1 - lr lambda nnz) Delta))) + G.
  * The prediction pass computes S_c for every batch at the final level (one
  * level): slot d*w of output c is <u, v_(cB+d)>.
  *

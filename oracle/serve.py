@@ -14,9 +14,13 @@ user's ratings at once and the accumulated update of Alg. 2:
       E_c = R_c - S_c                                   e_j = r_j - <u, v_j>
       T  += E_c (x) rescale(V_c|l (.) mask_c)           mask_c = lr on the first k slots of rated blocks
   G = rescale(relin(T))                                 block d: lr e_j v_j
-  G = G + rot(G, 2^t w), t < log2 B                      every block: lr sum_j e_j v_j
+  G = sum_{a < B} rot(G, a w)                           every block: lr sum_j e_j v_j
   G = G + rot(G, -kp)                                   doubled block layout
   UR = drop(rescale(UR * round((1 - lr*lambda*nnz) * Delta))) + G
+
+The block sum and the half-fill run as hoisted rounds (``block_sum_rounds``):
+radix-4 rotate-and-sums with strides w, 4w, 16w, ..., the half-fill merged into
+the last round.
 
 two levels per step. The prediction pass computes S_c for every item batch
 (one level). ``fold_in_fp64`` is the same update in float64.
@@ -39,10 +43,37 @@ def layout(k: int, slots: int):
     return kp, w, slots // w
 
 
-def rotation_steps(k: int, slots: int) -> List[int]:
-    """Every left-rotation amount a request uses: the in-block sum, the block sum, the half-fill."""
+def block_sum_rounds(k: int, slots: int) -> List[List[int]]:
+    """The gradient's block sum over the B slot blocks followed by the half-fill, as rounds of
+    hoisted rotate-and-sums (each round: G <- sum over its steps r of rot(G, r), step 0 = G itself).
+
+    Mathematically the block sum is G <- sum_{a < B} rot(G, a w) and the half-fill G <- G + rot(G, -kp);
+    the rounds factor the block offsets a w as sums of one step per round: radix-4 rounds with strides
+    w, 4 w, 16 w, ... (steps 0, s, 2 s, 3 s), then a radix-2 round when log2 B is odd, and the last round
+    also carries the half-fill (its steps r and r - kp), since rot(sum_r rot(G', r), -kp) is
+    sum_r rot(G', r - kp). Every round is one hoisted key switch (one ModUp, one inner product per
+    non-zero step, one ModDown) instead of one full key switch per doubling."""
     kp, w, B = layout(k, slots)
-    return rotsum_steps(kp) + [(1 << t) * w for t in range(highest_bit(B))] + [-kp]
+    lb = highest_bit(B)
+    rounds, stride, t = [], w, 0
+    while t < lb:
+        r = 4 if lb - t >= 2 else 2
+        rounds.append([j * stride for j in range(r)])
+        stride *= r
+        t += 2 if r == 4 else 1
+    last = rounds.pop() if rounds else [0]
+    rounds.append(last + [x - kp for x in last])
+    return rounds
+
+
+def rotation_steps(k: int, slots: int) -> List[int]:
+    """Every left-rotation amount a request uses: the in-block sum, then the non-zero steps of the
+    block-sum rounds (block sum and half-fill) in round order."""
+    kp, _, _ = layout(k, slots)
+    steps = rotsum_steps(kp)
+    for rnd in block_sum_rounds(k, slots):
+        steps += [x for x in rnd if x != 0 and x not in steps]
+    return steps
 
 
 def replicate_user(u: np.ndarray, k: int, slots: int) -> np.ndarray:
@@ -121,9 +152,8 @@ def fold_in_step(he: Ckks, UR: Ciphertext, R: Sequence[Ciphertext], V: Sequence[
         T = t3 if T is None else he.add(T, t3)
     out_lv = UR.level - 2
     G = he.zero(out_lv) if T is None else he.relin_rescale(T)
-    for t in range(highest_bit(B)):
-        G = he.add(G, he.rotate(G, (1 << t) * w))
-    G = he.add(G, he.rotate(G, -kp))
+    for steps in block_sum_rounds(k, slots):     # block sum over the B blocks, then the half-fill
+        G = he.rotate_sum_hoisted(G, steps)
     base = he.drop(he.rescale(const_mul(he, UR, 1.0 - lr * lam * len(items))), out_lv)
     return he.add(base, G)
 

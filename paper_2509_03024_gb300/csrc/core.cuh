@@ -414,6 +414,10 @@ void rotsum_items(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& 
                   cudaStream_t s);
 // Left-rotation amounts of that rotate-and-sum.
 std::vector<int> rotsum_steps(int kp);
+// Hoisted rotate-and-sum over explicit steps (Halevi-Shoup): out_i = in_i + sum over the non-zero steps r
+// of rot(in_i, r), one ModUp, one inner product per step, one ModDown; in_i may equal out_i.
+void hoisted_sum_items(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& out,
+                       const std::vector<int>& steps, int level, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- ctx helpers (ctx.cu)
 

@@ -182,10 +182,11 @@ constexpr int ks_min_blocks(int rb, int threads) {
     return (rb == 3 ? 1024 : 768) / threads > 0 ? (rb == 3 ? 1024 : 768) / threads : 1;
 }
 
-template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB>
+template <int LOGN, int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB>
 __global__ void __launch_bounds__(R * (1 << LOGM) / (1 << RB), ks_min_blocks(RB, R * (1 << LOGM) / (1 << RB)))
 ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, const ulonglong2* __restrict__ tw,
-              const u64* __restrict__ ninv, CombineArgs ca, int log_n) {
+              const u64* __restrict__ ninv, CombineArgs ca) {
+    constexpr int log_n = LOGN;  // the ring size is a compile-time constant of each launch
     constexpr int M = 1 << LOGM;
     constexpr int P = R == 1 ? 1 : R + 1;
     constexpr int V = 1 << RB;
@@ -255,7 +256,7 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
 
 // The fused passes keep radix-8 register blocks: with 16 residues per thread their load and
 // store stages run out of registers (measured slower, unlike the plain transform).
-template <int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB = 3>
+template <int LOGN, int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB = 3>
 void launch_pass(const Ctx& c, const KsRow* rows, int n_rows, int tiles, const CombineArgs& ca, int cls, double bytes,
                  cudaStream_t s) {
     if (n_rows == 0) return;
@@ -263,11 +264,11 @@ void launch_pass(const Ctx& c, const KsRow* rows, int n_rows, int tiles, const C
     constexpr size_t smem = sizeof(u64) * (1 << LOGM) * (R == 1 ? 1 : R + 1);
     const ulonglong2* tw = PASS == 1 ? (INV ? c.d_itw2 : c.d_tw2) : (INV ? c.d_itw : c.d_tw);
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE, RB>,
+        CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGN, LOGM, R, INV, PASS, LOAD, STORE, RB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchScope _ls(c.prof, cls, bytes, s, (double)n_rows * ((size_t)1 << (c.log_n - 1)) * LOGM);
-    ks_ntt_kernel<LOGM, R, INV, PASS, LOAD, STORE, RB><<<dim3(n_rows, tiles), T, smem, s>>>(rows, c.d_primes, tw, c.d_ninv,
-                                                                                        ca, c.log_n);
+    ks_ntt_kernel<LOGN, LOGM, R, INV, PASS, LOAD, STORE, RB><<<dim3(n_rows, tiles), T, smem, s>>>(rows, c.d_primes, tw,
+                                                                                              c.d_ninv, ca);
     CK(cudaGetLastError());
 }
 
@@ -280,7 +281,7 @@ void ks_transform(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs
     switch (c.log_n) {
 #define SINGLE(LG)                                                                        \
     case LG:                                                                              \
-        launch_pass<LG, 1, INV, 0, LOAD, STORE, 3>(c, rows, n_rows, 1, ca, cls, bytes, s); \
+        launch_pass<LG, LG, 1, INV, 0, LOAD, STORE, 3>(c, rows, n_rows, 1, ca, cls, bytes, s); \
         return;
         SINGLE(9)
         SINGLE(10)
@@ -290,29 +291,29 @@ void ks_transform(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs
 #undef SINGLE
         case 14:
             if (!INV) {
-                launch_pass<7, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
-                launch_pass<7, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<14, 7, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<14, 7, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
             } else {
-                launch_pass<7, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
-                launch_pass<7, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<14, 7, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<14, 7, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
             }
             return;
         case 15:
             if (!INV) {
-                launch_pass<7, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
-                launch_pass<8, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<15, 7, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<15, 8, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 8, ca, cls, bytes, s);
             } else {
-                launch_pass<8, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
-                launch_pass<7, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<15, 8, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 8, ca, cls, bytes, s);
+                launch_pass<15, 7, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
             }
             return;
         case 16:
             if (!INV) {
-                launch_pass<8, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
-                launch_pass<8, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<16, 8, 16, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<16, 8, 16, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
             } else {
-                launch_pass<8, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
-                launch_pass<8, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<16, 8, 16, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 16, ca, cls, bytes, s);
+                launch_pass<16, 8, 16, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 16, ca, cls, bytes, s);
             }
             return;
         default: fail(FHE_ERR_INVALID_ARG, "unsupported ring degree");
@@ -682,6 +683,35 @@ std::vector<int> rotsum_steps(int kp) {
     else
         for (int t = 0; (1 << t) < kp; t++) st.push_back(1 << t);
     return st;
+}
+
+void hoisted_sum_items(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& out,
+                       const std::vector<int>& steps, int level, cudaStream_t s) {
+    if (in.size() != out.size()) fail(FHE_ERR_INVALID_ARG, "hoisted rotate-and-sum: input and output counts differ");
+    if (in.empty()) return;
+    const size_t lw = c.ct_words() / 2;
+    HoistKeys hk{};
+    for (int st : steps) {
+        if (c.galois(st) == 1) continue;  // the identity term is always included
+        if (hk.count == kMaxHoist) fail(FHE_ERR_INVALID_ARG, "hoisted rotate-and-sum: too many steps");
+        hk.key[hk.count] = rotation_key(c, st).d;
+        hk.galois[hk.count] = (int)c.galois(st);
+        hk.count++;
+    }
+    if (hk.count == 0) {
+        std::vector<UnItem> cp;
+        for (size_t i = 0; i < in.size(); i++)
+            if (in[i] != out[i]) cp.push_back({in[i], out[i]});
+        items_copy(c, cp, 2, level + 1, s);
+        return;
+    }
+    // the 128-bit sums hold count * dnum products below 2^(2 max_bits)
+    int terms = hk.count * c.dnum(level), lg = 0;
+    while ((1 << lg) < terms) lg++;
+    if (2 * c.max_prime_bits + lg > 128) fail(FHE_ERR_INVALID_ARG, "hoisted rotate-and-sum: primes too wide for 128-bit sums");
+    std::vector<KsItem> ks;
+    for (size_t i = 0; i < in.size(); i++) ks.push_back({in[i] + lw, nullptr, in[i], nullptr, nullptr, out[i], out[i] + lw, 1});
+    ks_run(c, ks, level, &hk, s);
 }
 
 void rotsum_items(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& out, int kp, int level,

@@ -57,10 +57,11 @@ constexpr int tile_min_blocks(int threads) {
     return (RB == 3 ? 1024 : 768) / threads > 0 ? (RB == 3 ? 1024 : 768) / threads : 1;
 }
 
-template <int LOGM, int R, bool INV, int PASS, bool LAST, int RB = 3>
+template <int LOGN, int LOGM, int R, bool INV, int PASS, bool LAST, int RB = 3>
 __global__ void __launch_bounds__(R * (1 << LOGM) / (1 << RB), tile_min_blocks<LOGM, RB>(R * (1 << LOGM) / (1 << RB)))
 ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2* __restrict__ tw,
-                const u64* __restrict__ ninv, int log_n) {
+                const u64* __restrict__ ninv) {
+    constexpr int log_n = LOGN;  // the ring size is a compile-time constant of each launch
     constexpr int M = 1 << LOGM;
     constexpr int P = R == 1 ? 1 : R + 1;
     constexpr int V = 1 << RB;
@@ -161,19 +162,19 @@ ntt_tile_kernel(PolyBatch pb, const Prime* __restrict__ primes, const ulonglong2
     }
 }
 
-template <int LOGM, int R, bool INV, int PASS, bool LAST, int RB = nttc::kTileRB>
+template <int LOGN, int LOGM, int R, bool INV, int PASS, bool LAST, int RB = nttc::kTileRB>
 void launch_tile(const Ctx& c, const PolyBatch& pb, int tiles, cudaStream_t s, double bytes) {
     constexpr int T = R * (1 << LOGM) / (1 << RB);
     constexpr size_t smem = sizeof(u64) * (1 << LOGM) * (R == 1 ? 1 : R + 1);
     // row passes read the transposed [stage][group][row] tables
     const ulonglong2* tw = PASS == 1 ? (INV ? c.d_itw2 : c.d_tw2) : (INV ? c.d_itw : c.d_tw);
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(ntt_tile_kernel<LOGM, R, INV, PASS, LAST, RB>,
+        CK(cudaFuncSetAttribute(ntt_tile_kernel<LOGN, LOGM, R, INV, PASS, LAST, RB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // this pass runs LOGM butterfly stages over every row: N/2 butterflies per stage
     LaunchScope _ls(c.prof, INV ? K_NTT_INV : K_NTT_FWD, bytes, s, (double)pb.rows() * ((size_t)1 << (c.log_n - 1)) * LOGM);
-    ntt_tile_kernel<LOGM, R, INV, PASS, LAST, RB><<<dim3(pb.rows(), tiles), T, smem, s>>>(pb, c.d_primes, tw,
-                                                                                      c.d_ninv, c.log_n);
+    ntt_tile_kernel<LOGN, LOGM, R, INV, PASS, LAST, RB><<<dim3(pb.rows(), tiles), T, smem, s>>>(pb, c.d_primes, tw,
+                                                                                            c.d_ninv);
     CK(cudaGetLastError());
 }
 
@@ -183,36 +184,36 @@ void run_ntt(const Ctx& c, const PolyBatch& pb, cudaStream_t s) {
     if (rows == 0) return;
     const double bytes = 16.0 * rows * ((size_t)1 << c.log_n);
     switch (c.log_n) {
-        case 9: launch_tile<9, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
-        case 10: launch_tile<10, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
-        case 11: launch_tile<11, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
-        case 12: launch_tile<12, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
-        case 13: launch_tile<13, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 9: launch_tile<9, 9, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 10: launch_tile<10, 10, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 11: launch_tile<11, 11, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 12: launch_tile<12, 12, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
+        case 13: launch_tile<13, 13, 1, INV, 0, true, 3>(c, pb, 1, s, bytes); return;
         case 14:  // 128 x 128
             if (!INV) {
-                launch_tile<7, 16, false, 0, false>(c, pb, 128 / 16, s, bytes);
-                launch_tile<7, 16, false, 1, true>(c, pb, 128 / 16, s, bytes);
+                launch_tile<14, 7, 16, false, 0, false>(c, pb, 128 / 16, s, bytes);
+                launch_tile<14, 7, 16, false, 1, true>(c, pb, 128 / 16, s, bytes);
             } else {
-                launch_tile<7, 16, true, 1, false>(c, pb, 128 / 16, s, bytes);
-                launch_tile<7, 16, true, 0, true>(c, pb, 128 / 16, s, bytes);
+                launch_tile<14, 7, 16, true, 1, false>(c, pb, 128 / 16, s, bytes);
+                launch_tile<14, 7, 16, true, 0, true>(c, pb, 128 / 16, s, bytes);
             }
             return;
         case 15:  // 256 column transforms of 2^7 points (N2 = 256), then 128 rows of 2^8
             if (!INV) {
-                launch_tile<7, 16, false, 0, false>(c, pb, 256 / 16, s, bytes);
-                launch_tile<8, 16, false, 1, true>(c, pb, 128 / 16, s, bytes);
+                launch_tile<15, 7, 16, false, 0, false>(c, pb, 256 / 16, s, bytes);
+                launch_tile<15, 8, 16, false, 1, true>(c, pb, 128 / 16, s, bytes);
             } else {
-                launch_tile<8, 16, true, 1, false>(c, pb, 128 / 16, s, bytes);
-                launch_tile<7, 16, true, 0, true>(c, pb, 256 / 16, s, bytes);
+                launch_tile<15, 8, 16, true, 1, false>(c, pb, 128 / 16, s, bytes);
+                launch_tile<15, 7, 16, true, 0, true>(c, pb, 256 / 16, s, bytes);
             }
             return;
         case 16:  // 256 x 256
             if (!INV) {
-                launch_tile<8, 16, false, 0, false>(c, pb, 256 / 16, s, bytes);
-                launch_tile<8, 16, false, 1, true>(c, pb, 256 / 16, s, bytes);
+                launch_tile<16, 8, 16, false, 0, false>(c, pb, 256 / 16, s, bytes);
+                launch_tile<16, 8, 16, false, 1, true>(c, pb, 256 / 16, s, bytes);
             } else {
-                launch_tile<8, 16, true, 1, false>(c, pb, 256 / 16, s, bytes);
-                launch_tile<8, 16, true, 0, true>(c, pb, 256 / 16, s, bytes);
+                launch_tile<16, 8, 16, true, 1, false>(c, pb, 256 / 16, s, bytes);
+                launch_tile<16, 8, 16, true, 0, true>(c, pb, 256 / 16, s, bytes);
             }
             return;
         default: fail(FHE_ERR_INVALID_ARG, "unsupported ring degree");

@@ -95,15 +95,28 @@ SlotWork work_of(const fhe_server& sv, const Slot& sl, int cb) {
     return wk;
 }
 
-void rot_add(Ctx& c, const std::vector<u64*>& in, const std::vector<u64*>& out, int step, int level, cudaStream_t s) {
-    if (in.empty()) return;
-    const size_t lw = c.ct_words() / 2;
-    const EvalKey& key = rotation_key(c, step);
-    const int g = c.galois(step);
-    std::vector<KsItem> ks;
-    for (size_t i = 0; i < in.size(); i++)
-        ks.push_back({in[i] + lw, key.d, in[i], in[i], in[i] + lw, out[i], out[i] + lw, g});
-    keyswitch_items(c, ks, level, s);
+// The gradient's block sum over the B slot blocks followed by the half-fill, as rounds of hoisted
+// rotate-and-sums: radix-4 rounds with strides w, 4w, 16w, ... (steps 0, s, 2s, 3s), a radix-2 round
+// when log2 B is odd, the half-fill rotation by -kp merged into the last round (its steps r and r - kp).
+// One step per round, summed, meets every block offset a w once, and every one again shifted by -kp.
+std::vector<std::vector<int>> block_sum_rounds(int kp, int w, int B) {
+    std::vector<std::vector<int>> rounds;
+    const int lb = hb(B);
+    int stride = w;
+    for (int t = 0; t < lb;) {
+        const int r = lb - t >= 2 ? 4 : 2;
+        std::vector<int> rnd;
+        for (int j = 0; j < r; j++) rnd.push_back(j * stride);
+        rounds.push_back(rnd);
+        stride *= r;
+        t += r == 4 ? 2 : 1;
+    }
+    std::vector<int> last = rounds.empty() ? std::vector<int>{0} : rounds.back();
+    if (!rounds.empty()) rounds.pop_back();
+    const size_t n = last.size();
+    for (size_t i = 0; i < n; i++) last.push_back(last[i] - kp);
+    rounds.push_back(last);
+    return rounds;
 }
 
 // Inner products of every (slot, batch) pair listed, at `level`: result in wk.S (level - 1).
@@ -165,21 +178,10 @@ void fold_in_step(fhe_server& sv, const std::vector<Slot*>& group, int level, cu
     }
     relin_rescale_items(c, t3, gs, level - 1, s);
     const int l2 = level - 2;
-    for (int t = 0; t <= sv.beta; t++) {
-        const int step = t < sv.beta ? (1 << t) * sv.w : -sv.kp;
-        std::vector<u64*> in, out;
-        for (Slot* sl : group) {
-            SlotWork wt = work_of(sv, *sl, 0);
-            in.push_back(wt.G);
-            out.push_back(wt.Gt);
-        }
-        rot_add(c, in, out, step, l2, s);
-        std::vector<UnItem> cp;
-        for (Slot* sl : group) {
-            SlotWork wt = work_of(sv, *sl, 0);
-            cp.push_back({wt.Gt, wt.G});
-        }
-        items_copy(c, cp, 2, l2 + 1, s);
+    for (const std::vector<int>& steps : block_sum_rounds(sv.kp, sv.w, sv.B)) {  // block sum, half-fill
+        std::vector<u64*> gv;
+        for (Slot* sl : group) gv.push_back(work_of(sv, *sl, 0).G);
+        hoisted_sum_items(c, gv, gv, steps, l2, s);
     }
     // UR <- drop(rescale(UR * round(reg Delta))) + G
     std::vector<ConstItem> cm;
@@ -251,8 +253,9 @@ int fhe_serve_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t
     if (w > c.slots) return FHE_ERR_INVALID_ARG;
     int B = c.slots / w;
     std::vector<int> st = rotsum_steps(kp);
-    for (int t = 0; (1 << t) < B; t++) st.push_back((1 << t) * w);
-    st.push_back(-kp);
+    for (const std::vector<int>& rnd : block_sum_rounds(kp, w, B))
+        for (int x : rnd)
+            if (x != 0 && std::find(st.begin(), st.end(), x) == st.end()) st.push_back(x);
     if (out) {
         if (cap < st.size()) return FHE_ERR_INVALID_ARG;
         std::copy(st.begin(), st.end(), out);
@@ -286,8 +289,9 @@ int fhe_serve_create(fhe_ctx* ctx, const uint64_t* V, int32_t m, int32_t k, int3
         sv->lr = lr;
         sv->lam = lam;
         for (int r : rotsum_steps(sv->kp)) rotation_key(c, r);
-        for (int t = 0; t < sv->beta; t++) rotation_key(c, (1 << t) * sv->w);
-        rotation_key(c, -sv->kp);
+        for (const std::vector<int>& rnd : block_sum_rounds(sv->kp, sv->w, sv->B))
+            for (int x : rnd)
+                if (x != 0) rotation_key(c, x);
         const size_t w = c.ct_words(), lw = w / 2;
         CK(cudaMalloc((void**)&sv->V, sizeof(u64) * w * sv->n_vb));
         CK(cudaMemcpy(sv->V, V, sizeof(u64) * w * sv->n_vb, cudaMemcpyDeviceToDevice));

@@ -32,7 +32,8 @@ def test_encrypted_request_matches_fp64():
     kp, w, B = serve.layout(k, prm.slots)
     n_vb = -(-m // B)
     steps = serve.rotation_steps(k, prm.slots)
-    assert sorted(steps) == sorted([1, 2, 3] + [(1 << t) * w for t in range(mf.highest_bit(B))] + [-kp])
+    rounds = serve.block_sum_rounds(k, prm.slots)
+    assert sorted(steps) == sorted({1, 2, 3} | {x for r in rounds for x in r if x != 0})
     he.keygen(3, steps)
     rng = np.random.default_rng(2)
     V = rng.normal(0, 0.3, (m, k))
@@ -74,5 +75,45 @@ def test_row_layout_hand_example():
     want = np.zeros(32)
     want[16:19] = want[24:27] = 0.5
     assert np.array_equal(m1, want)
-    # in-block sums by 1, 2, 3 (hoisted, kp = 4), block sums by 8 and 16, the half-fill by -4
-    assert serve.rotation_steps(3, 32) == [1, 2, 3, 8, 16, -4]
+    # in-block sums by 1, 2, 3 (hoisted, kp = 4); B = 4 blocks: one radix-4 round over the block
+    # offsets 0, 8, 16, 24 with the half-fill by -4 merged into it
+    assert serve.block_sum_rounds(3, 32) == [[0, 8, 16, 24, -4, 4, 12, 20]]
+    assert serve.rotation_steps(3, 32) == [1, 2, 3, 8, 16, 24, -4, 4, 12, 20]
+
+
+def test_block_sum_rounds_cover_every_block_once():
+    """One step per round, summed, hits every block offset a*w (a < B) exactly once, and every one of
+    them again shifted by the half-fill -kp: the rounds are the block sum followed by the half-fill."""
+    from collections import Counter
+    from itertools import product
+    for k, slots in ((3, 32), (3, 64), (16, 1 << 15), (1, 1 << 9), (10, 1 << 14), (8, 16)):
+        kp, w, B = serve.layout(k, slots)
+        rounds = serve.block_sum_rounds(k, slots)
+        sums = Counter(sum(c) % slots for c in product(*rounds))
+        want = Counter([(a * w) % slots for a in range(B)] + [(a * w - kp) % slots for a in range(B)])
+        assert sums == want, (k, slots)
+        assert all(len(r) in (2, 4) for r in rounds[:-1]) and len(rounds[-1]) in (2, 4, 8)
+        assert len(rounds) == max(1, (mf.highest_bit(B) + 1) // 2)
+
+
+def test_hoisted_block_sum_rounds_equal_the_doubling_sums():
+    """Decrypted, the hoisted rounds give the block sum and half-fill of the doubling definition
+    G + rot(G, 2^t w) (t < log2 B) followed by G + rot(G, -kp), within the key-switch noise."""
+    prm = ckks.Params(9, (50,) * 4, (60,), 40)
+    he = ckks.Ckks(prm)
+    k = 3
+    kp, w, B = serve.layout(k, prm.slots)
+    doubling = [(1 << t) * w for t in range(mf.highest_bit(B))] + [-kp]
+    he.keygen(5, sorted(set(serve.rotation_steps(k, prm.slots) + doubling)))
+    z = np.random.default_rng(4).normal(0, 1, prm.slots)
+    G = he.encrypt(z, prm.top, 9)
+    H = G
+    for steps in serve.block_sum_rounds(k, prm.slots):
+        H = he.rotate_sum_hoisted(H, steps)
+    D = G
+    for s in doubling:
+        D = he.add(D, he.rotate(D, s))
+    want = sum(np.roll(z, -a * w) for a in range(B))
+    want = want + np.roll(want, kp)
+    assert np.abs(he.decrypt(D) - want).max() < 1e-6
+    assert np.abs(he.decrypt(H) - want).max() < 1e-6
