@@ -298,6 +298,7 @@ struct Ctx {
     struct Tune {
         int inner = 0;  // plain / fan-out key inner product (InnerVariant of ks_inner.cuh)
         int hoist = 0;  // hoisted rotate-and-sum inner product
+        int ntt = 0;    // tile shape of the plain two-pass NTT (NttTile of ntt_tile.cuh)
     } tune;
     int max_prime_bits = 0;       // over every prime
     int max_data_prime_bits = 0;  // over the data primes q_0..q_L

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ks_inner.cuh"
+#include "ntt_tile.cuh"
 
 using namespace fhe;
 
@@ -27,6 +28,7 @@ struct Family {
 const Family kFamilies[] = {
     {"ks_hoist_inner", INNER_N_VARIANTS, kInnerVariantNames, &Ctx::Tune::hoist},
     {"ks_inner", INNER_N_VARIANTS, kInnerVariantNames, &Ctx::Tune::inner},
+    {"ntt", ntt_tile::NTT_N_TILES, ntt_tile::kNttTileNames, &Ctx::Tune::ntt},
 };
 constexpr int kNumFamilies = sizeof(kFamilies) / sizeof(kFamilies[0]);
 
@@ -121,7 +123,7 @@ void tune_inner(Ctx& c, int level, std::vector<fhe_tune_result>& out) {
     ia.n_ext = c.n_ext;
     ia.log_n = c.log_n;
     ia.pr = c.d_primes;
-    for (int f = 0; f < kNumFamilies; f++) {
+    for (int f = 0; f < 2; f++) {
         const Family& fam = kFamilies[f];
         const bool hoist = f == 0;
         InnerArgs a = ia;
@@ -152,6 +154,39 @@ void tune_inner(Ctx& c, int level, std::vector<fhe_tune_result>& out) {
     CK(cudaDeviceSynchronize());
 }
 
+// Time every tile shape of the plain two-pass NTT (forward then inverse of the same rows; rings of
+// 2^14 and more only) on 32 limb rows per limb of the context (at least 256 rows).
+void tune_ntt(Ctx& c, std::vector<fhe_tune_result>& out) {
+    const Family& fam = kFamilies[2];
+    if (c.log_n < 14) return;
+    const int L1 = c.L + 1, polys = std::max(1, 256 / L1 + (256 % L1 ? 1 : 0));
+    DevTmp tmp;
+    u64* buf = tmp.get((size_t)polys * L1 * c.n);
+    fill_residues<<<1024, 256>>>(buf, (size_t)polys * L1 * c.n, c.log_n, 1, c.d_primes, 5);
+    CK(cudaGetLastError());
+    const PolyBatch pb = poly_batch(buf, (size_t)L1 * c.n, 0, polys, 1, 0, L1);
+    const int saved = c.tune.ntt;
+    double best = 1e30;
+    int best_v = 0;
+    const size_t first = out.size();
+    for (int v = 0; v < fam.n_variants; v++) {
+        c.tune.ntt = v;
+        const double ms = time_ms([&] {
+            ntt_forward(c, pb, (cudaStream_t)0);
+            ntt_inverse(c, pb, (cudaStream_t)0);
+        }, 3);
+        out.push_back(fhe_tune_result{fam.name, fam.variant_names[v], 0, ms});
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    (void)saved;
+    out[first + best_v].chosen = 1;
+    c.tune.ntt = best_v;
+    CK(cudaDeviceSynchronize());
+}
+
 template <typename F>
 int guarded(Ctx& c, F&& f) {
     try {
@@ -179,6 +214,7 @@ extern "C" int fhe_autotune(fhe_ctx* ctx, int32_t level, fhe_tune_result* out, i
         if (cap < 0 || (cap > 0 && !out)) fail(FHE_ERR_INVALID_ARG, "bad output array");
         CK(cudaDeviceSynchronize());
         tune_inner(c, level, res);
+        tune_ntt(c, res);
     });
     if (rc) return rc;
     const int n = (int)std::min<size_t>(res.size(), (size_t)cap);

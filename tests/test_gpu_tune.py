@@ -66,7 +66,7 @@ def test_autotune_keeps_one_variant_per_family():
     ctx = gpu_ctx("t11a2", 24)
     res = ctx.autotune()
     fams = {r["family"] for r in res}
-    assert fams == {"ks_hoist_inner", "ks_inner"}
+    assert fams == {"ks_hoist_inner", "ks_inner"}             # N = 2^11: one-pass NTT, no tile shapes
     for f in fams:
         rows = [r for r in res if r["family"] == f]
         assert sorted(r["variant"] for r in rows) == sorted(VARIANTS)
@@ -76,3 +76,29 @@ def test_autotune_keeps_one_variant_per_family():
         assert ctx.get_variant(f) == chosen[0]["variant"]
     with pytest.raises(capi.FheError, match="INVALID_ARG"):
         ctx.set_variant("ks_inner", "nope")
+
+
+@pytest.mark.parametrize("preset", ["paper", "t16a3"])
+def test_ntt_tile_shapes_bit_identical(preset):
+    """Every tile shape of the two-pass NTT gives the same transform (N = 2^15 and 2^16)."""
+    ctx = gpu_ctx(preset, 25)
+    L1 = ctx.top + 1
+    rng = np.random.default_rng(6)
+    a = np.stack([rng.integers(0, q, (3, ctx.n), dtype=np.uint64) for q in ctx.primes[:L1]], axis=1)
+    base = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    ref = None
+    for v in ("r16b4", "r8b4", "r32b4", "r16b3"):
+        ctx.set_variant("ntt", v)
+        t = base.clone()
+        ctx.ntt_forward(t, 3, L1)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = t.clone()
+        assert torch.equal(t, ref), f"tile shape {v} changes the forward transform"
+        ctx.ntt_inverse(t, 3, L1)
+        torch.cuda.synchronize()
+        assert torch.equal(t, base), f"tile shape {v}: inverse does not undo the forward transform"
+    res = ctx.autotune()
+    rows = [r for r in res if r["family"] == "ntt"]
+    assert sorted(r["variant"] for r in rows) == ["r16b3", "r16b4", "r32b4", "r8b4"]
+    assert sum(r["chosen"] for r in rows) == 1
