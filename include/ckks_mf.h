@@ -294,8 +294,10 @@ typedef struct {
 } fhe_mf_plan_info;
 
 /* The rotation amounts an MF epoch with rank k needs (keys must exist for all
- * of them). Writes up to cap entries to host `out`; returns the count (>= 0)
- * or an error code. */
+ * of them): the in-block sum's, the delta tree's baby steps r*w (0 < r < beta)
+ * and giant steps 2^t*beta*w (< B*w) in both directions, and the half-fill -kp.
+ * Writes up to cap entries to host `out`; returns the count (>= 0) or an error
+ * code. */
 int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t cap);
 
 /* EncryptCsrMatrix + batch-pair grouping (Alg. 1, Alg. 2, Fig. 5).
@@ -359,8 +361,13 @@ int fhe_mf_decrypt_factors(fhe_ctx* ctx, const fhe_mf_plan* plan, int32_t which,
                            void* stream);
 
 /* One encrypted SGD epoch (Alg. 1 error and gradient, Alg. 2 accumulators,
- * applied once per epoch): for every rating e_ij = r_ij - <u_i, v_j> with the
- * epoch-start factors, then
+ * applied once per epoch). Item batch c rotated by delta*w (delta < B) lines up
+ * the pairs of group (b, c, delta); the rotated copies come from a baby-step
+ * giant-step delta tree: with beta = 2^floor(log2(B)/2) and delta = g*beta + r,
+ * a baby (r > 0) is its giant g*beta rotated by r*w, a giant (g > 0) is giant
+ * (g - 2^hb(g))*beta rotated by 2^hb(g)*beta*w, and the rotations out of one
+ * node share its ModUp; the item gradients return along the same tree. For every
+ * rating e_ij = r_ij - <u_i, v_j> with the epoch-start factors, then
  *   u_i <- u_i (1 - lr*lambda*nnz_i) + lr * sum_j e_ij v_j,
  *   v_j <- v_j (1 - lr*lambda*nnz_j) + lr * sum_i e_ij u_i.
  * U: device, n_user_batches ciphertexts; V: device, n_item_batches; both at

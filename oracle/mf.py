@@ -99,11 +99,18 @@ class Plan:
     bin_of: List[int]          # rating bin of each group
     bin_batch: List[int]       # user batch of each bin
 
+    @property
+    def baby(self) -> int:
+        return baby_range(self.B)
+
     def rotation_steps(self) -> List[int]:
-        """Every left-rotation amount an epoch uses (negative = right)."""
+        """Every left-rotation amount an epoch uses (negative = right): the in-block sum, the
+        delta tree's baby steps r w (r < beta) and giant steps 2^t beta w in both directions, the
+        half-fill."""
+        tree = tree_steps(self.B)
         steps = rotsum_steps(self.kp)
-        steps += [(1 << t) * self.w for t in range(highest_bit(self.B))]
-        steps += [-(1 << t) * self.w for t in range(highest_bit(self.B))]
+        steps += [x * self.w for x in tree]
+        steps += [-x * self.w for x in tree]
         steps += [-self.kp]
         return steps
 
@@ -130,14 +137,52 @@ def block_sum(he: Ckks, P: Ciphertext, kp: int) -> Ciphertext:
     return S
 
 
-def delta_closure(deltas) -> List[int]:
-    """The deltas plus all their ancestors under parent(d) = d - 2^hb(d), plus 0."""
+# The delta tree (the Vr chain of Alg. 2's rotated item batches): every needed delta d is reached
+# from 0 by rotations of the item batch by multiples of w. Baby-step giant-step form with beta =
+# baby_range(B): write d = g beta + r (r < beta). A baby (r > 0) hangs off its giant g beta and is
+# one rotation by r w away; a giant g beta (g > 0) hangs off (g - 2^hb(g)) beta, one rotation by
+# 2^hb(g) beta w away. Rotations of one parent share its ModUp (hoisted fan-out), so the ModUps
+# per item batch fall from about B/2 (a binary tree over d) to about 3 B / (2 beta).
+
+def baby_range(B: int) -> int:
+    """beta = 2^floor(log2(B) / 2): the baby steps of the delta tree."""
+    return 1 << (highest_bit(B) // 2)
+
+
+def tree_parent(d: int, beta: int) -> Tuple[int, int]:
+    """(parent, rotation in blocks) of delta d > 0 in the baby-step giant-step delta tree."""
+    g, r = divmod(int(d), beta)
+    if r:
+        return g * beta, r
+    step = 1 << highest_bit(g)
+    return (g - step) * beta, step * beta
+
+
+def tree_depth(d: int, beta: int) -> int:
+    """Rotations from 0 to d: popcount of the giant index, plus one for a baby."""
+    g, r = divmod(int(d), beta)
+    return bin(g).count("1") + (1 if r else 0)
+
+
+def tree_steps(B: int) -> List[int]:
+    """Rotation amounts (in blocks) of the delta tree: baby steps 1..beta-1, giant steps 2^t beta < B."""
+    beta = baby_range(B)
+    steps = list(range(1, min(beta, B)))
+    t = beta
+    while t < B:
+        steps.append(t)
+        t <<= 1
+    return steps
+
+
+def delta_closure(deltas, beta: int) -> List[int]:
+    """The deltas plus all their ancestors in the delta tree, plus 0."""
     nodes = {0}
     for d in deltas:
         d = int(d)
         while d and d not in nodes:
             nodes.add(d)
-            d -= 1 << highest_bit(d)
+            d = tree_parent(d, beta)[0]
     return sorted(nodes)
 
 
@@ -200,7 +245,7 @@ def build_plan(n: int, m: int, k: int, rows, cols, vals, slots: int) -> Plan:
                            np.array([x[1] for x in items], dtype=np.float64)))
     closure = []
     for c in range(n_vb):
-        closure.append(delta_closure([g.delta for g in glist if g.c == c]))
+        closure.append(delta_closure([g.delta for g in glist if g.c == c], baby_range(B)))
     nnz_u = np.bincount(rows, minlength=n).astype(np.int64)
     nnz_v = np.bincount(cols, minlength=m).astype(np.int64)
     bin_of, bin_batch = assign_bins(glist, n_ub)
@@ -276,12 +321,13 @@ def simulate_epoch_slots(U: np.ndarray, V: np.ndarray, plan: Plan, lr: float, la
     UD = [pack_factors(U, plan, b) for b in range(plan.n_ub)]
     VD = [pack_factors(V, plan, c) for c in range(plan.n_vb)]
     Vr = []
+    beta = plan.baby
     for c in range(plan.n_vb):
         t = {0: VD[c]}
-        for d in sorted(plan.closure[c], key=lambda x: (bin(x).count("1"), x)):
+        for d in sorted(plan.closure[c], key=lambda x: (tree_depth(x, beta), x)):
             if d:
-                hb = 1 << highest_bit(d)
-                t[d] = _rot(t[d - hb], hb * plan.w)
+                par, step = tree_parent(d, beta)
+                t[d] = _rot(t[par], step * plan.w)
         Vr.append(t)
     TU = [np.zeros_like(UD[0]) for _ in range(plan.n_ub)]
     TV: Dict[Tuple[int, int], np.ndarray] = {}
@@ -302,10 +348,10 @@ def simulate_epoch_slots(U: np.ndarray, V: np.ndarray, plan: Plan, lr: float, la
         newU.append(unpack_factors(z, plan, b, plan.n))
     for c in range(plan.n_vb):
         H = {d: TV.get((c, d), np.zeros_like(VD[0])) for d in plan.closure[c]}
-        for d in sorted(plan.closure[c], key=lambda x: (bin(x).count("1"), x), reverse=True):
+        for d in sorted(plan.closure[c], key=lambda x: (tree_depth(x, beta), x), reverse=True):
             if d:
-                hb = 1 << highest_bit(d)
-                H[d - hb] = H[d - hb] + _rot(H[d], -hb * plan.w)
+                par, step = tree_parent(d, beta)
+                H[par] = H[par] + _rot(H[d], -step * plan.w)
         acc = H[0] + _rot(H[0], -plan.kp)
         z = VD[c] * reg_slots(plan.nnz_v, plan, c, lr, lam) + acc
         newV.append(unpack_factors(z, plan, c, plan.m))
@@ -371,13 +417,14 @@ class EncryptedMF:
             raise ValueError("level exhausted")
         # Vr chain: rotations of each item batch by delta*w along the delta tree
         Vr: List[Dict[int, Ciphertext]] = []
+        beta = p.baby
         for c in range(p.n_vb):
             t = {0: VD[c]}
-            for d in sorted(p.closure[c], key=lambda x: (bin(x).count("1"), x)):
+            for d in sorted(p.closure[c], key=lambda x: (tree_depth(x, beta), x)):
                 if d:
-                    hb = 1 << highest_bit(d)
+                    par, step = tree_parent(d, beta)
                     # hoisted: the children of a node share the ModUp of its c1
-                    t[d] = he.rotate_sum_hoisted(t[d - hb], [hb * p.w])
+                    t[d] = he.rotate_sum_hoisted(t[par], [step * p.w])
             Vr.append(t)
         TU: List[Optional[Ciphertext]] = [None] * p.n_ub
         TV: Dict[Tuple[int, int], Ciphertext] = {}
@@ -403,10 +450,10 @@ class EncryptedMF:
             H: Dict[int, Ciphertext] = {}
             for d in p.closure[c]:
                 H[d] = he.relin_rescale(TV[(c, d)]) if (c, d) in TV else he.zero(out_lv)
-            for d in sorted(p.closure[c], key=lambda x: (bin(x).count("1"), x), reverse=True):
+            for d in sorted(p.closure[c], key=lambda x: (tree_depth(x, p.baby), x), reverse=True):
                 if d:
-                    hb = 1 << highest_bit(d)
-                    H[d - hb] = he.add(H[d - hb], he.rotate(H[d], -hb * p.w))
+                    par, step = tree_parent(d, p.baby)
+                    H[par] = he.add(H[par], he.rotate(H[d], -step * p.w))
             acc = H[0]
             acc = he.add(acc, he.rotate(acc, -p.kp))
             reg = he.enc.encode(reg_slots(p.nnz_v, p, c, lr, lam))

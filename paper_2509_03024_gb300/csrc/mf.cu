@@ -13,7 +13,7 @@
 //
 // Epoch at level l (two levels per epoch, the accumulators of Alg. 2 applied
 // once per epoch):
-//   Vr[c][delta] = rot(Vr[c][parent], 2^hb(delta) w)  (delta tree, parent = delta - 2^hb)
+//   Vr[c][delta] = rot(Vr[c][parent], step w)  (baby-step giant-step delta tree, tree_parent below)
 //   per group: P = rescale(relin(UD_b (x) Vr)); S = rotsum_kp(P); E = R_g - S;
 //              M = rescale(Vr (.) mask_g); MU = rescale(UD_b (.) mask_g);
 //              TU_b += E (x) M;  TV[c][delta] += E (x) MU
@@ -45,6 +45,33 @@ int next_pow2(int x) {
 }
 int hbit(int x) { return 31 - __builtin_clz((unsigned)x); }
 int popc(int x) { return __builtin_popcount((unsigned)x); }
+
+// Delta tree in baby-step giant-step form (the Vr chain of Alg. 2's rotated item batches): with
+// beta = 2^floor(log2(B) / 2) write d = g beta + r (r < beta); a baby (r > 0) hangs off its giant
+// g beta, one rotation by r w away; a giant g beta (g > 0) hangs off (g - 2^hb(g)) beta, one
+// rotation by 2^hb(g) beta w away. The rotations out of one parent share its ModUp (hoisted
+// fan-out), so a full tree needs about 3 B / (2 beta) ModUps per item batch instead of B / 2.
+int baby_range(int B) { return 1 << (hbit(B) / 2); }
+// parent of d > 0; *step receives the rotation from the parent in blocks
+int tree_parent(int d, int beta, int* step) {
+    const int g = d / beta, r = d % beta;
+    if (r) {
+        *step = r;
+        return g * beta;
+    }
+    const int h = 1 << hbit(g);
+    *step = h * beta;
+    return (g - h) * beta;
+}
+int tree_depth(int d, int beta) { return popc(d / beta) + (d % beta ? 1 : 0); }
+// rotation amounts (in blocks) of the tree: the baby steps 1..beta-1 and the giant steps 2^t beta < B
+std::vector<int> tree_steps(int B) {
+    const int beta = baby_range(B);
+    std::vector<int> st;
+    for (int r = 1; r < std::min(beta, B); r++) st.push_back(r);
+    for (int t = beta; t < B; t <<= 1) st.push_back(t);
+    return st;
+}
 
 struct Group {
     int b, c, delta;
@@ -217,9 +244,9 @@ void check_plan_keys(const fhe_mf_plan& p) {
     Ctx& c = *p.c;
     if (!c.have_keys) fail(FHE_ERR_MISSING_KEY, "keys have not been generated");
     for (int r : rotsum_steps(p.kp)) rotation_key(c, r);
-    for (int t = 0; t < p.beta; t++) {
-        rotation_key(c, (1 << t) * p.w);
-        rotation_key(c, -(1 << t) * p.w);
+    for (int x : tree_steps(p.B)) {
+        rotation_key(c, x * p.w);
+        rotation_key(c, -x * p.w);
     }
     rotation_key(c, -p.kp);
 }
@@ -269,25 +296,27 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
         auto TV = [&](int nd) { return p.d_TV + (size_t)(nd - nd0) * 3 * lw; };
         CK(cudaMemsetAsync(p.d_TV, 0, sizeof(u64) * nodes * 3 * lw, s));
         CK(cudaMemsetAsync(p.d_H, 0, sizeof(u64) * nodes * w, s));
-        int maxpop = 0;
-        for (int nd = nd0; nd < nd1; nd++) maxpop = std::max(maxpop, popc(p.node_delta[nd]));
+        const int baby = baby_range(p.B);
+        int maxdepth = 0;
+        for (int nd = nd0; nd < nd1; nd++) maxdepth = std::max(maxdepth, tree_depth(p.node_delta[nd], baby));
 
-        // 1. delta trees of the wave's item batches, one launch set per popcount level
+        // 1. delta trees of the wave's item batches, one launch set per tree depth
         {
             std::vector<UnItem> roots;
             for (int cb = cb0; cb < cb1; cb++) roots.push_back({VD(cb), Vr(p.node(cb, 0))});
             items_copy(c, roots, 2, l0 + 1, s);
-            for (int pc = 1; pc <= maxpop; pc++) {
+            for (int dep = 1; dep <= maxdepth; dep++) {
                 std::vector<const u64*> in;
                 std::vector<u64*> out;
                 std::vector<int> steps;
                 for (int nd = nd0; nd < nd1; nd++) {
                     int d = p.node_delta[nd];
-                    if (popc(d) != pc) continue;
-                    int hb = 1 << hbit(d);
-                    in.push_back(Vr(p.node(p.node_c[nd], d - hb)));
+                    if (tree_depth(d, baby) != dep) continue;
+                    int step = 0;
+                    const int par = tree_parent(d, baby, &step);
+                    in.push_back(Vr(p.node(p.node_c[nd], par)));
                     out.push_back(Vr(nd));
-                    steps.push_back(hb * p.w);
+                    steps.push_back(step * p.w);
                 }
                 rotate_fanout_items(c, in, out, steps, l0, s);  // siblings share their parent's ModUp
             }
@@ -392,10 +421,10 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
         {
             u64* rot_buf = p.d_chunk;  // reuse the chunk area
             const int cap = (int)((size_t)p.chunk_alloc * 14 * lw / w);
-            for (int pc = maxpop; pc >= 1; pc--) {
+            for (int dep = maxdepth; dep >= 1; dep--) {
                 std::vector<int> lvl;
                 for (int nd = nd0; nd < nd1; nd++)
-                    if (popc(p.node_delta[nd]) == pc) lvl.push_back(nd);
+                    if (tree_depth(p.node_delta[nd], baby) == dep) lvl.push_back(nd);
                 for (size_t o = 0; o < lvl.size(); o += cap) {
                     size_t cnt = std::min(lvl.size() - o, (size_t)cap);
                     std::vector<const u64*> in;
@@ -405,11 +434,12 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
                     for (size_t i = 0; i < cnt; i++) {
                         int nd = lvl[o + i];
                         int d = p.node_delta[nd];
-                        int hb = 1 << hbit(d);
+                        int step = 0;
+                        const int par = tree_parent(d, baby, &step);
                         in.push_back(H(nd));
                         out.push_back(rot_buf + i * w);
-                        steps.push_back(-hb * p.w);
-                        by_parent[p.node(p.node_c[nd], d - hb)].push_back((int)i);
+                        steps.push_back(-step * p.w);
+                        by_parent[p.node(p.node_c[nd], par)].push_back((int)i);
                     }
                     rotate_items(c, in, out, steps, l2, false, s);
                     std::vector<AccTarget> tg;
@@ -599,7 +629,7 @@ void build_layout(fhe_mf_plan& p, int slots, int n, int m, int k, const int64_t*
         in[0] = 1;
         for (const Group& g : p.groups)
             if (g.c == cb)
-                for (int d = g.delta; d && !in[d]; d -= 1 << hbit(d)) in[d] = 1;
+                for (int d = g.delta, st = 0; d && !in[d]; d = tree_parent(d, baby_range(p.B), &st)) in[d] = 1;
         for (int d = 0; d < p.B; d++)
             if (in[d]) {
                 p.closure[cb].push_back(d);
@@ -666,8 +696,9 @@ int fhe_mf_rotation_steps(const fhe_ctx* ctx, int32_t k, int32_t* out, size_t ca
     if (w > c.slots) return FHE_ERR_INVALID_ARG;
     int B = c.slots / w;
     std::vector<int> st = rotsum_steps(kp);
-    for (int t = 0; (1 << t) < B; t++) st.push_back((1 << t) * w);
-    for (int t = 0; (1 << t) < B; t++) st.push_back(-(1 << t) * w);
+    const std::vector<int> tree = tree_steps(B);
+    for (int x : tree) st.push_back(x * w);
+    for (int x : tree) st.push_back(-x * w);
     st.push_back(-kp);
     if (out) {
         if (cap < st.size()) return FHE_ERR_INVALID_ARG;

@@ -43,7 +43,7 @@ def test_plan_groups_partition_ratings():
             assert sum(len(g.a) for g in plan.groups if g.b == b and g.c == c) == len(lst)
         for c, nodes in enumerate(plan.closure):
             for d in nodes:
-                assert d == 0 or (d - (1 << mf.highest_bit(d))) in nodes
+                assert d == 0 or mf.tree_parent(d, plan.baby)[0] in nodes
 
 
 def test_fp64_epoch_hand_checked_2x2():
@@ -229,3 +229,30 @@ def test_encrypted_predict_matches_fp64_row():
         got = np.concatenate([he.decrypt(ct)[::plan.w][:plan.B] for ct in out])[:m]
         want = V @ U[user]
         assert np.abs(got - want).max() < 1e-6
+
+
+def test_delta_tree_baby_step_giant_step():
+    """Every delta d < B is reached from 0 along its parents by rotations summing to d; a baby hangs
+    off its giant, a giant off a giant; the tree's rotation amounts are the baby steps 1..beta-1 and
+    the giant steps 2^t beta; a full tree needs only about 3B/(2 beta) parents (ModUps) instead of B/2."""
+    for B in (2, 4, 8, 32, 512, 1024, 2048):
+        beta = mf.baby_range(B)
+        assert beta * beta <= B < 4 * beta * beta
+        parents = set()
+        for d in range(1, B):
+            total, x, depth = 0, d, 0
+            while x:
+                par, step = mf.tree_parent(x, beta)
+                assert par < x and step > 0 and step in mf.tree_steps(B)
+                parents.add(par)
+                total += step
+                x = par
+                depth += 1
+            assert total == d and depth == mf.tree_depth(d, beta)
+            g, r = divmod(d, beta)
+            assert (mf.tree_parent(d, beta)[0] == g * beta) if r else (mf.tree_parent(d, beta)[0] % beta == 0)
+        assert sorted(mf.tree_steps(B)) == sorted(set(range(1, min(beta, B))) |
+                                                  {beta << t for t in range(16) if (beta << t) < B})
+        assert len(parents) <= 3 * B // (2 * beta) + 1
+    assert mf.delta_closure([37], 16) == [0, 32, 37]            # 37 = 2*16 + 5: giant 32 = 0 + 2*16, then + 5
+    assert mf.delta_closure([53], 16) == [0, 16, 48, 53]        # 53 = 3*16 + 5: giants 16, 48 = 16 + 2*16
