@@ -299,6 +299,7 @@ struct Ctx {
         int inner = 0;  // plain / fan-out key inner product (InnerVariant of ks_inner.cuh)
         int hoist = 0;  // hoisted rotate-and-sum inner product
         int ntt = 0;    // tile shape of the plain two-pass NTT (NttTile of ntt_tile.cuh)
+        int ks = 0;     // tile shape of the fused key-switch / rescale passes (KsTile of ks_pass.cuh)
     } tune;
     int max_prime_bits = 0;       // over every prime
     int max_data_prime_bits = 0;  // over the data primes q_0..q_L

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ks_inner.cuh"
+#include "ks_pass.cuh"
 #include "ntt_tile.cuh"
 
 using namespace fhe;
@@ -29,6 +30,7 @@ const Family kFamilies[] = {
     {"ks_hoist_inner", INNER_N_VARIANTS, kInnerVariantNames, &Ctx::Tune::hoist},
     {"ks_inner", INNER_N_VARIANTS, kInnerVariantNames, &Ctx::Tune::inner},
     {"ntt", ntt_tile::NTT_N_TILES, ntt_tile::kNttTileNames, &Ctx::Tune::ntt},
+    {"ks_pass", ksp::KS_N_TILES, ksp::kKsTileNames, &Ctx::Tune::ks},
 };
 constexpr int kNumFamilies = sizeof(kFamilies) / sizeof(kFamilies[0]);
 
@@ -187,6 +189,38 @@ void tune_ntt(Ctx& c, std::vector<fhe_tune_result>& out) {
     CK(cudaDeviceSynchronize());
 }
 
+// Time every tile shape of the fused key-switch / rescale passes on the exact rescale of 64 synthetic
+// ciphertexts at `level` (an inverse pass with the gather load and scaled store, a forward pass with
+// the centred load and the rescale store; rings of 2^14 and more only).
+void tune_ks(Ctx& c, int level, std::vector<fhe_tune_result>& out) {
+    const Family& fam = kFamilies[3];
+    if (c.log_n < 14) return;
+    const int items = 64;
+    DevTmp tmp;
+    const size_t w = c.ct_words();
+    u64* in = tmp.get((size_t)items * w);
+    u64* res = tmp.get((size_t)items * w);
+    fill_residues<<<1024, 256>>>(in, (size_t)items * w, c.log_n, 1, c.d_primes, 6);
+    CK(cudaGetLastError());
+    std::vector<UnItem> it;
+    for (int t = 0; t < items; t++) it.push_back({in + (size_t)t * w, res + (size_t)t * w});
+    double best = 1e30;
+    int best_v = 0;
+    const size_t first = out.size();
+    for (int v = 0; v < fam.n_variants; v++) {
+        c.tune.ks = v;
+        const double ms = time_ms([&] { items_rescale(c, it, 2, level, (cudaStream_t)0); }, 3);
+        out.push_back(fhe_tune_result{fam.name, fam.variant_names[v], 0, ms});
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    out[first + best_v].chosen = 1;
+    c.tune.ks = best_v;
+    CK(cudaDeviceSynchronize());
+}
+
 template <typename F>
 int guarded(Ctx& c, F&& f) {
     try {
@@ -215,6 +249,8 @@ extern "C" int fhe_autotune(fhe_ctx* ctx, int32_t level, fhe_tune_result* out, i
         CK(cudaDeviceSynchronize());
         tune_inner(c, level, res);
         tune_ntt(c, res);
+        tune_ks(c, level, res);
+        c.arena.reset((cudaStream_t)0);
     });
     if (rc) return rc;
     const int n = (int)std::min<size_t>(res.size(), (size_t)cap);

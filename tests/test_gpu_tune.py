@@ -102,3 +102,31 @@ def test_ntt_tile_shapes_bit_identical(preset):
     rows = [r for r in res if r["family"] == "ntt"]
     assert sorted(r["variant"] for r in rows) == ["r16b3", "r16b4", "r32b4", "r8b4"]
     assert sum(r["chosen"] for r in rows) == 1
+    rows = [r for r in res if r["family"] == "ks_pass"]
+    assert sorted(r["variant"] for r in rows) == ["r16", "r8"] and sum(r["chosen"] for r in rows) == 1
+
+
+@pytest.mark.parametrize("preset", ["paper", "t16a3"])
+def test_ks_pass_tile_shapes_bit_identical(preset):
+    """Every tile shape of the fused key-switch / rescale passes gives the same rotation, product and
+    rescale (N = 2^15 and 2^16)."""
+    ctx = gpu_ctx(preset, 26, [1, 5])
+    rng = np.random.default_rng(7)
+    count = 3
+    a, b = ctx.empty_ct(count), ctx.empty_ct(count)
+    for t in range(count):
+        ctx.encrypt(rng.normal(size=64), ctx.top, 300 + t, ct_slice(ctx, a, t))
+        ctx.encrypt(rng.normal(size=64), ctx.top, 400 + t, ct_slice(ctx, b, t))
+    ref = None
+    for v in ("r16", "r8"):
+        ctx.set_variant("ks_pass", v)
+        ro, pr, rs = ctx.empty_ct(count), ctx.empty_ct(count), ctx.empty_ct(count)
+        ctx.rotate(a, ro, count, ctx.top, 5)
+        ctx.mul_relin_rescale(a, b, pr, count, ctx.top)
+        ctx.rescale(a, rs, count, ctx.top)
+        torch.cuda.synchronize()
+        got = (ro, pr, rs)
+        if ref is None:
+            ref = got
+        for name, x, y in zip(("rotate", "mul_relin_rescale", "rescale"), got, ref):
+            assert torch.equal(x, y), f"{preset}: tile shape {v} changes {name}"
