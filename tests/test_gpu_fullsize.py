@@ -5,7 +5,7 @@
   ratings sit on two diagonals of two item batches and two user batches, so that the two-pass NTT,
   the fused ModUp / ModDown / relinearise-rescale passes, the plaintext-product rescale, the seeded
   rating ciphertexts (c1 regenerated on the device), the hoisted tree fan-out along a multi-node
-  delta-tree path (0 -> 1 -> 5) and the cached masks all run at the benchmark's instantiation. Every
+  delta-tree path (0 -> 32 -> 37) and the cached masks all run at the benchmark's instantiation. Every
   output ciphertext is compared with the oracle's in coefficient form.
 * The served ring (N = 2^16, thirteen 50-bit data primes, three 60-bit special primes, k = 16): one
   request through the server (one fold-in step, then the prediction row over two item batches),
@@ -27,13 +27,13 @@ pytestmark = pytest.mark.gpu
 
 
 def _paper_case():
-    """Users 0..39 rate items i, i + 5 (item batch 0) and 512 + i, 512 + i + 5 (item batch 1);
+    """Users 0..39 rate items i, i + 37 (item batch 0) and 512 + i, 512 + i + 37 (item batch 1);
     users 512..529 (user batch 1) rate item i - 512. B = 512 at N = 2^15 with k = 10, so the groups
-    are (b, c, delta) = (0,0,0), (0,0,5), (0,1,0), (0,1,5), (1,0,0) and each item batch's delta tree
-    is 0 -> 1 -> 5."""
+    are (b, c, delta) = (0,0,0), (0,0,37), (0,1,0), (0,1,37), (1,0,0), and each item batch's delta
+    tree (baby steps below 16) is 0 -> 32 -> 37: a giant step, then a baby step."""
     rows, cols = [], []
     for i in range(40):
-        for j in (i, (i + 5) % 512, 512 + i, 512 + i + 5):
+        for j in (i, (i + 37) % 512, 512 + i, 512 + i + 37):
             rows.append(i)
             cols.append(j)
     for i in range(512, 530):
