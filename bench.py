@@ -69,6 +69,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variants", default="", help="family=variant,... to set instead of autotuning "
+                                                   "(e.g. for a reproducible profile)")
     ap.add_argument("--served-requests", type=int, default=1000, help="requests per arrival rate")
     ap.add_argument("--served-pool", type=int, default=256, help="distinct pre-encrypted requests")
     ap.add_argument("--served-slots", type=int, default=48)
@@ -779,6 +781,11 @@ def run_epoch(args, rank, world, dev, dist, barrier, sub=False):
 def autotune(ctx, args):
     """Run the library's autotuner (untimed) unless --no-autotune; returns the chosen variant per
     kernel family and every variant's time, for the bench line."""
+    if args.variants:
+        for fv in args.variants.split(","):
+            fam, var = fv.split("=")
+            ctx.set_variant(fam.strip(), var.strip())
+        return {"autotuned": False, "set": args.variants}
     if args.no_autotune:
         return {"autotuned": False}
     res = ctx.autotune()

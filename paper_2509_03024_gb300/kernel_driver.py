@@ -5,6 +5,7 @@
   python -m paper_2509_03024_gb300.kernel_driver rotsum --preset paper --count 64 --kp 16 [--reps 3]
   python -m paper_2509_03024_gb300.kernel_driver probe --preset paper [--reps 2000]
   python -m paper_2509_03024_gb300.kernel_driver tune --preset paper [--level L]
+  (any kind) --variants family=variant,...   sets autotuner families, e.g. ntt=r8b4,ks_pass=r8
 
 `ntt` transforms `rows` limbs of N residues in place (rows / (L+1) polynomials
 of L+1 limbs); `keyswitch` rotates `count` top-level ciphertexts by one slot
@@ -33,6 +34,7 @@ def main():
     ap.add_argument("kind", choices=["ntt", "keyswitch", "rotsum", "probe", "tune"])
     ap.add_argument("--level", type=int, default=None)
     ap.add_argument("--variant", default=None, help="inner-product variant to use (ks_inner and ks_hoist_inner)")
+    ap.add_argument("--variants", default="", help="family=variant,... of the autotuner families to set")
     ap.add_argument("--kp", type=int, default=16)
     ap.add_argument("--preset", default="paper")
     ap.add_argument("--rows", type=int, default=1024)
@@ -53,6 +55,9 @@ def main():
     if args.variant:
         ctx.set_variant("ks_inner", args.variant)
         ctx.set_variant("ks_hoist_inner", args.variant)
+    for fv in filter(None, args.variants.split(",")):
+        fam, var = fv.split("=")
+        ctx.set_variant(fam, var)
     if args.kind == "keyswitch":
         ctx.keygen(1, [1])
     elif args.kind == "rotsum":
