@@ -243,7 +243,7 @@ int fhe_probe_int_pipe(fhe_ctx* ctx, int32_t reps, fhe_int_pipe_rates* out);
  * is 1 for the kept variant, `ms` the best of three timed launches). Returns the number of records
  * or an error code. Synchronises the device; allocates and frees temporary device memory.
  * Families: "ks_hoist_inner" (the hoisted rotate-and-sum's key inner product, 15 rotations),
- * "ks_inner" (a relinearisation's key inner product), variants v0 c1 p1 s1 s2; and "ntt" (the tile
+ * "ks_inner" (a relinearisation's key inner product), variants v0 c1 p1 s1 s2 s2l; "ntt" (the tile
  * shape of the plain two-pass NTT of rings 2^14..2^16: rows or columns per tile and residues per
  * thread, variants r16b4 r8b4 r32b4 r16b3; timed on a forward plus inverse transform of 256 rows);
  * "ks_pass" (rows or columns per tile of the fused key-switch and rescale passes of rings 2^14..2^16,

@@ -22,7 +22,7 @@
 
 namespace fhe {
 
-const char* const kInnerVariantNames[INNER_N_VARIANTS] = {"v0", "c1", "p1", "s1", "s2"};
+const char* const kInnerVariantNames[INNER_N_VARIANTS] = {"v0", "c1", "p1", "s1", "s2", "s2l"};
 
 namespace {
 
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) inner2_kernel(InnerArgs a) {
     else inner2_body<MACS, IPT, FANOUT>(a, x, k2, t0);
 }
 
-template <class MAC, int IPT>
+template <class MAC, int IPT, bool SCALAR = false>
 __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, int t0) {
     const int log_n = a.log_n, hl = log_n - 1;
     const int l1 = a.level + 1;
@@ -320,8 +320,17 @@ __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, i
             const ulonglong2 ka = kr[(size_t)(2 * j + 1) * kstride];
 #pragma unroll
             for (int i = 0; i < IPT; i++) {
-                const ulonglong2 v = (j == own ? ownr[i] : ext0[i] + (size_t)j * dstride)[sp];
-                const u64 vx = sw ? v.y : v.x, vy = sw ? v.x : v.y;
+                const ulonglong2* row = j == own ? ownr[i] : ext0[i] + (size_t)j * dstride;
+                u64 vx, vy;
+                if (SCALAR) {  // slots 2 k2 and 2 k2 + 1 come from slots src and src ^ 1
+                    const u64* r64 = reinterpret_cast<const u64*>(row);
+                    vx = r64[src];
+                    vy = r64[src ^ 1];
+                } else {
+                    const ulonglong2 v = row[sp];
+                    vx = sw ? v.y : v.x;
+                    vy = sw ? v.x : v.y;
+                }
                 s0x[i].mac(vx, kb.x);
                 s0y[i].mac(vy, kb.y);
                 s1x[i].mac(vx, ka.x);
@@ -353,7 +362,7 @@ __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, i
     }
 }
 
-template <class MACD, class MACS, int IPT>
+template <class MACD, class MACS, int IPT, bool SCALAR = false>
 __global__ void __launch_bounds__(256) hoist2_kernel(InnerArgs a) {
     const int hl = a.log_n - 1;
     const int x = blockIdx.y;
@@ -361,8 +370,8 @@ __global__ void __launch_bounds__(256) hoist2_kernel(InnerArgs a) {
     const int k2 = (int)(e & ((1u << hl) - 1u));
     const int t0 = (int)(e >> hl) * IPT;
     if (t0 >= a.items) return;
-    if (x <= a.level && a.split25) hoist2_body<MACD, IPT>(a, x, k2, t0);
-    else hoist2_body<MACS, IPT>(a, x, k2, t0);
+    if (x <= a.level && a.split25) hoist2_body<MACD, IPT, SCALAR>(a, x, k2, t0);
+    else hoist2_body<MACS, IPT, SCALAR>(a, x, k2, t0);
 }
 
 inline unsigned grid1(size_t work) {
@@ -391,7 +400,7 @@ void launch_ks_inner(const InnerArgs& a0, bool fanout, int variant, int max_data
     }
     // split at bit 25 needs data primes below 2^50 and at most 2^13 terms per sum
     a.split25 = max_data_prime_bits <= 50 && a.dn <= (1 << 13);
-    const bool two = variant == INNER_S2 && !fanout && a.shared_key;
+    const bool two = (variant == INNER_S2 || variant == INNER_S2L) && !fanout && a.shared_key;
 #define L2(MD, MS, I, F) inner2_kernel<MD, MS, I, F><<<grid2(a, I), 256, 0, s>>>(a)
     switch (variant) {
         case INNER_C1:
@@ -426,6 +435,7 @@ void launch_ks_hoist_inner(const InnerArgs& a0, int variant, int max_data_prime_
         case INNER_C1: H2(MacC, MacC, 1); break;
         case INNER_P1: H2(MacP32, MacP32, 1); break;
         case INNER_S2: H2(MacS25, MacP32, 2); break;
+        case INNER_S2L: hoist2_kernel<MacS25, MacP32, 2, true><<<grid2(a, 2), 256, 0, s>>>(a); break;
         default: H2(MacS25, MacP32, 1); break;
     }
 #undef H2

@@ -45,6 +45,8 @@ enum InnerVariant {
     INNER_P1,       // ... 32-bit schoolbook carry chain; 1 item per thread
     INNER_S1,       // ... data limbs split at bit 25 into carry-free column sums, special limbs P32
     INNER_S2,       // S1 with 2 items per thread sharing the key loads (plain: when the items share a key)
+    INNER_S2L,      // S2 reading each permuted residue with its own 64-bit load instead of a pair load and
+                    // two selects (hoisted only; the plain kernel runs S2)
     INNER_N_VARIANTS
 };
 extern const char* const kInnerVariantNames[INNER_N_VARIANTS];

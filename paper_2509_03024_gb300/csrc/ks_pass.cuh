@@ -49,20 +49,43 @@ struct CombineArgs {
     const u64* qlinv;  // ST_COMBINE_RS: [L+1][2] q_l^-1 mod q_i
 };
 
+// Per-row constants of the first pass's loads, read once per CTA: the row's prime and, for the base
+// conversion, the Shoup pairs of its (at most kConvMax) source limbs.
+constexpr int kConvMax = 4;
+struct RowConst {
+    u64 q, one_s, ql;
+    u64 w[kConvMax], ws[kConvMax];
+};
+
 template <int LOAD>
-__device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, const Prime* __restrict__ pr) {
+__device__ __forceinline__ RowConst row_const(const KsRow& r, const Prime* __restrict__ pr) {
+    RowConst c;
+    c.q = pr[r.prime].q;
+    c.one_s = pr[r.prime].one_s;
+    c.ql = LOAD == LD_CENTRED ? pr[r.limb].q : 0;
+#pragma unroll
+    for (int i = 0; i < kConvMax; i++) {
+        const bool on = LOAD == LD_CONV && i < r.src_cnt;
+        c.w[i] = on ? r.cst[(size_t)i * r.cst_stride] : 0;
+        c.ws[i] = on ? r.cst[(size_t)i * r.cst_stride + 1] : 0;
+    }
+    return c;
+}
+
+template <int LOAD>
+__device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, const Prime* __restrict__ pr,
+                                         const RowConst& rc) {
     if (LOAD == LD_PLAIN) return r.dst[k];
     if (LOAD == LD_GATHER) return r.src[r.galois == 1 ? (int)k : auto_src((int)k, r.galois, log_n)];
     if (LOAD == LD_CENTRED) {  // the centred representative of src[k] (mod q_limb) reduced mod the row's prime
-        const Prime P = pr[r.prime];
-        const u64 ql = pr[r.limb].q, v = r.src[k];
+        const u64 ql = rc.ql, v = r.src[k];
         const bool neg = v > (ql >> 1);
-        const u64 m = nttc::reduce_any(neg ? ql - v : v, P.q, P.one_s);
-        return neg ? (m ? P.q - m : 0) : m;
+        const u64 m = nttc::reduce_any(neg ? ql - v : v, rc.q, rc.one_s);
+        return neg ? (m ? rc.q - m : 0) : m;
     }
     if (LOAD == LD_MUL) return mul_mod(r.src[k], r.src2[k], pr[r.prime]);
     if (LOAD == LD_AXPY) {  // src + cst2 * src2 (both reduced)
-        const u64 p = pr[r.prime].q;
+        const u64 p = rc.q;
         u64 v = r.src[k];
         if (r.src2) v = add_mod(v, mul_shoup(r.src2[k], r.cst2[0], r.cst2[1], p), p);
         return v;
@@ -70,7 +93,31 @@ __device__ __forceinline__ u64 load_elem(const KsRow& r, size_t k, int log_n, co
     // LD_CONV: sum of the converted source limbs. For primes below 2^58 the forward transform that
     // follows runs without intermediate reduction, so the sum stays lazy (each term below 2p, at most
     // 8 terms, so below 16p; 16 stages add less than 32p: below 48p < 2^64); otherwise fully reduced.
-    const u64 p = pr[r.prime].q;
+    // Up to kConvMax sources: every source load is issued before the products (fixed trip count,
+    // predicated), so a thread's loads are in flight together.
+    const u64 p = rc.q;
+    if (r.src_cnt <= kConvMax) {
+        u64 x[kConvMax];
+#pragma unroll
+        for (int i = 0; i < kConvMax; i++) x[i] = i < r.src_cnt ? r.src[((size_t)i << log_n) + k] : 0;
+        if (p < ((u64)1 << 58)) {
+            u64 lazy = 0;
+#pragma unroll
+            for (int i = 0; i < kConvMax; i++)
+                if (i < r.src_cnt) lazy += shoup_lazy(x[i], rc.w[i], rc.ws[i], p);
+            return lazy;
+        }
+        u64 acc = 0;
+#pragma unroll
+        for (int i = 0; i < kConvMax; i++)
+            if (i < r.src_cnt) {
+                u64 t = shoup_lazy(x[i], rc.w[i], rc.ws[i], p);
+                t = t >= p ? t - p : t;
+                acc += t;
+                acc = acc >= p ? acc - p : acc;
+            }
+        return acc;
+    }
     if (p < ((u64)1 << 58) && r.src_cnt <= 8) {
         u64 lazy = 0;
         for (int i = 0; i < r.src_cnt; i++) {
@@ -163,6 +210,7 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
     extern __shared__ u64 sm[];
     const int tid = threadIdx.x;
     const KsRow r = rows[blockIdx.x];
+    const RowConst rc = row_const<LOAD>(r, primes);
     const u64 q = primes[r.prime].q;
     const ulonglong2* W = tw + ((size_t)r.prime << log_n);
     const int log_n2 = PASS == 0 ? log_n - LOGM : LOGM;
@@ -177,7 +225,7 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
 #pragma unroll
         for (int u = 0; u < V; u++)
             v[u] = load_elem<LOAD>(r, (size_t)(t0 + qq) + ((size_t)nttc::block_elem<LOGM, RB>(fb, g, u) << log_n2),
-                                   log_n, primes);
+                                   log_n, primes, rc);
         if (!INV && q < ((u64)1 << 58))
             nttc::tile_stages<LOGM, R, INV, PASS, false, true, true, RB>(sm, W, q, S1, t0, v);
         else
@@ -193,13 +241,13 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
 #pragma unroll 4
         for (int e = tid; e < R * M; e += T) {
             int x = e / R, qq = e % R;
-            sm[x * P + qq] = load_elem<LOAD>(r, (size_t)(t0 + qq) + ((size_t)x << log_n2), log_n, primes);
+            sm[x * P + qq] = load_elem<LOAD>(r, (size_t)(t0 + qq) + ((size_t)x << log_n2), log_n, primes, rc);
         }
     } else {
 #pragma unroll 4
         for (int e = tid; e < R * M; e += T) {
             int x = e & (M - 1), qq = e >> LOGM;
-            sm[x * P + qq] = load_elem<LOAD>(r, ((size_t)(t0 + qq) << LOGM) + x, log_n, primes);
+            sm[x * P + qq] = load_elem<LOAD>(r, ((size_t)(t0 + qq) << LOGM) + x, log_n, primes, rc);
         }
     }
     __syncthreads();

@@ -10,7 +10,7 @@ from tests.gpu_common import ct_slice, gpu_ctx, torch
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["v0", "c1", "p1", "s1", "s2"]
+VARIANTS = ["v0", "c1", "p1", "s1", "s2", "s2l"]
 
 
 @pytest.mark.parametrize("preset", ["t11a2", "paper"])
@@ -51,7 +51,7 @@ def test_epoch_identical_under_every_variant():
     plan.encrypt_factors(0, U, U0)
     plan.encrypt_factors(1, V, V0)
     ref = None
-    for v in ("v0", "s2", "c1", "p1"):
+    for v in ("v0", "s2", "c1", "p1", "s2l"):
         ctx.set_variant("ks_hoist_inner", v)
         ctx.set_variant("ks_inner", v)
         UD, VD = U0.clone(), V0.clone()
