@@ -247,7 +247,7 @@ int fhe_probe_int_pipe(fhe_ctx* ctx, int32_t reps, fhe_int_pipe_rates* out);
  * shape of the plain two-pass NTT of rings 2^14..2^16: rows or columns per tile and residues per
  * thread, variants r16b4 r8b4 r32b4 r16b3; timed on a forward plus inverse transform of 256 rows);
  * "ks_pass" (rows or columns per tile of the fused key-switch and rescale passes of rings 2^14..2^16,
- * variants r16 r8; timed on the exact rescale of 64 ciphertexts). A fresh context uses the first
+ * variants r16 r8 r8x; timed on the exact rescale of 64 ciphertexts). A fresh context uses the first
  * variant of each.
  * `family` and `variant` point to static strings. */
 typedef struct {

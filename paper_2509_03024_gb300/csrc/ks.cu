@@ -38,7 +38,7 @@
 
 namespace fhe {
 
-const char* const ksp::kKsTileNames[ksp::KS_N_TILES] = {"r16", "r8"};
+const char* const ksp::kKsTileNames[ksp::KS_N_TILES] = {"r16", "r8", "r8x"};
 
 namespace {
 

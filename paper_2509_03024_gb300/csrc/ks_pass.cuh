@@ -198,8 +198,11 @@ constexpr int ks_min_blocks(int rb, int threads) {
     return (rb == 3 ? 1024 : 768) / threads > 0 ? (rb == 3 ? 1024 : 768) / threads : 1;
 }
 
-template <int LOGN, int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB>
-__global__ void __launch_bounds__(R * (1 << LOGM) / (1 << RB), ks_min_blocks(RB, R * (1 << LOGM) / (1 << RB)))
+// LOOSE halves the CTAs per SM the launch bounds ask for, which doubles the registers a thread may use
+// (fewer spills, lower occupancy).
+template <int LOGN, int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB, bool LOOSE = false>
+__global__ void __launch_bounds__(R * (1 << LOGM) / (1 << RB),
+                                  (ks_min_blocks(RB, R * (1 << LOGM) / (1 << RB)) + (LOOSE ? 1 : 0)) / (LOOSE ? 2 : 1))
 ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, const ulonglong2* __restrict__ tw,
               const u64* __restrict__ ninv, CombineArgs ca) {
     constexpr int log_n = LOGN;  // the ring size is a compile-time constant of each launch
@@ -273,7 +276,7 @@ ks_ntt_kernel(const KsRow* __restrict__ rows, const Prime* __restrict__ primes, 
 
 // The fused passes keep radix-8 register blocks: with 16 residues per thread their load and
 // store stages run out of registers (measured slower, unlike the plain transform).
-template <int LOGN, int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB = 3>
+template <int LOGN, int LOGM, int R, bool INV, int PASS, int LOAD, int STORE, int RB = 3, bool LOOSE = false>
 void launch_pass(const Ctx& c, const KsRow* rows, int n_rows, int tiles, const CombineArgs& ca, int cls, double bytes,
                  cudaStream_t s) {
     if (n_rows == 0) return;
@@ -281,17 +284,17 @@ void launch_pass(const Ctx& c, const KsRow* rows, int n_rows, int tiles, const C
     constexpr size_t smem = sizeof(u64) * (1 << LOGM) * (R == 1 ? 1 : R + 1);
     const ulonglong2* tw = PASS == 1 ? (INV ? c.d_itw2 : c.d_tw2) : (INV ? c.d_itw : c.d_tw);
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGN, LOGM, R, INV, PASS, LOAD, STORE, RB>,
+        CK(cudaFuncSetAttribute(ks_ntt_kernel<LOGN, LOGM, R, INV, PASS, LOAD, STORE, RB, LOOSE>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchScope _ls(c.prof, cls, bytes, s, (double)n_rows * ((size_t)1 << (c.log_n - 1)) * LOGM);
-    ks_ntt_kernel<LOGN, LOGM, R, INV, PASS, LOAD, STORE, RB><<<dim3(n_rows, tiles), T, smem, s>>>(rows, c.d_primes, tw,
-                                                                                              c.d_ninv, ca);
+    ks_ntt_kernel<LOGN, LOGM, R, INV, PASS, LOAD, STORE, RB, LOOSE><<<dim3(n_rows, tiles), T, smem, s>>>(
+        rows, c.d_primes, tw, c.d_ninv, ca);
     CK(cudaGetLastError());
 }
 
 // A full forward (INV = false) or inverse transform over a row table: the first pass applies
 // LOAD, the last pass applies STORE (single-pass rings do both in one kernel).
-template <bool INV, int LOAD, int STORE, int R>
+template <bool INV, int LOAD, int STORE, int R, bool LOOSE = false>
 void ks_transform_t(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs& ca, int cls, double bytes,
                     cudaStream_t s) {
     constexpr int FIRST_ST = ST_LAZY;
@@ -308,29 +311,29 @@ void ks_transform_t(const Ctx& c, const KsRow* rows, int n_rows, const CombineAr
 #undef SINGLE
         case 14:
             if (!INV) {
-                launch_pass<14, 7, R, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
-                launch_pass<14, 7, R, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
+                launch_pass<14, 7, R, false, 0, LOAD, FIRST_ST, 3, LOOSE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
+                launch_pass<14, 7, R, false, 1, LD_PLAIN, STORE, 3, LOOSE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
             } else {
-                launch_pass<14, 7, R, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
-                launch_pass<14, 7, R, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
+                launch_pass<14, 7, R, true, 1, LOAD, FIRST_ST, 3, LOOSE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
+                launch_pass<14, 7, R, true, 0, LD_PLAIN, STORE, 3, LOOSE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
             }
             return;
         case 15:
             if (!INV) {
-                launch_pass<15, 7, R, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
-                launch_pass<15, 8, R, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
+                launch_pass<15, 7, R, false, 0, LOAD, FIRST_ST, 3, LOOSE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
+                launch_pass<15, 8, R, false, 1, LD_PLAIN, STORE, 3, LOOSE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
             } else {
-                launch_pass<15, 8, R, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
-                launch_pass<15, 7, R, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
+                launch_pass<15, 8, R, true, 1, LOAD, FIRST_ST, 3, LOOSE>(c, rows, n_rows, 128 / R, ca, cls, bytes, s);
+                launch_pass<15, 7, R, true, 0, LD_PLAIN, STORE, 3, LOOSE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
             }
             return;
         case 16:
             if (!INV) {
-                launch_pass<16, 8, R, false, 0, LOAD, FIRST_ST>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
-                launch_pass<16, 8, R, false, 1, LD_PLAIN, STORE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
+                launch_pass<16, 8, R, false, 0, LOAD, FIRST_ST, 3, LOOSE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
+                launch_pass<16, 8, R, false, 1, LD_PLAIN, STORE, 3, LOOSE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
             } else {
-                launch_pass<16, 8, R, true, 1, LOAD, FIRST_ST>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
-                launch_pass<16, 8, R, true, 0, LD_PLAIN, STORE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
+                launch_pass<16, 8, R, true, 1, LOAD, FIRST_ST, 3, LOOSE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
+                launch_pass<16, 8, R, true, 0, LD_PLAIN, STORE, 3, LOOSE>(c, rows, n_rows, 256 / R, ca, cls, bytes, s);
             }
             return;
         default: fail(FHE_ERR_INVALID_ARG, "unsupported ring degree");
@@ -338,9 +341,10 @@ void ks_transform_t(const Ctx& c, const KsRow* rows, int n_rows, const CombineAr
 }
 
 // The tile shapes of the fused passes the autotuner chooses between (family "ks_pass"): rows or
-// columns per tile of the two-pass rings; every shape computes the same bits. Each shape's
-// instantiations live in a translation unit of their own (ks_pass16.cu, ks_pass8.cu).
-enum KsTile { KS_R16 = 0, KS_R8, KS_N_TILES };
+// columns per tile of the two-pass rings (r8x: 8 with the register cap of LOOSE launch bounds); every
+// shape computes the same bits. Each shape's instantiations live in a translation unit of their own
+// (ks_pass16.cu, ks_pass8.cu, ks_pass8x.cu).
+enum KsTile { KS_R16 = 0, KS_R8, KS_R8X, KS_N_TILES };
 extern const char* const kKsTileNames[KS_N_TILES];
 
 #define KS_COMBOS(X)                      \
@@ -358,6 +362,9 @@ void ks_transform_r16(const Ctx& c, const KsRow* rows, int n_rows, const Combine
 template <bool INV, int LOAD, int STORE>
 void ks_transform_r8(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs& ca, int cls, double bytes,
                      cudaStream_t s);
+template <bool INV, int LOAD, int STORE>
+void ks_transform_r8x(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs& ca, int cls, double bytes,
+                      cudaStream_t s);
 
 // A full forward (INV = false) or inverse transform over a row table with the context's tile shape:
 // the first pass applies LOAD, the last pass applies STORE (single-pass rings do both in one kernel).
@@ -365,6 +372,7 @@ template <bool INV, int LOAD, int STORE>
 void ks_transform(const Ctx& c, const KsRow* rows, int n_rows, const CombineArgs& ca, int cls, double bytes,
                   cudaStream_t s) {
     if (c.tune.ks == KS_R8) ks_transform_r8<INV, LOAD, STORE>(c, rows, n_rows, ca, cls, bytes, s);
+    else if (c.tune.ks == KS_R8X) ks_transform_r8x<INV, LOAD, STORE>(c, rows, n_rows, ca, cls, bytes, s);
     else ks_transform_r16<INV, LOAD, STORE>(c, rows, n_rows, ca, cls, bytes, s);
 }
 

@@ -103,7 +103,7 @@ def test_ntt_tile_shapes_bit_identical(preset):
     assert sorted(r["variant"] for r in rows) == ["r16b3", "r16b4", "r32b4", "r8b4"]
     assert sum(r["chosen"] for r in rows) == 1
     rows = [r for r in res if r["family"] == "ks_pass"]
-    assert sorted(r["variant"] for r in rows) == ["r16", "r8"] and sum(r["chosen"] for r in rows) == 1
+    assert sorted(r["variant"] for r in rows) == ["r16", "r8", "r8x"] and sum(r["chosen"] for r in rows) == 1
 
 
 @pytest.mark.parametrize("preset", ["paper", "t16a3"])
@@ -118,7 +118,7 @@ def test_ks_pass_tile_shapes_bit_identical(preset):
         ctx.encrypt(rng.normal(size=64), ctx.top, 300 + t, ct_slice(ctx, a, t))
         ctx.encrypt(rng.normal(size=64), ctx.top, 400 + t, ct_slice(ctx, b, t))
     ref = None
-    for v in ("r16", "r8"):
+    for v in ("r16", "r8", "r8x"):
         ctx.set_variant("ks_pass", v)
         ro, pr, rs = ctx.empty_ct(count), ctx.empty_ct(count), ctx.empty_ct(count)
         ctx.rotate(a, ro, count, ctx.top, 5)
