@@ -301,6 +301,9 @@ struct Ctx {
         int ntt = 0;    // tile shape of the plain two-pass NTT (NttTile of ntt_tile.cuh)
         int ks = 0;     // tile shape of the fused key-switch / rescale passes (KsTile of ks_pass.cuh)
     } tune;
+    // the evaluation keys' data-prime rows are stored split at bit 25 (key_pack in ks_inner.cuh),
+    // set when every data prime has at most 50 bits
+    bool keys_packed = false;
     int max_prime_bits = 0;       // over every prime
     int max_data_prime_bits = 0;  // over the data primes q_0..q_L
 

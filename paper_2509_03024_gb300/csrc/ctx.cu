@@ -6,6 +6,7 @@
 #include <stdexcept>
 
 #include "core.cuh"
+#include "ks_inner.cuh"
 
 namespace fhe {
 
@@ -472,6 +473,16 @@ __global__ void evk_kernel(u64* b, const u64* __restrict__ a, const u64* __restr
     }
 }
 
+// The data-prime rows (limbs 0..L) of one key digit's two halves, stored split at bit 25.
+__global__ void key_pack_kernel(u64* kb, u64* ka, int L, int log_n) {
+    const size_t total = (size_t)(L + 1) << log_n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        kb[i] = key_pack(kb[i]);
+        ka[i] = key_pack(ka[i]);
+    }
+}
+
 __global__ void square_kernel(u64* out, const u64* __restrict__ s, int limbs, int log_n,
                               const Prime* __restrict__ pr) {
     const size_t total = (size_t)limbs << log_n;
@@ -915,6 +926,10 @@ static void make_evk(Ctx& c, EvalKey& key, const u64* d_s2, u64 obj, cudaStream_
             evk_kernel<<<blocks_for((size_t)ne * n), kT, 0, s>>>(kb, ka, c.d_sk, d_e, d_s2, ne, c.L, lo, hi,
                                                                  c.log_n, c.d_primes, c.d_pmod);
             CK(cudaGetLastError());
+            if (c.keys_packed) {
+                key_pack_kernel<<<blocks_for((size_t)(c.L + 1) * n), kT, 0, s>>>(kb, ka, c.L, c.log_n);
+                CK(cudaGetLastError());
+            }
         }
         CK(cudaStreamSynchronize(s));  // host staging buffers are reused
     }
@@ -1055,6 +1070,7 @@ int fhe_ctx_create(const fhe_params* p, fhe_ctx** out) {
         for (u64 q : c.primes) c.hprimes.push_back(make_prime(q));
         for (const Prime& P : c.hprimes) c.max_prime_bits = std::max(c.max_prime_bits, (int)P.b);
         for (int i = 0; i <= c.L; i++) c.max_data_prime_bits = std::max(c.max_data_prime_bits, (int)c.hprimes[i].b);
+        c.keys_packed = c.max_data_prime_bits <= 50;
         c.d_primes = dupload(c.hprimes);
         ntt_init();
         build_tables(c);

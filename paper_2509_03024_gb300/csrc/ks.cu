@@ -163,6 +163,7 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
         ia.n_ext = c.n_ext;
         ia.log_n = c.log_n;
         ia.pr = c.d_primes;
+        ia.keys_packed = c.keys_packed;
         if (!hk) {
             LaunchScope _ls(c.prof, K_KS_INNER,
                             8.0 * n * ((double)items * dn * next + (double)nkeys * dn * 2 * next + (double)items * 2 * next),

@@ -46,6 +46,7 @@ struct MacC {
         hi += ph + (lo < pl ? 1 : 0);
     }
     __device__ __forceinline__ u64 reduce(const Prime& P) const { return reduce128(lo, hi, P); }
+    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) { mac(a, packed ? key_unpack(k) : k); }
 };
 
 struct MacP {  // PTX 64-bit multiply-add with carry (the one-item legacy form of the plain kernel)
@@ -54,6 +55,7 @@ struct MacP {  // PTX 64-bit multiply-add with carry (the one-item legacy form o
         asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
     }
     __device__ __forceinline__ u64 reduce(const Prime& P) const { return reduce128(lo, hi, P); }
+    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) { mac(a, packed ? key_unpack(k) : k); }
 };
 
 // Schoolbook on 32-bit words in one carry chain per row: a0 b0 and a1 b1 first, then each cross
@@ -78,6 +80,7 @@ struct MacP32 {
     __device__ __forceinline__ u64 reduce(const Prime& P) const {
         return reduce128(((u64)r1 << 32) | r0, ((u64)r3 << 32) | r2, P);
     }
+    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) { mac(a, packed ? key_unpack(k) : k); }
 };
 
 // Operands below 2^50 split at bit 25: a b = a0 b0 + 2^25 (a0 b1 + a1 b0) + 2^50 a1 b1 with every
@@ -85,15 +88,23 @@ struct MacP32 {
 // four mad.wide.u32 per multiply-accumulate and no additions.
 struct MacS25 {
     u64 C0 = 0, C1 = 0, C2 = 0;
-    __device__ __forceinline__ void mac(u64 a, u64 b) {
-        const u32 m = (1u << 25) - 1u;
-        const u32 a0 = (u32)a & m, a1 = (u32)(a >> 25), b0 = (u32)b & m, b1 = (u32)(b >> 25);
+    __device__ __forceinline__ void mac4(u32 a0, u32 a1, u32 b0, u32 b1) {
         asm("mad.wide.u32 %0, %3, %5, %0;\n\t"
             "mad.wide.u32 %1, %3, %6, %1;\n\t"
             "mad.wide.u32 %1, %4, %5, %1;\n\t"
             "mad.wide.u32 %2, %4, %6, %2;"
             : "+l"(C0), "+l"(C1), "+l"(C2)
             : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    }
+    __device__ __forceinline__ void mac(u64 a, u64 b) {
+        const u32 m = (1u << 25) - 1u;
+        mac4((u32)a & m, (u32)(a >> 25), (u32)b & m, (u32)(b >> 25));
+    }
+    // a packed key (key_pack) already holds its two halves in its two words
+    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) {
+        const u32 m = (1u << 25) - 1u;
+        if (packed) mac4((u32)a & m, (u32)(a >> 25), (u32)k, (u32)(k >> 32));
+        else mac(a, k);
     }
     __device__ __forceinline__ u64 reduce(const Prime& P) const {
         // C0 + 2^25 C1 + 2^50 C2 as (hi, lo)
@@ -130,6 +141,7 @@ __global__ void __launch_bounds__(256, 4) inner_v0_kernel(InnerArgs a) {
         const Prime P = a.pr[px];
         const KsItem it = a.tab[t];
         const int own = x < l1 ? x / a.alpha : -1;
+        const bool packed = a.keys_packed && x < l1;
         MacP s0x, s0y, s1x, s1y;
         const int st = FANOUT ? a.src_of[t] : t;
         for (int j = 0; j < a.dn; j++) {
@@ -145,10 +157,10 @@ __global__ void __launch_bounds__(256, 4) inner_v0_kernel(InnerArgs a) {
             }
             const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 0) * a.n_ext + px) << log_n))[k2];
             const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 1) * a.n_ext + px) << log_n))[k2];
-            s0x.mac(vx, kb.x);
-            s0y.mac(vy, kb.y);
-            s1x.mac(vx, ka.x);
-            s1y.mac(vy, ka.y);
+            s0x.mack(vx, kb.x, packed);
+            s0y.mack(vy, kb.y, packed);
+            s1x.mack(vx, ka.x, packed);
+            s1y.mack(vy, ka.y, packed);
         }
         reinterpret_cast<ulonglong2*>(a.acc + ((size_t)((t * 2 + 0) * a.next + x) << log_n))[k2] =
             make_ulonglong2(s0x.reduce(P), s0y.reduce(P));
@@ -168,6 +180,7 @@ __global__ void __launch_bounds__(256, 3) hoist_v0_kernel(InnerArgs a) {
         const int t = (int)(row % a.items), x = (int)(row / a.items);
         const int px = x < l1 ? x : x + (a.L - a.level);
         const int own = x < l1 ? x / a.alpha : -1;
+        const bool packed = a.keys_packed && x < l1;
         const ulonglong2* ext0 = reinterpret_cast<const ulonglong2*>(a.ext) + (((size_t)t * a.dn * a.next + x) << (log_n - 1));
         const ulonglong2* own_row = reinterpret_cast<const ulonglong2*>(a.tab[t].d) + ((size_t)x << (log_n - 1));
         const size_t dstride = (size_t)a.next << (log_n - 1);
@@ -185,10 +198,10 @@ __global__ void __launch_bounds__(256, 3) hoist_v0_kernel(InnerArgs a) {
                 const u64 vx = sw ? v.y : v.x, vy = sw ? v.x : v.y;
                 const ulonglong2 kb = kr[(size_t)(2 * j) * kstride];
                 const ulonglong2 ka = kr[(size_t)(2 * j + 1) * kstride];
-                s0x.mac(vx, kb.x);
-                s0y.mac(vy, kb.y);
-                s1x.mac(vx, ka.x);
-                s1y.mac(vy, ka.y);
+                s0x.mack(vx, kb.x, packed);
+                s0y.mack(vy, kb.y, packed);
+                s1x.mack(vx, ka.x, packed);
+                s1y.mack(vy, ka.y, packed);
             }
         }
         const Prime P = a.pr[px];
@@ -227,6 +240,7 @@ __device__ __forceinline__ void inner2_body(const InnerArgs& a, int x, int k2, i
     const int l1 = a.level + 1;
     const int px = x < l1 ? x : x + (a.L - a.level);
     const int own = x < l1 ? x / a.alpha : -1;
+    const bool packed = a.keys_packed && x < l1;
     const u64* key = IPT > 1 ? a.shared_key : a.tab[t0].key;
     const int g = IPT > 1 ? (int)a.shared_galois : (int)a.tab[t0].galois;
     const ulonglong2* kr = reinterpret_cast<const ulonglong2*>(key) + ((size_t)px << hl) + k2;
@@ -261,10 +275,10 @@ __device__ __forceinline__ void inner2_body(const InnerArgs& a, int x, int k2, i
             const ulonglong2 v = (j == own ? ownr[i] : ext0[i] + (size_t)j * dstride)[perm ? sp : k2];
             const bool swp = perm && sw;
             const u64 vx = swp ? v.y : v.x, vy = swp ? v.x : v.y;
-            s0x[i].mac(vx, kb.x);
-            s0y[i].mac(vy, kb.y);
-            s1x[i].mac(vx, ka.x);
-            s1y[i].mac(vy, ka.y);
+            s0x[i].mack(vx, kb.x, packed);
+            s0y[i].mack(vy, kb.y, packed);
+            s1x[i].mack(vx, ka.x, packed);
+            s1y[i].mack(vy, ka.y, packed);
         }
     }
     const Prime P = a.pr[px];
@@ -297,6 +311,7 @@ __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, i
     const int l1 = a.level + 1;
     const int px = x < l1 ? x : x + (a.L - a.level);
     const int own = x < l1 ? x / a.alpha : -1;
+    const bool packed = a.keys_packed && x < l1;
     const ulonglong2* ext0[IPT];
     const ulonglong2* ownr[IPT];
 #pragma unroll
@@ -331,10 +346,10 @@ __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, i
                     vx = sw ? v.y : v.x;
                     vy = sw ? v.x : v.y;
                 }
-                s0x[i].mac(vx, kb.x);
-                s0y[i].mac(vy, kb.y);
-                s1x[i].mac(vx, ka.x);
-                s1y[i].mac(vy, ka.y);
+                s0x[i].mack(vx, kb.x, packed);
+                s0y[i].mack(vy, kb.y, packed);
+                s1x[i].mack(vx, ka.x, packed);
+                s1y[i].mack(vy, ka.y, packed);
             }
         }
     }

@@ -36,7 +36,14 @@ struct InnerArgs {
     const u64* shared_key;    // plain: non-null when every item uses this key ...
     long long shared_galois;  // ... and this automorphism (then several items per thread may run)
     int split25;              // set by the launchers: data limbs use the split-at-bit-25 sums
+    int keys_packed;          // the keys' data-prime rows are stored split at bit 25 (key_unpack)
 };
+
+// A data-prime key residue stored split at bit 25 (every data prime below 2^50): the low 25 bits in
+// the low 32-bit word, the rest in the high word, so that the column-sum multiply-accumulate takes
+// the two halves without any unpacking. Every other use unpacks it.
+__host__ __device__ __forceinline__ u64 key_pack(u64 k) { return (k & ((1ull << 25) - 1)) | ((k >> 25) << 32); }
+__host__ __device__ __forceinline__ u64 key_unpack(u64 k) { return (k & 0xFFFFFFFFull) | ((k >> 32) << 25); }
 
 // Launch variants (the autotuner times them; all give identical bits).
 enum InnerVariant {

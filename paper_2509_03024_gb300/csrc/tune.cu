@@ -125,6 +125,7 @@ void tune_inner(Ctx& c, int level, std::vector<fhe_tune_result>& out) {
     ia.n_ext = c.n_ext;
     ia.log_n = c.log_n;
     ia.pr = c.d_primes;
+    ia.keys_packed = c.keys_packed;
     for (int f = 0; f < 2; f++) {
         const Family& fam = kFamilies[f];
         const bool hoist = f == 0;
