@@ -142,6 +142,7 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
                     r.src_cnt = cnt;
                     r.prime = px;
                     r.galois = 1;
+                    r.pack = c.keys_packed && x < l1;  // raised data limbs stored split at bit 25
                     r2.push_back(r);
                 }
             }

@@ -46,7 +46,9 @@ struct MacC {
         hi += ph + (lo < pl ? 1 : 0);
     }
     __device__ __forceinline__ u64 reduce(const Prime& P) const { return reduce128(lo, hi, P); }
-    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) { mac(a, packed ? key_unpack(k) : k); }
+    __device__ __forceinline__ void macx(u64 a, bool ap, u64 k, bool kp) {
+        mac(ap ? key_unpack(a) : a, kp ? key_unpack(k) : k);
+    }
 };
 
 struct MacP {  // PTX 64-bit multiply-add with carry (the one-item legacy form of the plain kernel)
@@ -55,7 +57,9 @@ struct MacP {  // PTX 64-bit multiply-add with carry (the one-item legacy form o
         asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
     }
     __device__ __forceinline__ u64 reduce(const Prime& P) const { return reduce128(lo, hi, P); }
-    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) { mac(a, packed ? key_unpack(k) : k); }
+    __device__ __forceinline__ void macx(u64 a, bool ap, u64 k, bool kp) {
+        mac(ap ? key_unpack(a) : a, kp ? key_unpack(k) : k);
+    }
 };
 
 // Schoolbook on 32-bit words in one carry chain per row: a0 b0 and a1 b1 first, then each cross
@@ -80,7 +84,9 @@ struct MacP32 {
     __device__ __forceinline__ u64 reduce(const Prime& P) const {
         return reduce128(((u64)r1 << 32) | r0, ((u64)r3 << 32) | r2, P);
     }
-    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) { mac(a, packed ? key_unpack(k) : k); }
+    __device__ __forceinline__ void macx(u64 a, bool ap, u64 k, bool kp) {
+        mac(ap ? key_unpack(a) : a, kp ? key_unpack(k) : k);
+    }
 };
 
 // Operands below 2^50 split at bit 25: a b = a0 b0 + 2^25 (a0 b1 + a1 b0) + 2^50 a1 b1 with every
@@ -100,11 +106,12 @@ struct MacS25 {
         const u32 m = (1u << 25) - 1u;
         mac4((u32)a & m, (u32)(a >> 25), (u32)b & m, (u32)(b >> 25));
     }
-    // a packed key (key_pack) already holds its two halves in its two words
-    __device__ __forceinline__ void mack(u64 a, u64 k, bool packed) {
+    // a packed operand (key_pack) already holds its two halves in its two words
+    __device__ __forceinline__ void macx(u64 a, bool ap, u64 k, bool kp) {
         const u32 m = (1u << 25) - 1u;
-        if (packed) mac4((u32)a & m, (u32)(a >> 25), (u32)k, (u32)(k >> 32));
-        else mac(a, k);
+        const u32 a0 = ap ? (u32)a : (u32)a & m, a1 = ap ? (u32)(a >> 32) : (u32)(a >> 25);
+        const u32 b0 = kp ? (u32)k : (u32)k & m, b1 = kp ? (u32)(k >> 32) : (u32)(k >> 25);
+        mac4(a0, a1, b0, b1);
     }
     __device__ __forceinline__ u64 reduce(const Prime& P) const {
         // C0 + 2^25 C1 + 2^50 C2 as (hi, lo)
@@ -145,6 +152,7 @@ __global__ void __launch_bounds__(256, 4) inner_v0_kernel(InnerArgs a) {
         MacP s0x, s0y, s1x, s1y;
         const int st = FANOUT ? a.src_of[t] : t;
         for (int j = 0; j < a.dn; j++) {
+            const bool vpk = packed && j != own;  // raised digits of data limbs are stored packed
             u64 vx, vy;
             const u64* src = j == own ? it.d + ((size_t)x << log_n)
                                       : a.ext + ((size_t)((st * a.dn + j) * a.next + x) << log_n);
@@ -157,10 +165,10 @@ __global__ void __launch_bounds__(256, 4) inner_v0_kernel(InnerArgs a) {
             }
             const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 0) * a.n_ext + px) << log_n))[k2];
             const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(it.key + ((size_t)((j * 2 + 1) * a.n_ext + px) << log_n))[k2];
-            s0x.mack(vx, kb.x, packed);
-            s0y.mack(vy, kb.y, packed);
-            s1x.mack(vx, ka.x, packed);
-            s1y.mack(vy, ka.y, packed);
+            s0x.macx(vx, vpk, kb.x, packed);
+            s0y.macx(vy, vpk, kb.y, packed);
+            s1x.macx(vx, vpk, ka.x, packed);
+            s1y.macx(vy, vpk, ka.y, packed);
         }
         reinterpret_cast<ulonglong2*>(a.acc + ((size_t)((t * 2 + 0) * a.next + x) << log_n))[k2] =
             make_ulonglong2(s0x.reduce(P), s0y.reduce(P));
@@ -194,14 +202,15 @@ __global__ void __launch_bounds__(256, 3) hoist_v0_kernel(InnerArgs a) {
             const bool sw = src & 1;
             const ulonglong2* kr = reinterpret_cast<const ulonglong2*>(st.key) + koff;
             for (int j = 0; j < a.dn; j++) {
+                const bool vpk = packed && j != own;  // raised digits of data limbs are stored packed
                 const ulonglong2 v = (j == own ? own_row : ext0 + (size_t)j * dstride)[sp];
                 const u64 vx = sw ? v.y : v.x, vy = sw ? v.x : v.y;
                 const ulonglong2 kb = kr[(size_t)(2 * j) * kstride];
                 const ulonglong2 ka = kr[(size_t)(2 * j + 1) * kstride];
-                s0x.mack(vx, kb.x, packed);
-                s0y.mack(vy, kb.y, packed);
-                s1x.mack(vx, ka.x, packed);
-                s1y.mack(vy, ka.y, packed);
+                s0x.macx(vx, vpk, kb.x, packed);
+                s0y.macx(vy, vpk, kb.y, packed);
+                s1x.macx(vx, vpk, ka.x, packed);
+                s1y.macx(vy, vpk, ka.y, packed);
             }
         }
         const Prime P = a.pr[px];
@@ -265,6 +274,7 @@ __device__ __forceinline__ void inner2_body(const InnerArgs& a, int x, int k2, i
     }
     MAC s0x[IPT], s0y[IPT], s1x[IPT], s1y[IPT];
     for (int j = 0; j < a.dn; j++) {
+        const bool vpk = packed && j != own;  // raised digits of data limbs are stored packed
         const ulonglong2 kb = kr[(size_t)(2 * j) * kstride];
         const ulonglong2 ka = kr[(size_t)(2 * j + 1) * kstride];
         // plain items read their raised digits unpermuted (the automorphism was applied in K1);
@@ -275,10 +285,10 @@ __device__ __forceinline__ void inner2_body(const InnerArgs& a, int x, int k2, i
             const ulonglong2 v = (j == own ? ownr[i] : ext0[i] + (size_t)j * dstride)[perm ? sp : k2];
             const bool swp = perm && sw;
             const u64 vx = swp ? v.y : v.x, vy = swp ? v.x : v.y;
-            s0x[i].mack(vx, kb.x, packed);
-            s0y[i].mack(vy, kb.y, packed);
-            s1x[i].mack(vx, ka.x, packed);
-            s1y[i].mack(vy, ka.y, packed);
+            s0x[i].macx(vx, vpk, kb.x, packed);
+            s0y[i].macx(vy, vpk, kb.y, packed);
+            s1x[i].macx(vx, vpk, ka.x, packed);
+            s1y[i].macx(vy, vpk, ka.y, packed);
         }
     }
     const Prime P = a.pr[px];
@@ -331,6 +341,7 @@ __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, i
         const bool sw = src & 1;
         const ulonglong2* kr = reinterpret_cast<const ulonglong2*>(st.key) + koff;
         for (int j = 0; j < a.dn; j++) {
+            const bool vpk = packed && j != own;  // raised digits of data limbs are stored packed
             const ulonglong2 kb = kr[(size_t)(2 * j) * kstride];
             const ulonglong2 ka = kr[(size_t)(2 * j + 1) * kstride];
 #pragma unroll
@@ -346,10 +357,10 @@ __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, i
                     vx = sw ? v.y : v.x;
                     vy = sw ? v.x : v.y;
                 }
-                s0x[i].mack(vx, kb.x, packed);
-                s0y[i].mack(vy, kb.y, packed);
-                s1x[i].mack(vx, ka.x, packed);
-                s1y[i].mack(vy, ka.y, packed);
+                s0x[i].macx(vx, vpk, kb.x, packed);
+                s0y[i].macx(vy, vpk, kb.y, packed);
+                s1x[i].macx(vx, vpk, ka.x, packed);
+                s1y[i].macx(vy, vpk, ka.y, packed);
             }
         }
     }

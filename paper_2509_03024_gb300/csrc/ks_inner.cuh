@@ -36,7 +36,9 @@ struct InnerArgs {
     const u64* shared_key;    // plain: non-null when every item uses this key ...
     long long shared_galois;  // ... and this automorphism (then several items per thread may run)
     int split25;              // set by the launchers: data limbs use the split-at-bit-25 sums
-    int keys_packed;          // the keys' data-prime rows are stored split at bit 25 (key_unpack)
+    int keys_packed;          // the keys' data-prime rows, and the raised digits' data limbs (ext rows
+                              // x <= level), are stored split at bit 25 (key_unpack); the own-digit
+                              // rows read from the input are not
 };
 
 // A data-prime key residue stored split at bit 25 (every data prime below 2^50): the low 25 bits in

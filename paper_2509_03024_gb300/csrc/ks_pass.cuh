@@ -25,7 +25,7 @@ struct KsRow {
     int src_cnt;     // LD_CONV: number of source limbs
     int cst_stride;  // LD_CONV: words between consecutive source limbs' constant pairs
     int item, half, limb;  // ST_COMBINE(_RS): output item, component and limb
-    int pad;
+    int pack;              // ST_LAST (forward): store the residue split at bit 25 (key_pack)
     const u64* src2;       // LD_AXPY / LD_MUL: second source row (LD_AXPY: null = none); ST_RESCALE: the input limb
     const u64* cst2;       // LD_AXPY: Shoup pair of its factor; ST_RESCALE: q_l^-1 mod the row's prime
     u64* out2;             // ST_RESCALE: output row
@@ -149,7 +149,8 @@ __device__ __forceinline__ void store_elem(const KsRow& r, size_t k, u64 v, cons
             u64 t = shoup_lazy(v, ninv[2 * r.prime], ninv[2 * r.prime + 1], q);
             r.dst[k] = t >= q ? t - q : t;
         } else {
-            r.dst[k] = nttc::reduce_any(v, q, one_s);
+            const u64 t = nttc::reduce_any(v, q, one_s);
+            r.dst[k] = r.pack ? key_pack(t) : t;
         }
         return;
     }
