@@ -204,6 +204,19 @@ int fhe_rotate(fhe_ctx* ctx, const uint64_t* ct, uint64_t* out, int32_t count, i
 int fhe_rotate_sum(fhe_ctx* ctx, uint64_t* ct, uint64_t* out, int32_t count, int32_t level, int32_t kp,
                    void* stream);
 
+/* Fan-in rotation: for every group g, acc_g += sum_{first[g] <= i < first[g+1]} rot(ct_i, steps[i]),
+ * the back-rotation of the item gradients onto a delta tree's parent node (the paper's gradient
+ * accumulator, Alg. 2, applied to the rotated node gradients). The children's key inner products
+ * and rotated c0's are summed before one ModDown per group, so the bits differ from adding
+ * fhe_rotate results (same plaintext; the noise of one key switch per group). acc: device,
+ * n_groups ciphertexts at `level`, updated in place; ct: device, first[n_groups] ciphertexts at
+ * `level`, none aliasing an acc; first: host, n_groups + 1 non-decreasing offsets from 0 to the
+ * input count; steps: host, one nonzero rotation step (not a multiple of the slot count) per
+ * input, each with its rotation key. Errors: FHE_ERR_INVALID_ARG for bad offsets or steps,
+ * FHE_ERR_MISSING_KEY for a step without a key. */
+int fhe_rotate_fanin(fhe_ctx* ctx, uint64_t* acc, int32_t n_groups, const int32_t* first, const uint64_t* ct,
+                     const int32_t* steps, int32_t level, void* stream);
+
 /* ------------------------------------------------------------------ launch accounting */
 
 /* Measurement helper (no counterpart in the paper): the rate, in 10^9 butterflies per second,
@@ -261,6 +274,23 @@ int fhe_autotune(fhe_ctx* ctx, int32_t level, fhe_tune_result* out, int32_t cap)
  * change. fhe_get_variant writes the current variant's name (a static string) to *variant. */
 int fhe_set_variant(fhe_ctx* ctx, const char* family, const char* variant);
 int fhe_get_variant(const fhe_ctx* ctx, const char* family, const char** variant);
+
+/* Measurement helper (no counterpart in the paper): what the base conversion costs inside the fused
+ * ModUp pass, the evidence for keeping it on the CUDA cores. Times, with CUDA events (best of 5,
+ * after a warm-up, on the default stream), the forward-transform pass set of the key switch's
+ * conversion step over `sources` synthetic inputs at `level` (every target limb x outside a digit
+ * loads sum_{i in digit} y_i qhat_i mod p_x while its tile is read; Bajard et al. 2016) and the
+ * same rows loading one limb with no conversion. conv_ms - plain_ms bounds what any other form of
+ * the conversion could save inside the pass; an unfused form (a separate matrix product) would
+ * add roundtrip_bytes of HBM traffic (a write and a re-read of every converted limb). Errors:
+ * FHE_ERR_INVALID_ARG for level outside 1..L, sources < 1 or a null output. */
+typedef struct {
+    double conv_ms;          /* pass set with the conversion in its loads */
+    double plain_ms;         /* same rows, one plain limb load each */
+    int32_t rows;            /* converted limbs (transform rows) per pass set */
+    double roundtrip_bytes;  /* 16 N bytes per row */
+} fhe_conv_cost;
+int fhe_probe_conv_cost(fhe_ctx* ctx, int32_t level, int32_t sources, fhe_conv_cost* out);
 
 /* Per kernel class: launches, summed device time (only when timing was
  * requested), the algorithmic bytes those launches must move (inputs read

@@ -643,6 +643,47 @@ class Ckks:
                     c1 = self._add(c1, part, pr)
         return Ciphertext(np.stack([c0, c1]), lv)
 
+    def rotate_fanin(self, cts: Sequence[Ciphertext], steps: Sequence[int]) -> Ciphertext:
+        """sum_i rot(cts[i], steps[i]) with one ModDown for the whole sum.
+
+        Every input keeps its own ModUp: phi_g of its c1 is raised (ModUp) and multiplied with the
+        rotation key of its step; the inner products of all inputs are summed in Q_l u P and a
+        single ModDown ends the sum, which the phi_g of every c0 joins:
+          out0 = sum_i phi_gi(c0_i) + ModDown(sum_i sum_j ModUp_j(phi_gi(c1_i)) * b_{gi,j}),
+          out1 = ModDown(sum_i sum_j ModUp_j(phi_gi(c1_i)) * a_{gi,j}).
+        ModDown is linear up to its conversion error, so this equals the sum of rotate() results
+        within the key-switch noise but is not bit-identical to it. All inputs share one level."""
+        prm = self.prm
+        lv = cts[0].level
+        if any(ct.level != lv for ct in cts) or len(cts) != len(steps):
+            raise ValueError("fan-in rotation: inputs at one level, one step each")
+        pr = prm.q[: lv + 1]
+        basis = pr + prm.p
+        rows = self._key_rows(lv)
+        dn = prm.dnum(lv)
+        c0 = np.zeros((lv + 1, prm.n), dtype=np.uint64)
+        terms, kb, ka = [], [], []
+        for ct, r in zip(cts, steps):
+            g = prm.galois(r)
+            if g == 1:
+                raise ValueError("fan-in rotation: a step that is a multiple of the slot count")
+            if g not in self.rot:
+                raise KeyError(f"missing rotation key for step {r}")
+            c0 = self._add(c0, np.stack([ring.automorphism(ct.c[0][i], g, q) for i, q in enumerate(pr)]), pr)
+            c1g = np.stack([ring.automorphism(ct.c[1][i], g, q) for i, q in enumerate(pr)])
+            ups = self._modup(c1g, lv)
+            key = self.rot[g]
+            for j in range(dn):
+                terms.append(ups[j])
+                kb.append(key.b[j][rows])
+                ka.append(key.a[j][rows])
+        T = np.ascontiguousarray(np.stack(terms).transpose(1, 0, 2))  # [|basis|, terms, N]
+        halves = []
+        for K in (kb, ka):
+            acc = ring.polydot_rows(T, np.ascontiguousarray(np.stack(K).transpose(1, 0, 2)), basis)
+            halves.append(self._moddown(acc, lv))
+        return Ciphertext(np.stack([self._add(c0, halves[0], pr), halves[1]]), lv)
+
     def mul_relin_rescale(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
         """Ciphertext product (Eq. 8) followed by the fused relinearise-rescale."""
         return self.relin_rescale(self.tensor(a, b))

@@ -450,10 +450,16 @@ class EncryptedMF:
             H: Dict[int, Ciphertext] = {}
             for d in p.closure[c]:
                 H[d] = he.relin_rescale(TV[(c, d)]) if (c, d) in TV else he.zero(out_lv)
-            for d in sorted(p.closure[c], key=lambda x: (tree_depth(x, p.baby), x), reverse=True):
-                if d:
-                    par, step = tree_parent(d, p.baby)
-                    H[par] = he.add(H[par], he.rotate(H[d], -step * p.w))
+            # back-rotation, deepest nodes first: every parent takes the sum of its children rotated
+            # back with one ModDown (the children of a node all lie one level deeper)
+            nodes = [d for d in p.closure[c] if d]
+            for dep in sorted({tree_depth(d, p.baby) for d in nodes}, reverse=True):
+                kids: Dict[int, List[int]] = {}
+                for d in sorted(x for x in nodes if tree_depth(x, p.baby) == dep):
+                    kids.setdefault(tree_parent(d, p.baby)[0], []).append(d)
+                for par, ds in kids.items():
+                    back = he.rotate_fanin([H[d] for d in ds], [-tree_parent(d, p.baby)[1] * p.w for d in ds])
+                    H[par] = he.add(H[par], back)
             acc = H[0]
             acc = he.add(acc, he.rotate(acc, -p.kp))
             reg = he.enc.encode(reg_slots(p.nnz_v, p, c, lr, lam))

@@ -29,7 +29,7 @@ EXPORTS = [
     "fhe_keygen_from_seed", "fhe_add_rotation_keys", "fhe_encode", "fhe_encrypt", "fhe_encrypt_coeffs",
     "fhe_decrypt", "fhe_refresh", "fhe_ntt_forward", "fhe_ntt_inverse", "fhe_ct_to_coeff", "fhe_add", "fhe_sub",
     "fhe_mul_plain", "fhe_mul_relin_rescale", "fhe_tensor", "fhe_relinearize", "fhe_rescale", "fhe_rescale_noalloc",
-    "fhe_rotate", "fhe_rotate_sum", "fhe_probe_butterfly_rate", "fhe_probe_int_pipe", "fhe_autotune", "fhe_set_variant", "fhe_get_variant", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_layout", "fhe_mf_plan_destroy",
+    "fhe_rotate", "fhe_rotate_sum", "fhe_rotate_fanin", "fhe_probe_butterfly_rate", "fhe_probe_int_pipe", "fhe_probe_conv_cost", "fhe_autotune", "fhe_set_variant", "fhe_get_variant", "fhe_profile_begin", "fhe_profile_end", "fhe_mf_rotation_steps", "fhe_csr_pack", "fhe_mf_layout", "fhe_mf_plan_destroy",
     "fhe_mf_plan_get_info", "fhe_mf_plan_get_groups", "fhe_mf_plan_get_bins", "fhe_mf_plan_set_chunk", "fhe_mf_plan_set_wave_budget", "fhe_mf_encrypt_factors",
     "fhe_mf_decrypt_factors", "fhe_mf_sgd_epoch", "fhe_predict", "fhe_serve_rotation_steps",
     "fhe_serve_create", "fhe_serve_destroy", "fhe_serve_slots", "fhe_serve_submit", "fhe_serve_tick",
@@ -66,6 +66,11 @@ class IntPipeRates(ctypes.Structure):
                 ("imad_wide_gops", ctypes.c_double), ("mac_c_gmacs", ctypes.c_double),
                 ("mac_ptx64_gmacs", ctypes.c_double), ("mac_ptx32_gmacs", ctypes.c_double),
                 ("mac_wide_gmacs", ctypes.c_double)]
+
+
+class ConvCost(ctypes.Structure):
+    _fields_ = [("conv_ms", ctypes.c_double), ("plain_ms", ctypes.c_double), ("rows", ctypes.c_int32),
+                ("roundtrip_bytes", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):
@@ -119,8 +124,10 @@ def lib() -> ctypes.CDLL:
             "fhe_rescale_noalloc": [vp, vp, vp, i32, vp],
             "fhe_rotate": [vp, vp, vp, i32, i32, i32, vp],
             "fhe_rotate_sum": [vp, vp, vp, i32, i32, i32, vp],
+            "fhe_rotate_fanin": [vp, vp, i32, vp, vp, vp, i32, vp],
             "fhe_probe_butterfly_rate": [vp, i32, vp],
             "fhe_probe_int_pipe": [vp, i32, ctypes.POINTER(IntPipeRates)],
+            "fhe_probe_conv_cost": [vp, i32, i32, ctypes.POINTER(ConvCost)],
             "fhe_autotune": [vp, i32, ctypes.POINTER(TuneResult), i32],
             "fhe_set_variant": [vp, ctypes.c_char_p, ctypes.c_char_p],
             "fhe_get_variant": [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_char_p)],
@@ -331,6 +338,13 @@ class Context:
         """out = sum_{r < kp} rot(ct, r) (hoisted for kp <= 16)."""
         self._check(lib().fhe_rotate_sum(self.h, _ptr(ct), _ptr(out), count, level, kp, _stream(stream)))
 
+    def rotate_fanin(self, acc, first, ct, steps, level: int, stream=None):
+        """acc_g += sum_{first[g] <= i < first[g+1]} rot(ct_i, steps[i]), one ModDown per group."""
+        fo = np.ascontiguousarray(first, dtype=np.int32)
+        st = np.ascontiguousarray(steps, dtype=np.int32)
+        self._check(lib().fhe_rotate_fanin(self.h, _ptr(acc), fo.size - 1, fo.ctypes.data, _ptr(ct) if st.size else None,
+                                           st.ctypes.data if st.size else None, level, _stream(stream)))
+
     def serve_rotation_steps(self, k: int):
         buf = np.zeros(256, dtype=np.int32)
         rc = lib().fhe_serve_rotation_steps(self.h, k, buf.ctypes.data, buf.size)
@@ -359,6 +373,13 @@ class Context:
         out = IntPipeRates()
         self._check(lib().fhe_probe_int_pipe(self.h, reps, ctypes.byref(out)))
         return {name: getattr(out, name) for name, _ in IntPipeRates._fields_}
+
+    def probe_conv_cost(self, level: int, sources: int = 64) -> dict:
+        """Device time of the ModUp conversion pass set with and without the base conversion in its
+        loads, the rows it transforms and the HBM bytes an unfused conversion would add."""
+        out = ConvCost()
+        self._check(lib().fhe_probe_conv_cost(self.h, level, sources, ctypes.byref(out)))
+        return {name: getattr(out, name) for name, _ in ConvCost._fields_}
 
     def autotune(self, level: int = None) -> list:
         """Time every launch variant of each tunable kernel family at `level` (default: one below the

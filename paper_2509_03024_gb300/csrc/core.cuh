@@ -406,6 +406,12 @@ void keyswitch_items(Ctx& c, const std::vector<KsItem>& it, int level, cudaStrea
 void rotate_fanout_items(Ctx& c, const std::vector<const u64*>& in, const std::vector<u64*>& out,
                          const std::vector<int>& steps, int level, cudaStream_t s);
 
+// Fan-in rotation: acc_g += sum_{first_g <= i < first_{g+1}} rot(in_i, step_i) with one ModDown
+// per group (the children's key inner products and rotated c0's are summed before it). No in_i
+// may alias an acc_g.
+void rotate_fanin_items(Ctx& c, const std::vector<u64*>& acc, const std::vector<int>& first,
+                        const std::vector<const u64*>& in, const std::vector<int>& steps, int level, cudaStream_t s);
+
 // Relinearise and rescale in one key switch (ModDown divides by P q_level): out_i (level - 1)
 // from the 3-component t3_i (level). out_i may equal t3_i.
 void relin_rescale_items(Ctx& c, const std::vector<u64*>& t3, const std::vector<u64*>& out, int level,

@@ -1399,6 +1399,38 @@ int fhe_rotate_sum(fhe_ctx* ctx, uint64_t* ct, uint64_t* out, int32_t count, int
     });
 }
 
+int fhe_rotate_fanin(fhe_ctx* ctx, uint64_t* acc, int32_t n_groups, const int32_t* first, const uint64_t* ct,
+                     const int32_t* steps, int32_t level, void* stream) {
+    return guarded(ctx, [&] {
+        Ctx& c = ctx->c;
+        check_level(c, level);
+        check_keys(c);
+        if (n_groups < 0) fail(FHE_ERR_INVALID_ARG, "negative group count");
+        if (n_groups == 0) return;
+        check_ptr(acc, "acc");
+        check_ptr(first, "first");
+        const int total = first[n_groups];
+        if (first[0] != 0 || total < 0) fail(FHE_ERR_INVALID_ARG, "fan-in offsets must run from 0 to the input count");
+        if (total > 0) {
+            check_ptr(ct, "ct");
+            check_ptr(steps, "steps");
+        }
+        c.arena.reset(S(stream));
+        const size_t w = c.ct_words();
+        std::vector<u64*> a;
+        std::vector<int> fo(first, first + n_groups + 1), st;
+        std::vector<const u64*> in;
+        for (int g = 0; g < n_groups; g++) a.push_back(acc + g * w);
+        for (int i = 0; i < total; i++) {
+            const u64* x = ct + i * w;
+            if (x < acc + (size_t)n_groups * w && acc < x + w) fail(FHE_ERR_INVALID_ARG, "fan-in input aliases an output");
+            in.push_back(x);
+            st.push_back(steps[i]);
+        }
+        rotate_fanin_items(c, a, fo, in, st, level, S(stream));
+    });
+}
+
 int fhe_profile_begin(fhe_ctx* ctx, int32_t time_kernels) {
     return guarded(ctx, [&] {
         check_ptr(ctx, "ctx");

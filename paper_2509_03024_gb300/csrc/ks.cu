@@ -60,15 +60,56 @@ namespace {
 // With fused_rescale (relinearisation items: galois 1, addI0/addI1 = c0/c1, no addP0), K4/K5
 // divide by P q_level instead of P and the outputs are at level - 1:
 //   out_h = (acc_h + P c_h - Conv_{P u {q_l} -> Q_{l-1}}(acc_h + P c_h)) (P q_l)^-1.
+// Fan-in mode (fi set): K1-K3 per item as for a rotation (d = c1, addP0 = c0, galois of the item);
+// instead of K4/K5 the items' accumulators are summed into their group's fi->gacc and their
+// permuted c0's into fi->gc0 (the first contribution to a group sets, later ones add), and
+// the caller runs one ModDown per group (moddown_run).
+struct FanIn {
+    const std::vector<int>* group;  // per item: group index, non-decreasing
+    u64* gacc;                      // [group][2][next][N]
+    u64* gc0;                       // [group][level + 1][N]
+    std::vector<char>* touched;     // per group: already holds a contribution
+};
+
+// One fan-in accumulation row: dst (+)= sum over its sources of src[perm(k)] mod the row's prime.
+struct FanRow {
+    u64* dst;
+    int first, cnt, prime, set;
+};
+struct FanSrc {
+    const u64* src;
+    int galois;
+};
+
+__global__ void fanin_sum_kernel(const FanRow* __restrict__ rows, const FanSrc* __restrict__ srcs, int n_rows,
+                                 int log_n, const Prime* __restrict__ pr) {
+    const size_t total = (size_t)n_rows << log_n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const FanRow r = rows[e >> log_n];
+        const int k = (int)(e & (((size_t)1 << log_n) - 1));
+        const u64 q = pr[r.prime].q;
+        u64 t = r.set ? 0 : r.dst[k];
+        for (int j = 0; j < r.cnt; j++) {
+            const FanSrc x = srcs[r.first + j];
+            t = add_mod(t, x.src[x.galois == 1 ? k : auto_src(k, x.galois, log_n)], q);
+        }
+        r.dst[k] = t;
+    }
+}
+
+void moddown_run(Ctx& c, const std::vector<KsItem>& it, const KsItem* d_items, const u64* acc, int level,
+                 cudaStream_t s);
+
 void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* hk, cudaStream_t s,
-            bool fused_rescale = false, const std::vector<int>* fanout_src = nullptr) {
+            bool fused_rescale = false, const std::vector<int>* fanout_src = nullptr, const FanIn* fi = nullptr) {
     if (all.empty()) return;
     const int n = c.n, L = c.L, A = c.alpha, l1 = level + 1, next = l1 + A, dn = c.dnum(level);
     const int SP = fused_rescale ? A + 1 : A;  // ModDown source limbs
     const bool fan = fanout_src != nullptr;
     // bound the work area to ~6 GiB per sub-batch (per source: y and the raised digits; per item the rest)
     const size_t per_src = (size_t)(l1 + dn * next) * n * sizeof(u64);
-    const size_t per_item = (size_t)(2 * next + 2 * SP + 2 * l1 + (hk ? l1 : 0)) * n * sizeof(u64);
+    const size_t per_item =
+        (size_t)(2 * next + (fi ? 0 : 2 * SP + 2 * l1) + (hk ? l1 : 0)) * n * sizeof(u64);
     const size_t budget = (size_t)6 << 30;
     for (size_t b0 = 0; b0 < all.size();) {
         // items [b0, b0 + items): a fan-out sub-batch ends where a new source would exceed the budget
@@ -103,8 +144,8 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
         u64* y = c.scratch_u64("ks_y", (size_t)n_sources * l1 * n);
         u64* ext = c.scratch_u64("ks_ext", (size_t)n_sources * dn * next * n);
         u64* acc = c.scratch_u64("ks_acc", (size_t)items * 2 * next * n);
-        u64* yP = c.scratch_u64("ks_yp", (size_t)items * 2 * SP * n);
-        u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
+        u64* yP = fi ? nullptr : c.scratch_u64("ks_yp", (size_t)items * 2 * SP * n);
+        u64* conv = fi ? nullptr : c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
         CombineArgs ca{d_items, acc, c.d_pinv, next, nullptr};
         const CombineArgs none{nullptr, nullptr, nullptr, 0, nullptr};
 
@@ -242,6 +283,52 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
             ks_transform<false, LD_CONV, ST_COMBINE_RS>(c, d_r5, (int)r5.size(), cr, K_NTT_FWD, 16.0 * r5.size() * n, s);
             continue;
         }
+        if (fi) {
+            // sum the sub-batch's accumulators and permuted c0's into their groups
+            std::vector<FanRow> fr;
+            std::vector<FanSrc> fs;
+            for (int t0 = 0; t0 < items;) {
+                const int g = (*fi->group)[b0 - items + t0];
+                int t1 = t0 + 1;
+                while (t1 < items && (*fi->group)[b0 - items + t1] == g) t1++;
+                const int set = (*fi->touched)[g] ? 0 : 1;
+                (*fi->touched)[g] = 1;
+                for (int h = 0; h < 2; h++)
+                    for (int x = 0; x < next; x++) {
+                        fr.push_back({fi->gacc + (((size_t)g * 2 + h) * next + x) * n, (int)fs.size(), t1 - t0,
+                                      x < l1 ? x : x + (L - level), set});
+                        for (int t = t0; t < t1; t++) fs.push_back({acc + (((size_t)t * 2 + h) * next + x) * n, 1});
+                    }
+                for (int i = 0; i < l1; i++) {
+                    fr.push_back({fi->gc0 + ((size_t)g * l1 + i) * n, (int)fs.size(), t1 - t0, i, set});
+                    for (int t = t0; t < t1; t++) fs.push_back({it[t].addP0 + (size_t)i * n, (int)it[t].galois});
+                }
+                t0 = t1;
+            }
+            const FanRow* d_fr = c.arena.push_vec(fr, s);
+            const FanSrc* d_fs = c.arena.push_vec(fs, s);
+            LaunchScope _ls(c.prof, K_ELEMENTWISE, 8.0 * n * (fs.size() + 2.0 * fr.size()), s);
+            const size_t total = fr.size() * (size_t)n;
+            fanin_sum_kernel<<<(unsigned)std::min<size_t>((total + 255) / 256, (size_t)152 * 16), 256, 0, s>>>(
+                d_fr, d_fs, (int)fr.size(), c.log_n, c.d_primes);
+            CK(cudaGetLastError());
+            continue;
+        }
+        moddown_run(c, it, ca.items, acc, level, s);
+    }
+}
+
+// K4/K5 of a plain key switch over the items' accumulators acc ([item][2][next][N]): out_h =
+// (acc_h - Conv_{P->Q}(acc_h)) P^-1 + the item's add terms.
+void moddown_run(Ctx& c, const std::vector<KsItem>& it, const KsItem* d_items, const u64* acc, int level,
+                 cudaStream_t s) {
+    const int n = c.n, L = c.L, A = c.alpha, l1 = level + 1, next = l1 + A;
+    const int items = (int)it.size();
+    u64* yP = c.scratch_u64("ks_yp", (size_t)items * 2 * A * n);
+    u64* conv = c.scratch_u64("ks_conv", (size_t)items * 2 * l1 * n);
+    const CombineArgs ca{d_items, acc, c.d_pinv, next, nullptr};
+    const CombineArgs none{nullptr, nullptr, nullptr, 0, nullptr};
+    {
         // K4: y_k = INTT(acc_h special limb k) * Phat_k^-1
         std::vector<KsRow> r4;
         for (int t = 0; t < items; t++)
@@ -390,6 +477,48 @@ void rotate_fanout_items(Ctx& c, const std::vector<const u64*>& in, const std::v
         src.push_back(k == 0 || in[i] != in[ord[k - 1]] ? (int)k : src.back());
     }
     ks_run(c, ks, level, nullptr, s, false, &src);
+}
+
+void rotate_fanin_items(Ctx& c, const std::vector<u64*>& acc, const std::vector<int>& first,
+                        const std::vector<const u64*>& in, const std::vector<int>& steps, int level, cudaStream_t s) {
+    if (first.size() != acc.size() + 1 || in.size() != steps.size() || first.back() != (int)in.size() ||
+        first.front() != 0)
+        fail(FHE_ERR_INVALID_ARG, "fan-in: group offsets do not cover the inputs");
+    const int n = c.n, l1 = level + 1, next = l1 + c.alpha;
+    const size_t lw = c.ct_words() / 2;
+    // groups with children, in chunks whose group accumulators stay within ~2 GiB
+    std::vector<int> gs;
+    for (size_t g = 0; g < acc.size(); g++) {
+        if (first[g + 1] < first[g]) fail(FHE_ERR_INVALID_ARG, "fan-in: group offsets decrease");
+        if (first[g + 1] > first[g]) gs.push_back((int)g);
+    }
+    const size_t per_group = (size_t)(2 * next + l1) * n * sizeof(u64);
+    const size_t chunk = std::max<size_t>(1, ((size_t)2 << 30) / per_group);
+    for (size_t c0 = 0; c0 < gs.size(); c0 += chunk) {
+        const int groups = (int)std::min(chunk, gs.size() - c0);
+        u64* gacc = c.scratch_u64("ks_gacc", (size_t)groups * 2 * next * n);
+        u64* gc0 = c.scratch_u64("ks_gc0", (size_t)groups * l1 * n);
+        std::vector<KsItem> ks;
+        std::vector<int> grp;
+        for (int g = 0; g < groups; g++)
+            for (int i = first[gs[c0 + g]]; i < first[gs[c0 + g] + 1]; i++) {
+                const int gal = (int)c.galois(steps[i]);
+                if (gal == 1) fail(FHE_ERR_INVALID_ARG, "fan-in rotation by a multiple of the slot count");
+                const EvalKey& key = rotation_key(c, steps[i]);
+                ks.push_back({in[i] + lw, key.d, in[i], nullptr, nullptr, nullptr, nullptr, gal});
+                grp.push_back(g);
+            }
+        std::vector<char> touched(groups, 0);
+        const FanIn fi{&grp, gacc, gc0, &touched};
+        ks_run(c, ks, level, nullptr, s, false, nullptr, &fi);
+        // one ModDown per group: acc_g + (gacc_g - Conv(gacc_g)) P^-1 + (gc0_g, 0)
+        std::vector<KsItem> gi;
+        for (int g = 0; g < groups; g++) {
+            u64* a = acc[gs[c0 + g]];
+            gi.push_back({nullptr, nullptr, gc0 + (size_t)g * l1 * n, a, a + lw, a, a + lw, 1});
+        }
+        moddown_run(c, gi, c.arena.push_vec(gi, s), gacc, level, s);
+    }
 }
 
 void relin_rescale_items(Ctx& c, const std::vector<u64*>& t3, const std::vector<u64*>& out, int level,

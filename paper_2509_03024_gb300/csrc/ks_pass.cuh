@@ -351,6 +351,7 @@ extern const char* const kKsTileNames[KS_N_TILES];
 #define KS_COMBOS(X)                      \
     X(true, LD_GATHER, ST_SCALE)          \
     X(false, LD_CONV, ST_LAST)            \
+    X(false, LD_GATHER, ST_LAST)          \
     X(true, LD_AXPY, ST_SCALE)            \
     X(false, LD_CONV, ST_COMBINE_RS)      \
     X(false, LD_CONV, ST_COMBINE)         \

@@ -232,7 +232,7 @@ void ensure_workspace(fhe_mf_plan& p) {
         if (p.chunk <= 0)
             p.chunk = (int)std::max<size_t>(1, std::min<size_t>(std::max<size_t>(p.groups.size(), 1),
                                                                 budget / per_group));
-        // the back-rotation and final steps reuse the chunk area
+        // the final steps reuse the chunk area
         const int need = (int)((p.n_ub + p.n_vb + 13) / 14) + 1;
         const int alloc_groups = std::max(p.chunk, need);
         p.d_chunk = plan_alloc<u64>(p, (size_t)alloc_groups * 14 * lw);
@@ -417,40 +417,29 @@ void run_epoch(fhe_mf_plan& p, u64* U, u64* V, int level, double lr, double lam,
             relin_rescale_items(c, t3, outs, l1, s);
         }
 
-        // 4. back-rotation of the item gradients along the delta trees (deepest first)
-        {
-            u64* rot_buf = p.d_chunk;  // reuse the chunk area
-            const int cap = (int)((size_t)p.chunk_alloc * 14 * lw / w);
-            for (int dep = maxdepth; dep >= 1; dep--) {
-                std::vector<int> lvl;
-                for (int nd = nd0; nd < nd1; nd++)
-                    if (tree_depth(p.node_delta[nd], baby) == dep) lvl.push_back(nd);
-                for (size_t o = 0; o < lvl.size(); o += cap) {
-                    size_t cnt = std::min(lvl.size() - o, (size_t)cap);
-                    std::vector<const u64*> in;
-                    std::vector<u64*> out;
-                    std::vector<int> steps;
-                    std::map<int, std::vector<int>> by_parent;
-                    for (size_t i = 0; i < cnt; i++) {
-                        int nd = lvl[o + i];
-                        int d = p.node_delta[nd];
-                        int step = 0;
-                        const int par = tree_parent(d, baby, &step);
-                        in.push_back(H(nd));
-                        out.push_back(rot_buf + i * w);
-                        steps.push_back(-step * p.w);
-                        by_parent[p.node(p.node_c[nd], par)].push_back((int)i);
-                    }
-                    rotate_items(c, in, out, steps, l2, false, s);
-                    std::vector<AccTarget> tg;
-                    std::vector<BinItem> cbi;
-                    for (auto& kv : by_parent) {
-                        tg.push_back({H(kv.first), (int)cbi.size(), (int)kv.second.size()});
-                        for (int i : kv.second) cbi.push_back({rot_buf + (size_t)i * w, nullptr, nullptr});
-                    }
-                    items_sum_acc(c, tg, cbi, 2, l2 + 1, s);
-                }
+        // 4. back-rotation of the item gradients along the delta trees (deepest first): every parent
+        //    takes the sum of its children rotated back, with one ModDown
+        for (int dep = maxdepth; dep >= 1; dep--) {
+            std::map<int, std::vector<std::pair<int, int>>> kids;  // parent node -> (child node, step)
+            for (int nd = nd0; nd < nd1; nd++) {
+                const int d = p.node_delta[nd];
+                if (tree_depth(d, baby) != dep) continue;
+                int step = 0;
+                const int par = tree_parent(d, baby, &step);
+                kids[p.node(p.node_c[nd], par)].push_back({nd, -step * p.w});
             }
+            std::vector<u64*> acc;
+            std::vector<int> first{0}, steps;
+            std::vector<const u64*> in;
+            for (auto& kv : kids) {
+                acc.push_back(H(kv.first));
+                for (auto& ch : kv.second) {
+                    in.push_back(H(ch.first));
+                    steps.push_back(ch.second);
+                }
+                first.push_back((int)in.size());
+            }
+            rotate_fanin_items(c, acc, first, in, steps, l2, s);
         }
 
         // 5. the wave's item batches: half-fill and apply (V_c is read only by its own wave)

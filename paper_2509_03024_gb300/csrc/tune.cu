@@ -287,3 +287,55 @@ extern "C" int fhe_get_variant(const fhe_ctx* ctx, const char* family, const cha
         }
     return FHE_ERR_INVALID_ARG;
 }
+
+extern "C" int fhe_probe_conv_cost(fhe_ctx* ctx, int32_t level, int32_t sources, fhe_conv_cost* out) {
+    if (!ctx) return FHE_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    return guarded(c, [&] {
+        if (level < 1 || level > c.L) fail(FHE_ERR_INVALID_ARG, "level out of range");
+        if (sources < 1 || !out) fail(FHE_ERR_INVALID_ARG, "need sources >= 1 and an output");
+        CK(cudaDeviceSynchronize());
+        const int n = c.n, L = c.L, A = c.alpha, l1 = level + 1, next = l1 + A, dn = c.dnum(level);
+        DevTmp tmp;
+        u64* y = tmp.get((size_t)sources * l1 * n);
+        u64* ext = tmp.get((size_t)sources * dn * next * n);
+        fill_residues<<<1024, 256>>>(y, (size_t)sources * l1 * n, c.log_n, 1, c.d_primes, 7);
+        CK(cudaGetLastError());
+        // the rows of the conversion step (K2 of the key switch), and the same rows with a plain load
+        std::vector<ksp::KsRow> rc, rp;
+        for (int t = 0; t < sources; t++)
+            for (int j = 0; j < dn; j++) {
+                const int lo = j * A, cnt = std::min(A, l1 - lo);
+                for (int x = 0; x < next; x++) {
+                    if (x >= lo && x < lo + cnt) continue;
+                    const int px = x < l1 ? x : x + (L - level);
+                    ksp::KsRow r{};
+                    r.dst = ext + (((size_t)t * dn + j) * next + x) * n;
+                    r.src = y + ((size_t)t * l1 + lo) * n;
+                    r.cst = c.d_up_hat + 2 * (((size_t)level * (L + 1) + lo) * c.n_ext + px);
+                    r.cst_stride = 2 * c.n_ext;
+                    r.src_cnt = cnt;
+                    r.prime = px;
+                    r.galois = 1;
+                    r.pack = c.keys_packed && x < l1;
+                    rc.push_back(r);
+                    r.src_cnt = 1;
+                    rp.push_back(r);
+                }
+            }
+        const int rows = (int)rc.size();
+        const ksp::KsRow* d_rc = c.arena.push_vec(rc, (cudaStream_t)0);
+        const ksp::KsRow* d_rp = c.arena.push_vec(rp, (cudaStream_t)0);
+        const ksp::CombineArgs none{nullptr, nullptr, nullptr, 0, nullptr};
+        const double bytes = 16.0 * rows * n;
+        out->conv_ms = time_ms(
+            [&] { ksp::ks_transform<false, ksp::LD_CONV, ksp::ST_LAST>(c, d_rc, rows, none, K_NTT_FWD, bytes, 0); }, 5);
+        out->plain_ms = time_ms(
+            [&] { ksp::ks_transform<false, ksp::LD_GATHER, ksp::ST_LAST>(c, d_rp, rows, none, K_NTT_FWD, bytes, 0); },
+            5);
+        out->rows = rows;
+        out->roundtrip_bytes = bytes;
+        CK(cudaDeviceSynchronize());
+        c.arena.reset((cudaStream_t)0);
+    });
+}

@@ -5,6 +5,7 @@
   python -m paper_2509_03024_gb300.kernel_driver rotsum --preset paper --count 64 --kp 16 [--reps 3]
   python -m paper_2509_03024_gb300.kernel_driver probe --preset paper [--reps 2000]
   python -m paper_2509_03024_gb300.kernel_driver tune --preset paper [--level L]
+  python -m paper_2509_03024_gb300.kernel_driver convcost --preset paper [--level L] [--count 64]
   (any kind) --variants family=variant,...   sets autotuner families, e.g. ntt=r8b4,ks_pass=r8
 
 `ntt` transforms `rows` limbs of N residues in place (rows / (L+1) polynomials
@@ -15,7 +16,8 @@ product in an epoch). Prints CUDA-event timings per repetition and, for the last
 repetition, the device time of each kernel class; `probe` prints the register-only
 butterfly rate of fhe_probe_butterfly_rate (`reps` loop trips) and the integer-pipe rates of
 fhe_probe_int_pipe; `tune` runs the autotuner at `level` (default top - 1) and prints every
-variant's time.
+variant's time; `convcost` times the ModUp conversion pass set over `count` sources with and
+without the base conversion in its loads (fhe_probe_conv_cost, at `level`, default the top).
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ def main():
     from paper_2509_03024_gb300.workloads import PRESETS
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("kind", choices=["ntt", "keyswitch", "rotsum", "probe", "tune"])
+    ap.add_argument("kind", choices=["ntt", "keyswitch", "rotsum", "probe", "tune", "convcost"])
     ap.add_argument("--level", type=int, default=None)
     ap.add_argument("--variant", default=None, help="inner-product variant to use (ks_inner and ks_hoist_inner)")
     ap.add_argument("--variants", default="", help="family=variant,... of the autotuner families to set")
@@ -51,6 +53,11 @@ def main():
         return
     if args.kind == "tune":
         print(json.dumps({"kind": "tune", "preset": args.preset, "results": ctx.autotune(args.level)}))
+        return
+    if args.kind == "convcost":
+        lv = ctx.top if args.level is None else args.level
+        print(json.dumps({"kind": "convcost", "preset": args.preset, "level": lv, "sources": args.count,
+                          **ctx.probe_conv_cost(lv, args.count)}))
         return
     if args.variant:
         ctx.set_variant("ks_inner", args.variant)

@@ -187,6 +187,34 @@ def test_rotate_sum_bit_exact(preset, kp, level_off):
         assert (to_coeff(ctx, keep, level, 2) == got).all()
 
 
+@pytest.mark.parametrize("preset,level_off", [("t10", 0), ("t11a2", 1)])
+def test_rotate_fanin_bit_exact(preset, level_off):
+    """acc_g += sum_i rot(ct_i, s_i) with one ModDown per group; groups of 3, 1, 0 and 4 children."""
+    steps = [1, -3, 5, 2, -1, 7, 1, -3]
+    first = [0, 3, 4, 4, 8]
+    keys = sorted(set(steps))
+    ctx = gpu_ctx(preset, SEED, keys)
+    he = oracle_ctx(preset, SEED, keys)
+    level = ctx.top - level_off
+    G, C = len(first) - 1, len(steps)
+    xs = [_slots(ctx.slots, 70 + i) for i in range(G + C)]
+    acc, ch = ctx.empty_ct(G), ctx.empty_ct(C)
+    for i, x in enumerate(xs):
+        ctx.encrypt(x, ctx.top, 300 + i, ct_slice(ctx, acc, i) if i < G else ct_slice(ctx, ch, i - G))
+    o = [he.drop(he.encrypt(x, he.prm.top, 300 + i), level) for i, x in enumerate(xs)]
+    ctx.rotate_fanin(acc, first, ch, steps, level)
+    got = to_coeff(ctx, acc, level, G)
+    for g in range(G):
+        kids = range(first[g], first[g + 1])
+        want = o[g]
+        if len(kids):
+            want = he.add(want, he.rotate_fanin([o[G + i] for i in kids], [steps[i] for i in kids]))
+        assert_ct_equal(got[g], want, f"fan-in group {g}")
+        dec = ctx.decrypt(ct_slice(ctx, acc, g), level)
+        ref = xs[g] + sum((np.roll(xs[G + i], -steps[i]) for i in kids), np.zeros(ctx.slots))
+        assert np.abs(dec - ref).max() < 1e-4
+
+
 def test_errors_are_reported_and_context_survives():
     ctx = gpu_ctx("t10", SEED, [1])
     from paper_2509_03024_gb300.capi import FheError

@@ -130,3 +130,19 @@ def test_ks_pass_tile_shapes_bit_identical(preset):
             ref = got
         for name, x, y in zip(("rotate", "mul_relin_rescale", "rescale"), got, ref):
             assert torch.equal(x, y), f"{preset}: tile shape {v} changes {name}"
+
+
+def test_conv_cost_probe():
+    """The conversion-cost probe times both pass sets over the key switch's conversion rows."""
+    ctx = gpu_ctx("t11a2", 27)
+    lv = ctx.top
+    r = ctx.probe_conv_cost(lv, 4)
+    l1, a = lv + 1, ctx.alpha
+    dn = -(-l1 // a)
+    want_rows = 4 * sum(l1 + a - min(a, l1 - j * a) for j in range(dn))
+    assert r["rows"] == want_rows and r["roundtrip_bytes"] == 16.0 * want_rows * ctx.n
+    assert r["conv_ms"] > 0 and r["plain_ms"] > 0
+    with pytest.raises(capi.FheError, match="INVALID_ARG"):
+        ctx.probe_conv_cost(0, 4)
+    with pytest.raises(capi.FheError, match="INVALID_ARG"):
+        ctx.probe_conv_cost(lv, 0)

@@ -392,3 +392,29 @@ def test_mul_plain_multiplies_the_integer_plaintext():
     p[[0, 3, prm.n - 1]] = [1000, -7, 1 << 20]
     got = _centred_plaintext(he, he.mul_plain(ct, p))
     assert got == _int_negacyclic(p.tolist(), _centred_plaintext(he, ct))
+
+
+def test_rotate_fanin_is_the_sum_of_rotations_plus_small_noise():
+    """decrypt(rotate_fanin(cts, steps)) = sum_i phi_(5^r_i)(decrypt(cts[i])) in Z[X]/(X^N+1) up to the
+    key-switch noise, and the slots are the sum of the rotated slot vectors; one input reduces to one
+    rotation (same plaintext), and the order of the inputs does not change the bits."""
+    prm = ckks.Params(8, (50, 40, 40), (60,), 40)
+    he = ckks.Ckks(prm)
+    steps = [3, -5, 7]
+    he.keygen(21, steps)
+    rng = np.random.default_rng(22)
+    zs = [rng.normal(0, 1, prm.slots) for _ in steps]
+    cts = [he.encrypt(z, prm.top, 40 + i) for i, z in enumerate(zs)]
+    out = he.rotate_fanin(cts, steps)
+    want = sum(np.roll(z, -r) for z, r in zip(zs, steps))
+    assert np.abs(he.decrypt(out) - want).max() < 1e-6
+    seq = he.add(he.add(he.rotate(cts[0], 3), he.rotate(cts[1], -5)), he.rotate(cts[2], 7))
+    d_out = he.decrypt_coeffs(out)
+    d_seq = he.decrypt_coeffs(seq)
+    assert max(abs(a - b) for a, b in zip(d_out, d_seq)) < 2 ** 20          # noise, far below Delta = 2^40
+    assert (out.c != seq.c).any()                                           # one ModDown, other bits
+    perm = he.rotate_fanin([cts[2], cts[0], cts[1]], [7, 3, -5])
+    assert (perm.c == out.c).all()
+    one = he.rotate_fanin([cts[1]], [-5])
+    assert (one.c == he.rotate(cts[1], -5).c).all()                         # one input: the plain key switch
+    assert np.abs(he.decrypt(one) - np.roll(zs[1], 5)).max() < 1e-6
