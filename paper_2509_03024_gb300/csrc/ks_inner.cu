@@ -243,13 +243,13 @@ __global__ void __launch_bounds__(256, 3) hoist_v0_kernel(InnerArgs a) {
 // Plain / fan-out: every item of a thread uses the key `key` and the automorphism `g` (IPT > 1 only
 // when the items share them); FANOUT reads item t's digits from source src_of[t] through its
 // automorphism.
-template <class MAC, int IPT, bool FANOUT>
+template <class MAC, int IPT, bool FANOUT, bool PK>
 __device__ __forceinline__ void inner2_body(const InnerArgs& a, int x, int k2, int t0) {
     const int log_n = a.log_n, hl = log_n - 1;
     const int l1 = a.level + 1;
     const int px = x < l1 ? x : x + (a.L - a.level);
     const int own = x < l1 ? x / a.alpha : -1;
-    const bool packed = a.keys_packed && x < l1;
+    constexpr bool packed = PK;  // keys_packed && x < l1, fixed per block
     const u64* key = IPT > 1 ? a.shared_key : a.tab[t0].key;
     const int g = IPT > 1 ? (int)a.shared_galois : (int)a.tab[t0].galois;
     const ulonglong2* kr = reinterpret_cast<const ulonglong2*>(key) + ((size_t)px << hl) + k2;
@@ -311,17 +311,24 @@ __global__ void __launch_bounds__(256) inner2_kernel(InnerArgs a) {
     const int k2 = (int)(e & ((1u << hl) - 1u));
     const int t0 = (int)(e >> hl) * IPT;
     if (t0 >= a.items) return;
-    if (x <= a.level && a.split25) inner2_body<MACD, IPT, FANOUT>(a, x, k2, t0);
-    else inner2_body<MACS, IPT, FANOUT>(a, x, k2, t0);
+    const bool pk = a.keys_packed && x <= a.level;  // uniform per block
+    if (x <= a.level && a.split25) {
+        if (pk) inner2_body<MACD, IPT, FANOUT, true>(a, x, k2, t0);
+        else inner2_body<MACD, IPT, FANOUT, false>(a, x, k2, t0);
+    } else if (pk) {
+        inner2_body<MACS, IPT, FANOUT, true>(a, x, k2, t0);
+    } else {
+        inner2_body<MACS, IPT, FANOUT, false>(a, x, k2, t0);
+    }
 }
 
-template <class MAC, int IPT, bool SCALAR = false>
+template <class MAC, int IPT, bool SCALAR, bool PK>
 __device__ __forceinline__ void hoist2_body(const InnerArgs& a, int x, int k2, int t0) {
     const int log_n = a.log_n, hl = log_n - 1;
     const int l1 = a.level + 1;
     const int px = x < l1 ? x : x + (a.L - a.level);
     const int own = x < l1 ? x / a.alpha : -1;
-    const bool packed = a.keys_packed && x < l1;
+    constexpr bool packed = PK;  // keys_packed && x < l1, fixed per block
     const ulonglong2* ext0[IPT];
     const ulonglong2* ownr[IPT];
 #pragma unroll
@@ -396,8 +403,15 @@ __global__ void __launch_bounds__(256) hoist2_kernel(InnerArgs a) {
     const int k2 = (int)(e & ((1u << hl) - 1u));
     const int t0 = (int)(e >> hl) * IPT;
     if (t0 >= a.items) return;
-    if (x <= a.level && a.split25) hoist2_body<MACD, IPT, SCALAR>(a, x, k2, t0);
-    else hoist2_body<MACS, IPT, SCALAR>(a, x, k2, t0);
+    const bool pk = a.keys_packed && x <= a.level;  // uniform per block
+    if (x <= a.level && a.split25) {
+        if (pk) hoist2_body<MACD, IPT, SCALAR, true>(a, x, k2, t0);
+        else hoist2_body<MACD, IPT, SCALAR, false>(a, x, k2, t0);
+    } else if (pk) {
+        hoist2_body<MACS, IPT, SCALAR, true>(a, x, k2, t0);
+    } else {
+        hoist2_body<MACS, IPT, SCALAR, false>(a, x, k2, t0);
+    }
 }
 
 inline unsigned grid1(size_t work) {
