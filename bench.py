@@ -46,13 +46,13 @@ sys.path.insert(0, HERE)
 
 METRIC = "encrypted MF ratings/sec, served vs one-by-one on 1 GB300; p50/p99 latency"
 # DRAM bytes per limb row of a forward NTT pass at N = 2^15, from the ncu capture (dram__bytes_read
-# + write) of the fused ModUp passes of the current kernels (64 rotations at level 7, 2048 rows per
-# pass): (615 MB + 1020 MB) / 2 passes / 2048 rows
-NCU_FWD_DRAM_BYTES_PER_ROW = (615.0e6 + 1020.0e6) / 2 / 2048
+# + write) of the fused ModUp passes of the current kernels (the hoisted rotate-and-sum of 64
+# ciphertexts at level 6, 1856 rows per pass): (552.8 MB + 917.4 MB) / 2 passes / 1856 rows
+NCU_FWD_DRAM_BYTES_PER_ROW = (552.8e6 + 917.4e6) / 2 / 1856
 # the same for the served ring's forward passes (N = 2^16, 13 + 3 primes): ncu dram__bytes_read + write
 # of the four forward passes (ModUp conversion and second pass, ModDown conversion and combine) of a
-# key switch of 8 top-level ciphertexts, 1239 MB over 1488 limb-row passes (0.79 x the algorithmic 16 N)
-NCU_SERVED_FWD_DRAM_BYTES_PER_ROW = 1239.0e6 / 1488
+# key switch of 8 top-level ciphertexts, 1240 MB over 1488 limb-row passes (0.79 x the algorithmic 16 N)
+NCU_SERVED_FWD_DRAM_BYTES_PER_ROW = 1239.7e6 / 1488
 UNIT = "ratings/s"
 SEED = 20250903
 LR, LAM, K_RANK = 0.005, 0.02, 10
