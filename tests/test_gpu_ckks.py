@@ -215,6 +215,27 @@ def test_rotate_fanin_bit_exact(preset, level_off):
         assert np.abs(dec - ref).max() < 1e-4
 
 
+def test_rotate_fanin_group_across_sub_batches():
+    """A group whose children span two key-switch sub-batches (about 54 children of a top-level
+    N = 2^16, 20 + 3 prime ciphertext fit the 6 GiB work area): the second sub-batch adds to the
+    first one's group sums. Checked by decryption against the sum of rotated slot vectors."""
+    steps_set = [1, 2, 3, -1, 5, 7, -4, 9]
+    ctx = gpu_ctx("large", SEED, steps_set)
+    level = ctx.top
+    first = [0, 70, 73]
+    steps = [steps_set[i % len(steps_set)] for i in range(first[-1])]
+    G, C = len(first) - 1, first[-1]
+    xs = [_slots(ctx.slots, 500 + i) for i in range(G + C)]
+    acc, ch = ctx.empty_ct(G), ctx.empty_ct(C)
+    for i, x in enumerate(xs):
+        ctx.encrypt(x, level, 900 + i, ct_slice(ctx, acc, i) if i < G else ct_slice(ctx, ch, i - G))
+    ctx.rotate_fanin(acc, first, ch, steps, level)
+    for g in range(G):
+        ref = xs[g] + sum(np.roll(xs[G + i], -steps[i]) for i in range(first[g], first[g + 1]))
+        dec = ctx.decrypt(ct_slice(ctx, acc, g), level)
+        assert np.abs(dec - ref).max() < 1e-4, f"group {g}"
+
+
 def test_errors_are_reported_and_context_survives():
     ctx = gpu_ctx("t10", SEED, [1])
     from paper_2509_03024_gb300.capi import FheError
