@@ -309,8 +309,7 @@ void ks_run(Ctx& c, const std::vector<KsItem>& all, int level, const HoistKeys* 
             const FanSrc* d_fs = c.arena.push_vec(fs, s);
             LaunchScope _ls(c.prof, K_ELEMENTWISE, 8.0 * n * (fs.size() + 2.0 * fr.size()), s);
             const size_t total = fr.size() * (size_t)n;
-            fanin_sum_kernel<<<(unsigned)std::min<size_t>((total + 255) / 256, (size_t)152 * 16), 256, 0, s>>>(
-                d_fr, d_fs, (int)fr.size(), c.log_n, c.d_primes);
+            fanin_sum_kernel<<<grid1(total), 256, 0, s>>>(d_fr, d_fs, (int)fr.size(), c.log_n, c.d_primes);
             CK(cudaGetLastError());
             continue;
         }
