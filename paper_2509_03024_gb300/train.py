@@ -111,6 +111,8 @@ def cli():
     ap.add_argument("--preset", default=None, help="CKKS parameter preset (default: the workload's)")
     ap.add_argument("--checkpoint", default=None, help="write the encrypted state here after every epoch")
     ap.add_argument("--resume", default=None, help="continue from a checkpoint written by --checkpoint")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the first launch variant of each kernel family instead of timing them first")
     args = ap.parse_args()
     build.build()
     if args.workload == "tiny":
@@ -125,6 +127,9 @@ def cli():
         preset = W.PRESETS[args.preset]
     ctx = capi.Context.from_preset(preset)
     ctx.keygen(args.seed, ctx.mf_rotation_steps(k))
+    tuned = {}
+    if not args.no_autotune:  # every variant gives the same bits; the fastest is kept for this context
+        tuned = {r["family"]: r["variant"] for r in ctx.autotune() if r["chosen"]}
     plan = capi.MfPlan(ctx, train.n, train.m, k, train.row_ptr, train.col_idx, train.vals)
     rows, cols, vals = train.triples()
     trow, tcol, tval = test.triples()
@@ -162,7 +167,7 @@ def cli():
     epoch_s = [c for c in times] if times else None
     out = {"workload": args.workload, "preset": preset.name, "log_scale": preset.log_scale, "epochs": args.epochs,
            "lr": lr, "lambda": args.lam, "damped": args.damped,
-           "refreshes": refreshes, "epoch_s": epoch_s, "diverged": diverged, "curve": curve}
+           "refreshes": refreshes, "epoch_s": epoch_s, "diverged": diverged, "tuning": tuned, "curve": curve}
     if times:
         out["ratings_per_s"] = float(rows.size * len(times) / sum(times))
     print(json.dumps(out))
