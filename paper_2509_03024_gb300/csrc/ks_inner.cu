@@ -102,11 +102,8 @@ struct MacS25 {
             : "+l"(C0), "+l"(C1), "+l"(C2)
             : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
     }
-    __device__ __forceinline__ void mac(u64 a, u64 b) {
-        const u32 m = (1u << 25) - 1u;
-        mac4((u32)a & m, (u32)(a >> 25), (u32)b & m, (u32)(b >> 25));
-    }
-    // a packed operand (key_pack) already holds its two halves in its two words
+    // an unpacked operand is split with a mask and a shift; a packed one (key_pack) already holds
+    // its two halves in its two words
     __device__ __forceinline__ void macx(u64 a, bool ap, u64 k, bool kp) {
         const u32 m = (1u << 25) - 1u;
         const u32 a0 = ap ? (u32)a : (u32)a & m, a1 = ap ? (u32)(a >> 32) : (u32)(a >> 25);

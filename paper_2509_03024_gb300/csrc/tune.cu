@@ -32,7 +32,6 @@ const Family kFamilies[] = {
     {"ntt", ntt_tile::NTT_N_TILES, ntt_tile::kNttTileNames, &Ctx::Tune::ntt},
     {"ks_pass", ksp::KS_N_TILES, ksp::kKsTileNames, &Ctx::Tune::ks},
 };
-constexpr int kNumFamilies = sizeof(kFamilies) / sizeof(kFamilies[0]);
 
 __global__ void fill_residues(u64* p, size_t words, int log_n, int n_limbs, const Prime* __restrict__ pr, u64 seed) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < words; e += (size_t)gridDim.x * blockDim.x) {
