@@ -68,6 +68,35 @@ class IntPipeRates(ctypes.Structure):
                 ("mac_wide_gmacs", ctypes.c_double)]
 
 
+def tune_cache_key(device_name: str, n: int, primes: Sequence[int], level: int) -> str:
+    """Key of a stored autotuner choice: the GPU model, and the ring and level it was timed on."""
+    return f"{device_name}|N={n}|q={','.join(str(int(p)) for p in primes)}|level={level}"
+
+
+def load_tune_cache(path: str) -> dict:
+    """The stored choices ({key: {family: variant}}); empty when the file is absent."""
+    import json
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except FileNotFoundError:
+        return {}
+    if not isinstance(data, dict):
+        raise ValueError(f"{path}: not an autotuner cache")
+    return data
+
+
+def store_tune_cache(path: str, key: str, choices: dict) -> None:
+    """Adds or replaces one key's choices; the file is replaced atomically."""
+    import json
+    data = load_tune_cache(path)
+    data[key] = dict(choices)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class ConvCost(ctypes.Structure):
     _fields_ = [("conv_ms", ctypes.c_double), ("plain_ms", ctypes.c_double), ("rows", ctypes.c_int32),
                 ("roundtrip_bytes", ctypes.c_double)]
@@ -381,17 +410,32 @@ class Context:
         self._check(lib().fhe_probe_conv_cost(self.h, level, sources, ctypes.byref(out)))
         return {name: getattr(out, name) for name, _ in ConvCost._fields_}
 
-    def autotune(self, level: int = None) -> list:
+    def autotune(self, level: int = None, cache: Optional[str] = None) -> list:
         """Time every launch variant of each tunable kernel family at `level` (default: one below the
         top, the level of an epoch's per-group products) and keep the fastest. Returns
-        [{family, variant, chosen, ms}]."""
+        [{family, variant, chosen, ms}]. With `cache` (a JSON file path), choices are stored under the
+        GPU model and the ring (degree, primes, level), and a later call that finds its key sets the
+        stored choices without timing (records then carry ms None and cached True)."""
         level = self.top - 1 if level is None else level
+        key = None
+        if cache:
+            import torch
+            key = tune_cache_key(torch.cuda.get_device_name(self.device), self.n, self.primes, level)
+            hit = load_tune_cache(cache).get(key)
+            if hit:
+                for fam, var in hit.items():
+                    self.set_variant(fam, var)
+                return [{"family": f, "variant": v, "chosen": True, "ms": None, "cached": True}
+                        for f, v in hit.items()]
         arr = (TuneResult * 64)()
         n = lib().fhe_autotune(self.h, level, arr, 64)
         if n < 0:
             self._check(n)
-        return [{"family": r.family.decode(), "variant": r.variant.decode(), "chosen": bool(r.chosen),
-                 "ms": r.ms} for r in arr[:min(n, 64)]]
+        res = [{"family": r.family.decode(), "variant": r.variant.decode(), "chosen": bool(r.chosen),
+                "ms": r.ms} for r in arr[:min(n, 64)]]
+        if key:
+            store_tune_cache(cache, key, {r["family"]: r["variant"] for r in res if r["chosen"]})
+        return res
 
     def set_variant(self, family: str, variant: str):
         self._check(lib().fhe_set_variant(self.h, family.encode(), variant.encode()))

@@ -113,6 +113,8 @@ def cli():
     ap.add_argument("--resume", default=None, help="continue from a checkpoint written by --checkpoint")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the first launch variant of each kernel family instead of timing them first")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuner choices per GPU model and ring (read, and written on a miss)")
     args = ap.parse_args()
     build.build()
     if args.workload == "tiny":
@@ -129,7 +131,7 @@ def cli():
     ctx.keygen(args.seed, ctx.mf_rotation_steps(k))
     tuned = {}
     if not args.no_autotune:  # every variant gives the same bits; the fastest is kept for this context
-        tuned = {r["family"]: r["variant"] for r in ctx.autotune() if r["chosen"]}
+        tuned = {r["family"]: r["variant"] for r in ctx.autotune(cache=args.tune_cache) if r["chosen"]}
     plan = capi.MfPlan(ctx, train.n, train.m, k, train.row_ptr, train.col_idx, train.vals)
     rows, cols, vals = train.triples()
     trow, tcol, tval = test.triples()

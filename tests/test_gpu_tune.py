@@ -78,6 +78,18 @@ def test_autotune_keeps_one_variant_per_family():
         ctx.set_variant("ks_inner", "nope")
 
 
+def test_autotune_cache_sets_stored_choices(tmp_path):
+    path = str(tmp_path / "tune.json")
+    ctx = gpu_ctx("t11a2", 24)
+    first = {r["family"]: r["variant"] for r in ctx.autotune(cache=path) if r["chosen"]}
+    other = gpu_ctx("t11a2", 25)                              # a fresh context on the same ring
+    hit = other.autotune(cache=path)
+    assert all(r.get("cached") for r in hit)
+    assert {r["family"]: r["variant"] for r in hit} == first
+    for f, v in first.items():
+        assert other.get_variant(f) == v
+
+
 @pytest.mark.parametrize("preset", ["paper", "t16a3"])
 def test_ntt_tile_shapes_bit_identical(preset):
     """Every tile shape of the two-pass NTT gives the same transform (N = 2^15 and 2^16)."""
