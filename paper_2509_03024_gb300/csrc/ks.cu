@@ -493,14 +493,14 @@ void rotate_fanin_items(Ctx& c, const std::vector<u64*>& acc, const std::vector<
     }
     const size_t per_group = (size_t)(2 * next + l1) * n * sizeof(u64);
     const size_t chunk = std::max<size_t>(1, ((size_t)2 << 30) / per_group);
-    for (size_t c0 = 0; c0 < gs.size(); c0 += chunk) {
-        const int groups = (int)std::min(chunk, gs.size() - c0);
+    for (size_t g0 = 0; g0 < gs.size(); g0 += chunk) {
+        const int groups = (int)std::min(chunk, gs.size() - g0);
         u64* gacc = c.scratch_u64("ks_gacc", (size_t)groups * 2 * next * n);
         u64* gc0 = c.scratch_u64("ks_gc0", (size_t)groups * l1 * n);
         std::vector<KsItem> ks;
         std::vector<int> grp;
         for (int g = 0; g < groups; g++)
-            for (int i = first[gs[c0 + g]]; i < first[gs[c0 + g] + 1]; i++) {
+            for (int i = first[gs[g0 + g]]; i < first[gs[g0 + g] + 1]; i++) {
                 const int gal = (int)c.galois(steps[i]);
                 if (gal == 1) fail(FHE_ERR_INVALID_ARG, "fan-in rotation by a multiple of the slot count");
                 const EvalKey& key = rotation_key(c, steps[i]);
@@ -513,7 +513,7 @@ void rotate_fanin_items(Ctx& c, const std::vector<u64*>& acc, const std::vector<
         // one ModDown per group: acc_g + (gacc_g - Conv(gacc_g)) P^-1 + (gc0_g, 0)
         std::vector<KsItem> gi;
         for (int g = 0; g < groups; g++) {
-            u64* a = acc[gs[c0 + g]];
+            u64* a = acc[gs[g0 + g]];
             gi.push_back({nullptr, nullptr, gc0 + (size_t)g * l1 * n, a, a + lw, a, a + lw, 1});
         }
         moddown_run(c, gi, c.arena.push_vec(gi, s), gacc, level, s);
